@@ -1,0 +1,184 @@
+/*
+ * lbcm.h -- C ABI of the GB300 (sm_103a) colour-gradient lattice Boltzmann library with
+ * nonorthogonal central moments (Saito, De Rosis, Festuccia, Kaneko, Abe, Koyama,
+ * "Color-gradient lattice Boltzmann model with nonorthogonal central moments:
+ * Hydrodynamic melt-jet breakup simulations", arXiv:1804.08923).
+ *
+ * One context holds one D3Q27 lattice resident on one GPU.  lb_step advances it by the
+ * paper's time step (Section II): pull streaming with the Section IV.A boundaries, the
+ * phase field and its isotropic gradient, the central-moment collision (Eq. scoll with
+ * Eqs. EES, Phi, ketF, ketFd), the perturbation (Eq. perturb) and the recolouring
+ * (Eqs. op3r, op3b).
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked "device" must be CUDA device pointers on the context's device;
+ *    "host" pointers are ordinary host memory (pinned memory is faster, not required).
+ *  - Every call is ordered on the CUDA stream given at creation.  Only lb_mass, lb_save,
+ *    lb_load, the host variants of lb_fields / lb_populations / lb_init, and lb_step at a
+ *    check_every boundary synchronise that stream.
+ *  - Errors are returned as lb_status; a message for the calling thread is available from
+ *    lb_last_error().  No call aborts or throws across this interface.
+ *  - Populations are laid out [k][i][z][y][x] (k = 0 red, 1 blue; i in the order of
+ *    Eq. velVec; x fastest), single precision.
+ */
+#ifndef LBCM_H
+#define LBCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBCM_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define LB_API __attribute__((visibility("default")))
+#else
+#define LB_API
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,     /* invalid argument or parameter combination */
+    LB_ENOMEM = 2,     /* device allocation failed */
+    LB_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    LB_EUNSTABLE = 4,  /* a periodic check found a non-finite colour mass */
+    LB_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    LB_ESTATE = 6,     /* call out of order (e.g. lb_step before lb_init) */
+    LB_ENOTIMPL = 7    /* entry point declared but not provided by this build */
+} lb_status;
+
+/* Boundary kinds.  x and y are always periodic.  z_lo: PERIODIC, FREESLIP or INLET;
+ * z_hi: PERIODIC, FREESLIP or CONVECTIVE; PERIODIC must be given for both or neither. */
+typedef enum {
+    LB_BC_PERIODIC = 0,
+    LB_BC_FREESLIP = 1,   /* half-way specular reflection (Section IV.A, wall boundaries) */
+    LB_BC_INLET = 2,      /* circular inflow disc with free slip around it (Section IV.A) */
+    LB_BC_CONVECTIVE = 3  /* first-order implicit convective outflow (Section IV.A) */
+} lb_bc;
+
+typedef struct {
+    int32_t nx, ny, nz;    /* lattice extent; nx*ny*nz < 2^31 */
+    int32_t bc_zlo, bc_zhi;
+} lb_grid;
+
+typedef enum { LB_STORE_FP32 = 0 } lb_storage;
+
+typedef struct {
+    double rho_r0, rho_b0;  /* initial densities (Eq. order); gamma = rho_r0/rho_b0 >= 19/27 */
+    double nu_r, nu_b;      /* kinematic viscosities, > 0; s_2nu from Eq. (shear) */
+    double sigma;           /* interfacial tension; A = 9 sigma / (4 tau(x)) from Eq. (sigma) */
+    double beta;            /* recolouring parameter of Eqs. (op3r, op3b); 0.7 in the paper */
+    double g[3];            /* gravity in the body force F = (rho - rho_b0) g (Eq. bodyForceJet) */
+    double s0, s1;          /* rates of the conserved moments; 0 in the paper */
+    double s2b, s3, s4, s5, s6; /* bulk and higher-order rates; 1 in the paper */
+    double u_in;            /* inlet plug velocity u_j0 along +z */
+    double d_in;            /* inlet disc diameter D_j0, centred at ((nx-1)/2, (ny-1)/2) */
+    double noise_amp;       /* relative amplitude a of the radial inlet noise, 0 = none */
+    uint64_t seed;          /* seed of the counter-based inlet noise */
+    double eps_grad;        /* regulariser: |grad phi| -> sqrt(|grad phi|^2 + eps^2) */
+    int32_t storage;        /* lb_storage */
+    int32_t check_every;    /* every so many steps lb_step checks the colour masses (0 = never) */
+} lb_params;
+
+/* Fills *p with the paper's defaults: rho_r0 = rho_b0 = 1, nu = 1/6, sigma = 0, beta = 0.7,
+ * g = 0, s0 = s1 = 0, s2b..s6 = 1, no inlet, eps_grad = 1e-6, FP32 storage, no checks. */
+LB_API void lb_params_default(lb_params *p);
+
+typedef struct lb_ctx lb_ctx;
+
+/* Number and byte sizes of the device buffers a context needs (at most LB_MAX_BUFFERS).
+ * Buffer 0 and 1: population ping-pong, 54 * nodes * 4 bytes each; 2: densities
+ * rho_r, rho_b of the current step; 3: outflow history ping-pong; 4: small tables and
+ * reduction partials.  Returns LB_EINVAL for invalid grids or parameters. */
+#define LB_MAX_BUFFERS 8
+LB_API lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *sizes_out, int32_t *n_out);
+
+/* Creates a context and allocates its device buffers with cudaMalloc on the current
+ * device.  stream: a cudaStream_t (NULL = legacy default stream).  *out is set only on
+ * success; the caller releases it with lb_destroy. */
+LB_API lb_status lb_create(const lb_grid *grid, const lb_params *params, void *stream, lb_ctx **out);
+
+/* As lb_create, but on caller-owned device memory (e.g. from PyTorch's allocator):
+ * bufs[j] must hold at least sizes[j] bytes as reported by lb_buffer_sizes, aligned to
+ * 256 bytes.  The buffers must outlive the context; lb_destroy does not free them. */
+LB_API lb_status lb_create_with_buffers(const lb_grid *grid, const lb_params *params, void *stream,
+                                 void *const *bufs, const size_t *sizes, int32_t n, lb_ctx **out);
+
+/* Initial state kinds for lb_init. */
+typedef enum {
+    LB_INIT_UNIFORM = 0, /* args = {rho_r, rho_b, ux, uy, uz} */
+    LB_INIT_DROPLET = 1, /* args = {R, W}: red sphere of Section III at the domain centre */
+    LB_INIT_JET = 2,     /* args unused: quiescent all-blue domain of Section IV.A */
+    LB_INIT_FIELDS = 3   /* rho_r, rho_b (nodes each) and u (3*nodes, component-major) given */
+} lb_init_kind;
+
+/* Sets populations from fields: f_i^k = rho_k [varphi_i(alpha_k) + w_i (3 cu + 9/2 cu^2
+ * - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2)] (the equilibrium of Eq. EES per colour with Phi = 0),
+ * copies the outflow plane into the history, and resets the step counter to 0.
+ * fields_on_device: 1 if rho_r/rho_b/u are device pointers, 0 for host pointers. */
+LB_API lb_status lb_init(lb_ctx *ctx, int32_t kind, const double *args, int32_t nargs,
+                  const float *rho_r, const float *rho_b, const float *u, int32_t fields_on_device);
+
+/* Advances the lattice by n >= 0 time steps (Eq. LBE with the operator split of Section II). */
+LB_API lb_status lb_step(lb_ctx *ctx, int64_t n);
+
+/* Number of steps taken since lb_init / lb_load. */
+LB_API int64_t lb_step_count(const lb_ctx *ctx);
+
+/* Macroscopic fields of the current post-collision state, one float per node each:
+ * rho_r, rho_b (sums of the colour populations), phi (Eq. order), u_x, u_y, u_z
+ * (rho u = sum_i f_i c_i - F/2, the collision having added F), p (Eq. press with rho and
+ * alpha-bar).  mask selects outputs (bit j = LB_FIELD_*); outs[j] receives field j when
+ * its bit is set.  on_device: outs are device (1) or host (0) pointers. */
+enum { LB_FIELD_RHO_R = 0, LB_FIELD_RHO_B = 1, LB_FIELD_PHI = 2, LB_FIELD_UX = 3,
+       LB_FIELD_UY = 4, LB_FIELD_UZ = 5, LB_FIELD_P = 6, LB_NFIELDS = 7 };
+LB_API lb_status lb_fields(lb_ctx *ctx, uint32_t mask, float *const *outs, int32_t on_device);
+
+/* Copies the current populations [k][i][z][y][x] (54 * nodes floats) into out. */
+LB_API lb_status lb_populations(lb_ctx *ctx, float *out, int32_t on_device);
+
+/* Copies the outflow history plane [k][i][y][x] (54 * nx * ny floats) into out. */
+LB_API lb_status lb_history(lb_ctx *ctx, float *out, int32_t on_device);
+
+/* Per-colour total mass of the current state, summed in FP64 on the device with a
+ * fixed-order two-stage reduction (deterministic).  out[0] red, out[1] blue.  A
+ * non-finite population makes the corresponding sum non-finite.  Synchronises. */
+LB_API lb_status lb_mass(lb_ctx *ctx, double out[2]);
+
+/* Checkpoint: lb_save writes the state (header, populations, history, step counter) to
+ * host memory.  Pass buf = NULL to query the size in *nbytes.  lb_load restores a state
+ * saved from a context with the same grid and storage.  Both synchronise. */
+LB_API lb_status lb_save(lb_ctx *ctx, void *buf, size_t *nbytes);
+LB_API lb_status lb_load(lb_ctx *ctx, const void *buf, size_t nbytes);
+
+/* Kernel timing for profiling.  lb_profile_enable(ctx, capacity) makes the following
+ * lb_step calls bracket each kernel launch with CUDA events on the context's stream, for
+ * at most `capacity` steps (events are created here, not during stepping); capacity 0
+ * disables.  lb_profile_read synchronises, writes per-kernel total device milliseconds
+ * and launch counts (index LB_KERNEL_*, up to n_kinds entries), and clears the record. */
+enum { LB_KERNEL_BOUNDARY = 0, LB_KERNEL_PHASE_FIELD = 1, LB_KERNEL_COLLIDE = 2, LB_NKERNELS = 3 };
+LB_API lb_status lb_profile_enable(lb_ctx *ctx, int32_t capacity);
+LB_API lb_status lb_profile_read(lb_ctx *ctx, double *ms, int64_t *launches, int32_t n_kinds);
+
+/* Total number of kernels this context has launched since creation. */
+LB_API int64_t lb_kernel_launches(const lb_ctx *ctx);
+
+/* Discrete adjoint of lb_step (gradient of an objective at step T with respect to
+ * inlet velocity, sigma, viscosity and inlet profile).  Not provided by this build:
+ * returns LB_ENOTIMPL. */
+LB_API lb_status lb_adjoint(lb_ctx *ctx, int32_t objective, int64_t T, const double *obj_args,
+                     double *grad_out, int32_t n_grad);
+
+/* Message for the last failing call made by this thread ("" if none). */
+LB_API const char *lb_last_error(void);
+
+/* Releases the context (and its buffers when it allocated them).  NULL is ignored. */
+LB_API void lb_destroy(lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBCM_H */

@@ -1,0 +1,183 @@
+"""GB300 colour-gradient lattice Boltzmann with nonorthogonal central moments
+(arXiv:1804.08923): Python binding of the C ABI in ``include/lbcm.h``.
+
+The binding only marshals arguments: every step of the method runs in the CUDA kernels
+of ``liblbcm.so``.  PyTorch supplies device memory (``lb_create_with_buffers``) and the
+CUDA stream.  There is no CPU fallback: without the compiled library or a GPU, creating
+a lattice raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _abi
+from ._abi import (BC_CONVECTIVE, BC_FREESLIP, BC_INLET, BC_PERIODIC, FIELD_NAMES, INIT_DROPLET, INIT_FIELDS,
+                   INIT_JET, INIT_UNIFORM, LBError, library, make_grid, make_params)
+
+__all__ = ["Lattice", "LBError", "library", "make_grid", "make_params", "BC_PERIODIC", "BC_FREESLIP",
+           "BC_INLET", "BC_CONVECTIVE", "FIELD_NAMES"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Lattice:
+    """One D3Q27 two-colour lattice resident on a CUDA device.
+
+    grid: (nx, ny, nz); bc: (bc_zlo, bc_zhi); params: dict of lb_params fields.
+    Buffers are torch uint8 tensors owned by this object (PyTorch's caching allocator);
+    the library works on them through lb_create_with_buffers.
+    """
+
+    def __init__(self, grid, params: dict, bc=(BC_PERIODIC, BC_PERIODIC), device=None, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1804_08923_gb300 needs a CUDA device; no CPU fallback exists")
+        self.lib = library()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.nx, self.ny, self.nz = (int(v) for v in grid)
+        self.shape = (self.nz, self.ny, self.nx)
+        self.nodes = self.nx * self.ny * self.nz
+        self._g = make_grid(self.nx, self.ny, self.nz, *bc)
+        self._p = make_params(params)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            sizes = (C.c_size_t * _abi.MAX_BUFFERS)()
+            n = C.c_int32()
+            _abi.check(self.lib.lb_buffer_sizes(C.byref(self._g), C.byref(self._p), sizes, C.byref(n)))
+            self._bufs = [torch.empty(int(sizes[j]), dtype=torch.uint8, device=self.device) for j in range(n.value)]
+            ptrs = (C.c_void_p * n.value)(*[b.data_ptr() for b in self._bufs])
+            szs = (C.c_size_t * n.value)(*[int(sizes[j]) for j in range(n.value)])
+            ctx = C.c_void_p()
+            _abi.check(self.lib.lb_create_with_buffers(C.byref(self._g), C.byref(self._p),
+                                                       C.c_void_p(self.stream.cuda_stream), ptrs, szs, n,
+                                                       C.byref(ctx)))
+            self._ctx = ctx
+
+    # ------------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self.lib.lb_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ init
+    def init_uniform(self, rho_r, rho_b, u=(0.0, 0.0, 0.0)):
+        args = (C.c_double * 5)(rho_r, rho_b, *u)
+        _abi.check(self.lib.lb_init(self._ctx, INIT_UNIFORM, args, 5, None, None, None, 0))
+
+    def init_droplet(self, R, W=4.0):
+        args = (C.c_double * 2)(R, W)
+        _abi.check(self.lib.lb_init(self._ctx, INIT_DROPLET, args, 2, None, None, None, 0))
+
+    def init_jet(self):
+        _abi.check(self.lib.lb_init(self._ctx, INIT_JET, None, 0, None, None, None, 0))
+
+    def init_fields(self, rho_r, rho_b, u):
+        """Fields as numpy arrays (host) or CUDA float32 tensors (device); shapes
+        (nz, ny, nx) and (3, nz, ny, nx)."""
+        torch = _torch()
+        if isinstance(rho_r, torch.Tensor) and rho_r.is_cuda:
+            ts = [t.to(self.device, torch.float32).contiguous() for t in (rho_r, rho_b, u)]
+            ps = [C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_float)) for t in ts]
+            _abi.check(self.lib.lb_init(self._ctx, INIT_FIELDS, None, 0, ps[0], ps[1], ps[2], 1))
+            self.stream.synchronize()
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (rho_r, rho_b, u)]
+            assert arrs[0].size == self.nodes and arrs[1].size == self.nodes and arrs[2].size == 3 * self.nodes
+            ps = [a.ctypes.data_as(C.POINTER(C.c_float)) for a in arrs]
+            _abi.check(self.lib.lb_init(self._ctx, INIT_FIELDS, None, 0, ps[0], ps[1], ps[2], 0))
+
+    # ------------------------------------------------------------------ stepping
+    def step(self, n=1):
+        _abi.check(self.lib.lb_step(self._ctx, C.c_int64(n)))
+
+    @property
+    def step_count(self) -> int:
+        return int(self.lib.lb_step_count(self._ctx))
+
+    # ------------------------------------------------------------------ outputs
+    def fields(self, names=FIELD_NAMES, device=True, out=None):
+        """Dict of macroscopic fields (float32, shape (nz, ny, nx)) as CUDA tensors
+        (device=True) or numpy arrays (device=False); `out` may supply the arrays."""
+        torch = _torch()
+        mask, outs, keep = 0, (C.POINTER(C.c_float) * len(FIELD_NAMES))(), {}
+        for j, nm in enumerate(FIELD_NAMES):
+            if nm not in names:
+                continue
+            mask |= 1 << j
+            if device:
+                t = out[nm] if out else torch.empty(self.shape, dtype=torch.float32, device=self.device)
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == self.nodes
+                outs[j] = C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_float))
+            else:
+                t = out[nm] if out else np.empty(self.shape, dtype=np.float32)
+                assert t.dtype == np.float32 and t.flags.c_contiguous and t.size == self.nodes
+                outs[j] = t.ctypes.data_as(C.POINTER(C.c_float))
+            keep[nm] = t
+        _abi.check(self.lib.lb_fields(self._ctx, C.c_uint32(mask), outs, 1 if device else 0))
+        return keep
+
+    def populations(self, device=True):
+        """Current populations, shape (2, 27, nz, ny, nx), float32."""
+        torch = _torch()
+        shp = (2, 27) + self.shape
+        if device:
+            t = torch.empty(shp, dtype=torch.float32, device=self.device)
+            _abi.check(self.lib.lb_populations(self._ctx, C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_float)), 1))
+            return t
+        a = np.empty(shp, dtype=np.float32)
+        _abi.check(self.lib.lb_populations(self._ctx, a.ctypes.data_as(C.POINTER(C.c_float)), 0))
+        return a
+
+    def history(self):
+        """Outflow history plane, shape (2, 27, ny, nx), float32 numpy."""
+        a = np.empty((2, 27, self.ny, self.nx), dtype=np.float32)
+        _abi.check(self.lib.lb_history(self._ctx, a.ctypes.data_as(C.POINTER(C.c_float)), 0))
+        return a
+
+    def mass(self):
+        out = (C.c_double * 2)()
+        _abi.check(self.lib.lb_mass(self._ctx, out))
+        return np.array([out[0], out[1]])
+
+    def save(self) -> bytes:
+        n = C.c_size_t()
+        _abi.check(self.lib.lb_save(self._ctx, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _abi.check(self.lib.lb_save(self._ctx, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    # ------------------------------------------------------------------ profiling
+    def profile_enable(self, capacity: int):
+        _abi.check(self.lib.lb_profile_enable(self._ctx, int(capacity)))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total device ms, launches)} since profile_enable / the last read."""
+        ms = (C.c_double * 3)()
+        cnt = (C.c_int64 * 3)()
+        _abi.check(self.lib.lb_profile_read(self._ctx, ms, cnt, 3))
+        return {_abi.KERNEL_NAMES[k]: (ms[k], int(cnt[k])) for k in range(3)}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.lb_kernel_launches(self._ctx))
+
+    def load(self, blob: bytes):
+        _abi.check(self.lib.lb_load(self._ctx, blob, C.c_size_t(len(blob))))

@@ -1,0 +1,656 @@
+// lbcm_api.cu -- host side of the C ABI declared in include/lbcm.h: parameter
+// validation, device buffers, initial states, macroscopic fields, FP64 colour-mass
+// reduction, checkpoints, and the step loop.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbcm.h"
+#include "lbcm_device.cuh"
+#include "lbcm_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+lb_status fail(lb_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+lb_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(LB_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define LB_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr int kMassBlocks = 1024;  // fixed first-stage grid: the reduction order never changes
+constexpr int kMassThreads = 256;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct AuxLayout {
+    size_t disc, zin, zout, partial, total;
+};
+
+AuxLayout aux_layout(const lb_grid &g) {
+    const size_t plane = (size_t)g.nx * g.ny;
+    AuxLayout L;
+    size_t off = 0;
+    L.disc = off;
+    off = align_up(off + plane);
+    L.zin = off;
+    off = align_up(off + 18 * plane * sizeof(float));
+    L.zout = off;
+    off = align_up(off + 18 * plane * sizeof(float));
+    L.partial = off;
+    off = align_up(off + 2 * kMassBlocks * sizeof(double) + 2 * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+lb_status validate(const lb_grid *g, const lb_params *p) {
+    if (!g || !p) return fail(LB_EINVAL, "grid and params must not be NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(LB_EINVAL, "lattice extents must be >= 1");
+    const long long nn = (long long)g->nx * g->ny * g->nz;
+    if (nn >= (1ll << 31)) return fail(LB_EINVAL, "nx*ny*nz must be < 2^31");
+    const bool zlo_ok = g->bc_zlo == LB_BC_PERIODIC || g->bc_zlo == LB_BC_FREESLIP || g->bc_zlo == LB_BC_INLET;
+    const bool zhi_ok = g->bc_zhi == LB_BC_PERIODIC || g->bc_zhi == LB_BC_FREESLIP || g->bc_zhi == LB_BC_CONVECTIVE;
+    if (!zlo_ok || !zhi_ok) return fail(LB_EINVAL, "bc_zlo must be PERIODIC/FREESLIP/INLET, bc_zhi PERIODIC/FREESLIP/CONVECTIVE");
+    if ((g->bc_zlo == LB_BC_PERIODIC) != (g->bc_zhi == LB_BC_PERIODIC))
+        return fail(LB_EINVAL, "z must be periodic at both ends or at neither");
+    if (g->bc_zlo != LB_BC_PERIODIC && g->nz < 2) return fail(LB_EINVAL, "walls need nz >= 2");
+    if (g->bc_zhi == LB_BC_CONVECTIVE && g->nz < 3) return fail(LB_EINVAL, "convective outflow needs nz >= 3");
+    if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0)) return fail(LB_EINVAL, "rho_r0 and rho_b0 must be > 0");
+    if (!(p->nu_r > 0) || !(p->nu_b > 0)) return fail(LB_EINVAL, "nu_r and nu_b must be > 0");
+    const double gamma = p->rho_r0 / p->rho_b0;
+    const double alpha_r = 1.0 - (1.0 - 8.0 / 27.0) / gamma;
+    if (!(alpha_r >= 0.0 && alpha_r < 1.0)) return fail(LB_EINVAL, "density ratio gamma must be >= 19/27 (alpha_r in [0,1))");
+    if (!(p->sigma >= 0) || !std::isfinite(p->sigma)) return fail(LB_EINVAL, "sigma must be finite and >= 0");
+    if (!std::isfinite(p->beta)) return fail(LB_EINVAL, "beta must be finite");
+    const double s[7] = {p->s0, p->s1, p->s2b, p->s3, p->s4, p->s5, p->s6};
+    for (double v : s)
+        if (!(v >= 0.0 && v < 2.0)) return fail(LB_EINVAL, "relaxation rates must lie in [0, 2)");
+    if (!(p->eps_grad >= 0) || !std::isfinite(p->eps_grad)) return fail(LB_EINVAL, "eps_grad must be finite and >= 0");
+    if (p->storage != LB_STORE_FP32) return fail(LB_EINVAL, "storage must be LB_STORE_FP32");
+    if (p->check_every < 0) return fail(LB_EINVAL, "check_every must be >= 0");
+    if (g->bc_zlo == LB_BC_INLET) {
+        if (!(p->d_in >= 0) || !std::isfinite(p->d_in) || !std::isfinite(p->u_in) || !std::isfinite(p->noise_amp))
+            return fail(LB_EINVAL, "inlet parameters must be finite, d_in >= 0");
+    }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p->g[d])) return fail(LB_EINVAL, "gravity must be finite");
+    return LB_OK;
+}
+
+}  // namespace
+
+struct lb_ctx {
+    lb_grid g;
+    lb_params p;
+    cudaStream_t stream = nullptr;
+    bool owns = false;
+    void *bufs[LB_MAX_BUFFERS] = {};
+    size_t sizes[LB_MAX_BUFFERS] = {};
+    int nbufs = 0;
+    float *pop[2] = {nullptr, nullptr};
+    float *rho = nullptr;
+    float *hist[2] = {nullptr, nullptr};
+    uint8_t *disc = nullptr;
+    float *zin = nullptr, *zout = nullptr;
+    double *partial = nullptr;
+    int cur = 0, hcur = 0;
+    int64_t step = 0;
+    bool initialized = false;
+    long long nn = 0, plane = 0;
+    long long launches = 0;
+    std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded step
+    int prof_cap = 0, prof_used = 0;
+};
+
+namespace lbcm {
+
+// ------------------------------------------------------------ initial populations
+// f_i^k = rho_k [varphi_i(alpha_k) + w_i P(c_i.u, u^2)]  (Eq. EES per colour, Phi = 0)
+__global__ void init_kernel(float *__restrict__ pop, float *__restrict__ hist, const float *__restrict__ fr,
+                            const float *__restrict__ fb, const float *__restrict__ fu, int kind, int nx, int ny, int nz,
+                            float a0, float a1, float a2, float a3, float a4, float rho_r0, float rho_b0,
+                            float alpha_r, float alpha_b) {
+    const long long NN = (long long)nx * ny * nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+        float rr, rb, ux = 0.0f, uy = 0.0f, uz = 0.0f;
+        if (kind == LB_INIT_UNIFORM) {
+            rr = a0; rb = a1; ux = a2; uy = a3; uz = a4;
+        } else if (kind == LB_INIT_DROPLET) {
+            // Section III: rho_r = rho_r0/2 [1 - tanh(2(r-R)/W)], rho_b = rho_b0/2 [1 + tanh(...)]
+            const float dx = x - 0.5f * (nx - 1), dy = y - 0.5f * (ny - 1), dz = z - 0.5f * (nz - 1);
+            const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float t = tanhf(2.0f * (r - a0) / a1);
+            rr = 0.5f * rho_r0 * (1.0f - t);
+            rb = 0.5f * rho_b0 * (1.0f + t);
+        } else if (kind == LB_INIT_JET) {
+            rr = 0.0f; rb = rho_b0;
+        } else {
+            rr = fr[n]; rb = fb[n]; ux = fu[n]; uy = fu[NN + n]; uz = fu[2 * NN + n];
+        }
+        const float usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+            const float pw = wgt(i) * eq_poly(cu, usq);
+            const float vr = rr * (varphi(i, alpha_r, 1.0f - alpha_r) + pw);
+            const float vb = rb * (varphi(i, alpha_b, 1.0f - alpha_b) + pw);
+            pop[(long long)i * NN + n] = vr;
+            pop[(long long)(27 + i) * NN + n] = vb;
+            if (z == nz - 1) {
+                const long long h = (long long)y * nx + x, P = (long long)nx * ny;
+                hist[(long long)i * P + h] = vr;
+                hist[(long long)(27 + i) * P + h] = vb;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------- fields
+__global__ void fields_kernel(const float *__restrict__ pop, float *o_rr, float *o_rb,
+                              float *o_phi, float *o_ux, float *o_uy, float *o_uz, float *o_p, long long NN,
+                              float inv_rho_r0, float inv_rho_b0, float rho_b0, float gx, float gy, float gz,
+                              float alpha_r, float alpha_b) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+        float rr = 0.0f, rb = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const float a = __ldg(pop + (long long)i * NN + n), b = __ldg(pop + (long long)(27 + i) * NN + n);
+            rr += a;
+            rb += b;
+            if (cx(i) != 0) jx += cx(i) * (a + b);
+            if (cy(i) != 0) jy += cy(i) * (a + b);
+            if (cz(i) != 0) jz += cz(i) * (a + b);
+        }
+        const float rho = rr + rb;
+        const float A = rr * inv_rho_r0, B = rb * inv_rho_b0;
+        const float phi = (A - B) / (A + B);
+        const float fo = rho - rho_b0;
+        if (o_rr) o_rr[n] = rr;
+        if (o_rb) o_rb[n] = rb;
+        if (o_phi) o_phi[n] = phi;
+        if (o_ux) o_ux[n] = (jx - 0.5f * fo * gx) / rho;
+        if (o_uy) o_uy[n] = (jy - 0.5f * fo * gy) / rho;
+        if (o_uz) o_uz[n] = (jz - 0.5f * fo * gz) / rho;
+        if (o_p) {
+            const float alpha = 0.5f * (1.0f + phi) * alpha_r + 0.5f * (1.0f - phi) * alpha_b;
+            o_p[n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (press)
+        }
+    }
+}
+
+// ------------------------------------------------------------- FP64 colour mass
+// Stage 1: block b of colour k adds, in FP64 and a fixed order, every population of its
+// fixed node range, reduces the block by warp shuffles and writes one partial.  Stage 2:
+// one block adds the partials in a fixed tree order.
+__global__ void __launch_bounds__(kMassThreads) mass_partial_kernel(const float *__restrict__ pop, long long NN,
+                                                                    double *__restrict__ partial) {
+    const int k = blockIdx.y;
+    const long long per = (NN + gridDim.x - 1) / gridDim.x;
+    const long long n0 = blockIdx.x * per, n1 = min(NN, n0 + per);
+    double acc = 0.0;
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) acc += (double)__ldg(pop + (long long)(27 * k + i) * NN + n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double warp_sums[kMassThreads / 32];
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kMassThreads / 32; ++w) t += warp_sums[w];
+        partial[k * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) mass_final_kernel(const double *__restrict__ partial, int nblocks,
+                                                          double *__restrict__ out) {
+    __shared__ double s[1024];
+    for (int k = 0; k < 2; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partial[k * nblocks + b];
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = s[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace lbcm
+
+namespace {
+
+using namespace lbcm;
+
+lb_status setup_ctx(lb_ctx *c) {
+    const lb_grid &g = c->g;
+    c->nn = (long long)g.nx * g.ny * g.nz;
+    c->plane = (long long)g.nx * g.ny;
+    const size_t pop_bytes = (size_t)54 * c->nn * sizeof(float);
+    const size_t hist_bytes = (size_t)54 * c->plane * sizeof(float);
+    c->pop[0] = (float *)c->bufs[0];
+    c->pop[1] = (float *)c->bufs[1];
+    c->rho = (float *)c->bufs[2];
+    c->hist[0] = (float *)c->bufs[3];
+    c->hist[1] = (float *)((char *)c->bufs[3] + align_up(hist_bytes));
+    const AuxLayout L = aux_layout(g);
+    char *aux = (char *)c->bufs[4];
+    c->disc = (uint8_t *)(aux + L.disc);
+    c->zin = (float *)(aux + L.zin);
+    c->zout = (float *)(aux + L.zout);
+    c->partial = (double *)(aux + L.partial);
+    (void)pop_bytes;
+    // inlet disc membership, decided in FP64 on the host:
+    // (2x - (nx-1))^2 + (2y - (ny-1))^2 < D^2  <=>  (x - x_c)^2 + (y - y_c)^2 < (D/2)^2
+    std::vector<uint8_t> disc((size_t)c->plane, 0);
+    if (g.bc_zlo == LB_BC_INLET) {
+        for (int y = 0; y < g.ny; ++y)
+            for (int x = 0; x < g.nx; ++x) {
+                const double dx = 2.0 * x - (g.nx - 1), dy = 2.0 * y - (g.ny - 1);
+                disc[(size_t)y * g.nx + x] = dx * dx + dy * dy < c->p.d_in * c->p.d_in;
+            }
+    }
+    LB_CUDA(cudaMemcpyAsync(c->disc, disc.data(), disc.size(), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaMemsetAsync(c->zin, 0, 18 * c->plane * sizeof(float), c->stream));
+    LB_CUDA(cudaMemsetAsync(c->zout, 0, 18 * c->plane * sizeof(float), c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+StepArgs make_args(const lb_ctx *c) {
+    const lb_grid &g = c->g;
+    const lb_params &p = c->p;
+    StepArgs a{};
+    a.pin = c->pop[c->cur];
+    a.pout = c->pop[c->cur ^ 1];
+    a.rho = c->rho;
+    a.hist_in = c->hist[c->hcur];
+    a.hist_out = c->hist[c->hcur ^ 1];
+    a.zin = c->zin;
+    a.zout = c->zout;
+    a.disc = c->disc;
+    a.NN = c->nn;
+    a.plane = c->plane;
+    a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+    a.bc_zlo = g.bc_zlo; a.bc_zhi = g.bc_zhi;
+    a.rho_r0 = (float)p.rho_r0; a.rho_b0 = (float)p.rho_b0;
+    a.inv_rho_r0 = (float)(1.0 / p.rho_r0); a.inv_rho_b0 = (float)(1.0 / p.rho_b0);
+    const double alpha_b = 8.0 / 27.0;
+    a.alpha_b = (float)alpha_b;
+    a.alpha_r = (float)(1.0 - (1.0 - alpha_b) / (p.rho_r0 / p.rho_b0));
+    a.inv_nu_r = (float)(1.0 / p.nu_r); a.inv_nu_b = (float)(1.0 / p.nu_b);
+    a.sigma = (float)p.sigma; a.beta = (float)p.beta;
+    a.eps2 = (float)(p.eps_grad * p.eps_grad);
+    a.gx = (float)p.g[0]; a.gy = (float)p.g[1]; a.gz = (float)p.g[2];
+    a.s0 = (float)p.s0; a.s1 = (float)p.s1; a.s2b = (float)p.s2b; a.s3 = (float)p.s3;
+    a.s4 = (float)p.s4; a.s5 = (float)p.s5; a.s6 = (float)p.s6;
+    a.u_in = (float)p.u_in; a.noise_amp = (float)p.noise_amp;
+    a.xc = (float)(0.5 * (g.nx - 1)); a.yc = (float)(0.5 * (g.ny - 1));
+    a.seed = p.seed;
+    a.step = c->step;
+    return a;
+}
+
+lb_status run_mass(lb_ctx *c, const float *pop, double out[2]) {
+    mass_partial_kernel<<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(pop, c->nn, c->partial);
+    mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->partial, kMassBlocks, c->partial + 2 * kMassBlocks);
+    c->launches += 2;
+    LB_CUDA(cudaGetLastError());
+    LB_CUDA(cudaMemcpyAsync(out, c->partial + 2 * kMassBlocks, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)std::min<long long>(std::max<long long>(b, 1), 152ll * 64);
+}
+
+constexpr uint64_t kMagic = 0x314D43424C4C4231ull;  // "1BLLBCM1"
+
+}  // namespace
+
+extern "C" {
+
+void lb_params_default(lb_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->rho_r0 = 1.0;
+    p->rho_b0 = 1.0;
+    p->nu_r = p->nu_b = 1.0 / 6.0;
+    p->beta = 0.7;
+    p->s2b = p->s3 = p->s4 = p->s5 = p->s6 = 1.0;
+    p->eps_grad = 1e-6;
+    p->storage = LB_STORE_FP32;
+}
+
+const char *lb_last_error(void) { return g_err.c_str(); }
+
+lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *sizes_out, int32_t *n_out) {
+    lb_status s = validate(grid, params);
+    if (s != LB_OK) return s;
+    if (!sizes_out || !n_out) return fail(LB_EINVAL, "sizes_out and n_out must not be NULL");
+    const size_t nn = (size_t)grid->nx * grid->ny * grid->nz, plane = (size_t)grid->nx * grid->ny;
+    sizes_out[0] = align_up(54 * nn * sizeof(float));
+    sizes_out[1] = sizes_out[0];
+    sizes_out[2] = align_up(2 * nn * sizeof(float));
+    sizes_out[3] = 2 * align_up(54 * plane * sizeof(float));
+    sizes_out[4] = aux_layout(*grid).total;
+    *n_out = 5;
+    return LB_OK;
+}
+
+static lb_status create_common(const lb_grid *grid, const lb_params *params, void *stream, void *const *bufs,
+                               const size_t *sizes, int32_t n, bool own, lb_ctx **out) {
+    if (!out) return fail(LB_EINVAL, "out must not be NULL");
+    size_t need[LB_MAX_BUFFERS];
+    int32_t nb = 0;
+    lb_status s = lb_buffer_sizes(grid, params, need, &nb);
+    if (s != LB_OK) return s;
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(LB_ENOMEM, "host allocation of the context failed");
+    c->g = *grid;
+    c->p = *params;
+    c->stream = (cudaStream_t)stream;
+    c->owns = own;
+    c->nbufs = nb;
+    if (own) {
+        for (int j = 0; j < nb; ++j) {
+            cudaError_t e = cudaMalloc(&c->bufs[j], need[j]);
+            if (e != cudaSuccess) {
+                for (int q = 0; q < j; ++q) cudaFree(c->bufs[q]);
+                delete c;
+                (void)cudaGetLastError();
+                return fail(LB_ENOMEM, std::string("cudaMalloc of ") + std::to_string(need[j]) + " bytes failed: " +
+                                           cudaGetErrorString(e));
+            }
+            c->sizes[j] = need[j];
+        }
+    } else {
+        if (!bufs || !sizes || n < nb) {
+            delete c;
+            return fail(LB_EINVAL, "lb_create_with_buffers needs as many buffers as lb_buffer_sizes reports");
+        }
+        for (int j = 0; j < nb; ++j) {
+            if (!bufs[j] || sizes[j] < need[j] || ((uintptr_t)bufs[j] % kAlign) != 0) {
+                delete c;
+                return fail(LB_EINVAL, "buffer " + std::to_string(j) + " is NULL, too small or not 256-byte aligned");
+            }
+            c->bufs[j] = bufs[j];
+            c->sizes[j] = sizes[j];
+        }
+    }
+    s = setup_ctx(c);
+    if (s != LB_OK) {
+        lb_destroy(c);
+        return s;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_grid *grid, const lb_params *params, void *stream, lb_ctx **out) {
+    return create_common(grid, params, stream, nullptr, nullptr, 0, true, out);
+}
+
+lb_status lb_create_with_buffers(const lb_grid *grid, const lb_params *params, void *stream, void *const *bufs,
+                                 const size_t *sizes, int32_t n, lb_ctx **out) {
+    return create_common(grid, params, stream, bufs, sizes, n, false, out);
+}
+
+static void free_profile(lb_ctx *c) {
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_cap = c->prof_used = 0;
+}
+
+void lb_destroy(lb_ctx *c) {
+    if (!c) return;
+    free_profile(c);
+    if (c->owns)
+        for (int j = 0; j < c->nbufs; ++j)
+            if (c->bufs[j]) cudaFree(c->bufs[j]);
+    delete c;
+}
+
+lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, const float *rho_r, const float *rho_b,
+                  const float *u, int32_t fields_on_device) {
+    if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
+    float a[5] = {0, 0, 0, 0, 0};
+    const float *fr = nullptr, *fb = nullptr, *fu = nullptr;
+    switch (kind) {
+        case LB_INIT_UNIFORM:
+            if (!args || nargs < 5) return fail(LB_EINVAL, "UNIFORM needs args {rho_r, rho_b, ux, uy, uz}");
+            for (int j = 0; j < 5; ++j) a[j] = (float)args[j];
+            if (!(a[0] >= 0 && a[1] >= 0 && a[0] + a[1] > 0)) return fail(LB_EINVAL, "UNIFORM densities must be >= 0 with a positive sum");
+            break;
+        case LB_INIT_DROPLET:
+            if (!args || nargs < 2 || !(args[0] > 0) || !(args[1] > 0)) return fail(LB_EINVAL, "DROPLET needs args {R > 0, W > 0}");
+            a[0] = (float)args[0];
+            a[1] = (float)args[1];
+            break;
+        case LB_INIT_JET:
+            break;
+        case LB_INIT_FIELDS:
+            if (!rho_r || !rho_b || !u) return fail(LB_EINVAL, "FIELDS needs rho_r, rho_b and u");
+            break;
+        default:
+            return fail(LB_EINVAL, "unknown init kind");
+    }
+    // the state is written into pop[0]; pop[1] stages host fields
+    c->cur = 0;
+    c->hcur = 0;
+    if (kind == LB_INIT_FIELDS) {
+        if (fields_on_device) {
+            fr = rho_r; fb = rho_b; fu = u;
+        } else {
+            float *stage = c->pop[1];
+            const size_t nb = (size_t)c->nn * sizeof(float);
+            LB_CUDA(cudaMemcpyAsync(stage, rho_r, nb, cudaMemcpyHostToDevice, c->stream));
+            LB_CUDA(cudaMemcpyAsync(stage + c->nn, rho_b, nb, cudaMemcpyHostToDevice, c->stream));
+            LB_CUDA(cudaMemcpyAsync(stage + 2 * c->nn, u, 3 * nb, cudaMemcpyHostToDevice, c->stream));
+            fr = stage; fb = stage + c->nn; fu = stage + 2 * c->nn;
+        }
+    }
+    const double alpha_b = 8.0 / 27.0;
+    const double alpha_r = 1.0 - (1.0 - alpha_b) / (c->p.rho_r0 / c->p.rho_b0);
+    init_kernel<<<grid_for(c->nn, 256), 256, 0, c->stream>>>(
+        c->pop[0], c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz, a[0], a[1], a[2], a[3], a[4],
+        (float)c->p.rho_r0, (float)c->p.rho_b0, (float)alpha_r, (float)alpha_b);
+    c->launches += 1;
+    LB_CUDA(cudaGetLastError());
+    if (kind == LB_INIT_FIELDS && !fields_on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
+    c->step = 0;
+    c->initialized = true;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx *c, int64_t n) {
+    if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
+    if (n < 0) return fail(LB_EINVAL, "n must be >= 0");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_step before lb_init/lb_load");
+    for (int64_t s = 0; s < n; ++s) {
+        StepArgs a = make_args(c);
+        cudaEvent_t *ev = nullptr;
+        if (c->prof_used < c->prof_cap) ev = &c->prof_ev[4 * (size_t)c->prof_used++];
+        cudaError_t e = launch_step(a, c->stream, ev, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_step");
+        c->cur ^= 1;
+        if (c->g.bc_zhi == LB_BC_CONVECTIVE) c->hcur ^= 1;
+        c->step += 1;
+        if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
+            double m[2];
+            lb_status st = run_mass(c, c->pop[c->cur], m);
+            if (st != LB_OK) return st;
+            if (!std::isfinite(m[0]) || !std::isfinite(m[1]))
+                return fail(LB_EUNSTABLE, "non-finite colour mass at step " + std::to_string(c->step));
+        }
+    }
+    return LB_OK;
+}
+
+int64_t lb_step_count(const lb_ctx *c) { return c ? c->step : -1; }
+
+lb_status lb_fields(lb_ctx *c, uint32_t mask, float *const *outs, int32_t on_device) {
+    if (!c || !outs) return fail(LB_EINVAL, "ctx and outs must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_fields before lb_init/lb_load");
+    if (mask >> LB_NFIELDS) return fail(LB_EINVAL, "unknown field bit in mask");
+    float *dst[LB_NFIELDS] = {};
+    float *stage = c->pop[c->cur ^ 1];
+    for (int j = 0; j < LB_NFIELDS; ++j) {
+        if (!(mask & (1u << j))) continue;
+        if (!outs[j]) return fail(LB_EINVAL, "outs[" + std::to_string(j) + "] is NULL but selected");
+        dst[j] = on_device ? outs[j] : stage + (long long)j * c->nn;
+    }
+    const double alpha_b = 8.0 / 27.0;
+    const double alpha_r = 1.0 - (1.0 - alpha_b) / (c->p.rho_r0 / c->p.rho_b0);
+    fields_kernel<<<grid_for(c->nn, 256), 256, 0, c->stream>>>(
+        c->pop[c->cur], dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], c->nn,
+        (float)(1.0 / c->p.rho_r0), (float)(1.0 / c->p.rho_b0), (float)c->p.rho_b0, (float)c->p.g[0],
+        (float)c->p.g[1], (float)c->p.g[2], (float)alpha_r, (float)alpha_b);
+    c->launches += 1;
+    LB_CUDA(cudaGetLastError());
+    if (!on_device) {
+        for (int j = 0; j < LB_NFIELDS; ++j)
+            if (dst[j]) LB_CUDA(cudaMemcpyAsync(outs[j], dst[j], c->nn * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        LB_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return LB_OK;
+}
+
+lb_status lb_populations(lb_ctx *c, float *out, int32_t on_device) {
+    if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_populations before lb_init/lb_load");
+    LB_CUDA(cudaMemcpyAsync(out, c->pop[c->cur], (size_t)54 * c->nn * sizeof(float),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_history(lb_ctx *c, float *out, int32_t on_device) {
+    if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_history before lb_init/lb_load");
+    LB_CUDA(cudaMemcpyAsync(out, c->hist[c->hcur], (size_t)54 * c->plane * sizeof(float),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_mass(lb_ctx *c, double out[2]) {
+    if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_mass before lb_init/lb_load");
+    return run_mass(c, c->pop[c->cur], out);
+}
+
+struct SaveHeader {
+    uint64_t magic;
+    int32_t nx, ny, nz, storage;
+    int64_t step;
+    uint64_t pop_bytes, hist_bytes;
+};
+
+lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
+    if (!c || !nbytes) return fail(LB_EINVAL, "ctx and nbytes must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_save before lb_init/lb_load");
+    const size_t pb = (size_t)54 * c->nn * sizeof(float), hb = (size_t)54 * c->plane * sizeof(float);
+    const size_t total = sizeof(SaveHeader) + pb + hb;
+    if (!buf) {
+        *nbytes = total;
+        return LB_OK;
+    }
+    if (*nbytes < total) return fail(LB_EINVAL, "checkpoint buffer too small");
+    SaveHeader h{kMagic, c->g.nx, c->g.ny, c->g.nz, c->p.storage, c->step, pb, hb};
+    std::memcpy(buf, &h, sizeof(h));
+    char *p = (char *)buf + sizeof(h);
+    LB_CUDA(cudaMemcpyAsync(p, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaMemcpyAsync(p + pb, c->hist[c->hcur], hb, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    *nbytes = total;
+    return LB_OK;
+}
+
+lb_status lb_load(lb_ctx *c, const void *buf, size_t nbytes) {
+    if (!c || !buf) return fail(LB_EINVAL, "ctx and buf must not be NULL");
+    if (nbytes < sizeof(SaveHeader)) return fail(LB_EINVAL, "checkpoint too small");
+    SaveHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const size_t pb = (size_t)54 * c->nn * sizeof(float), hb = (size_t)54 * c->plane * sizeof(float);
+    if (h.magic != kMagic || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.storage != c->p.storage ||
+        h.pop_bytes != pb || h.hist_bytes != hb || nbytes < sizeof(h) + pb + hb)
+        return fail(LB_EINVAL, "checkpoint does not match this context (grid, storage or size)");
+    const char *p = (const char *)buf + sizeof(h);
+    c->cur = 0;
+    c->hcur = 0;
+    LB_CUDA(cudaMemcpyAsync(c->pop[0], p, pb, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaMemcpyAsync(c->hist[0], p + pb, hb, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    c->step = h.step;
+    c->initialized = true;
+    return LB_OK;
+}
+
+lb_status lb_profile_enable(lb_ctx *c, int32_t capacity) {
+    if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
+    if (capacity < 0) return fail(LB_EINVAL, "capacity must be >= 0");
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    free_profile(c);
+    c->prof_ev.resize(4 * (size_t)capacity);
+    for (auto &e : c->prof_ev) LB_CUDA(cudaEventCreate(&e));
+    c->prof_cap = capacity;
+    return LB_OK;
+}
+
+lb_status lb_profile_read(lb_ctx *c, double *ms, int64_t *launches, int32_t n_kinds) {
+    if (!c || !ms || !launches) return fail(LB_EINVAL, "ctx, ms and launches must not be NULL");
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    double acc[LB_NKERNELS] = {0, 0, 0};
+    int64_t cnt[LB_NKERNELS] = {0, 0, 0};
+    const bool planes = c->g.bc_zlo != LB_BC_PERIODIC || c->g.bc_zhi != LB_BC_PERIODIC;
+    for (int s = 0; s < c->prof_used; ++s) {
+        cudaEvent_t *ev = &c->prof_ev[4 * (size_t)s];
+        float t;
+        for (int k = 0; k < LB_NKERNELS; ++k) {
+            if (k == LB_KERNEL_BOUNDARY && !planes) continue;
+            LB_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            acc[k] += t;
+            cnt[k] += 1;
+        }
+    }
+    for (int k = 0; k < n_kinds && k < LB_NKERNELS; ++k) {
+        ms[k] = acc[k];
+        launches[k] = cnt[k];
+    }
+    c->prof_used = 0;
+    return LB_OK;
+}
+
+int64_t lb_kernel_launches(const lb_ctx *c) { return c ? c->launches : -1; }
+
+lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_args, double *grad_out,
+                     int32_t n_grad) {
+    (void)c; (void)objective; (void)T; (void)obj_args; (void)grad_out; (void)n_grad;
+    return fail(LB_ENOTIMPL, "lb_adjoint is not provided by this build");
+}
+
+}  // extern "C"

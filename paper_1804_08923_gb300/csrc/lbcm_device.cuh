@@ -1,0 +1,110 @@
+// lbcm_device.cuh -- D3Q27 lattice constants and per-node device math of the
+// colour-gradient central-moment LB step (arXiv:1804.08923, Section II), FP32.
+//
+// Everything here is compile-time unrolled over the 27 directions so that direction
+// indices fold into immediates and the 27-vectors live in registers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbcm {
+
+// Velocity set of Eq. (velVec): c+1 packed two bits per direction.
+constexpr unsigned long long kPackX = 0x20888895489549ull;
+constexpr unsigned long long kPackY = 0x0a089548a09495ull;
+constexpr unsigned long long kPackZ = 0x08a0a0a0954955ull;
+
+__host__ __device__ constexpr int cx(int i) { return (int)((kPackX >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cy(int i) { return (int)((kPackY >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cz(int i) { return (int)((kPackZ >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int csq(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+// position of direction i in the 3x3x3 tensor-product array [cx+1][cy+1][cz+1]
+__host__ __device__ constexpr int cell(int i) { return (cx(i) + 1) * 9 + (cy(i) + 1) * 3 + (cz(i) + 1); }
+// direction with c_z flipped (specular reflection on a z wall)
+__host__ __device__ constexpr int mirror_z(int i) {
+    int r = 0;
+    for (int j = 0; j < 27; ++j)
+        if (cx(j) == cx(i) && cy(j) == cy(i) && cz(j) == -cz(i)) r = j;
+    return r;
+}
+// rank of direction i among those with the same c_z = +1 (or -1), 0..8
+__host__ __device__ constexpr int zrank(int i) {
+    int r = 0;
+    for (int j = 0; j < i; ++j)
+        if (cz(j) == cz(i)) ++r;
+    return r;
+}
+
+// D3Q27 weights
+__host__ __device__ constexpr float wgt(int i) {
+    return csq(i) == 0 ? 8.0f / 27.0f : csq(i) == 1 ? 2.0f / 27.0f : csq(i) == 2 ? 1.0f / 54.0f : 1.0f / 216.0f;
+}
+// Eq. (B_i)
+__host__ __device__ constexpr float bcoef(int i) {
+    return csq(i) == 0 ? -10.0f / 27.0f : wgt(i);
+}
+// Eq. (varphi_ik): varphi_i(alpha) = alpha (rest) or k_q (1 - alpha)
+__host__ __device__ constexpr float varphi_k(int i) {
+    return csq(i) == 1 ? 2.0f / 19.0f : csq(i) == 2 ? 1.0f / 38.0f : 1.0f / 152.0f;
+}
+__device__ __forceinline__ float varphi(int i, float alpha, float one_m_alpha) {
+    return csq(i) == 0 ? alpha : varphi_k(i) * one_m_alpha;
+}
+// Eq. (Phi): coefficient of nu (G : c c) by speed class, G : c c = (c.u)(c.grad rho)/24
+__host__ __device__ constexpr float phi_corr(int i) {
+    return csq(i) == 1 ? 16.0f / 24.0f : csq(i) == 2 ? 4.0f / 24.0f : 1.0f / 24.0f;
+}
+// 1/|c_i| for the recolouring angle (0 for the rest direction)
+__host__ __device__ constexpr float inv_cnorm(int i) {
+    return csq(i) == 0 ? 0.0f : csq(i) == 1 ? 1.0f : csq(i) == 2 ? 0.70710678118654752f : 0.57735026918962576f;
+}
+
+// Polynomial part of Eq. (EES): 3 cu + 9/2 cu^2 - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2
+__device__ __forceinline__ float eq_poly(float cu, float usq) {
+    float t = fmaf(4.5f, cu, 3.0f);            // 3 + 4.5 cu
+    t = fmaf(4.5f * cu, cu, t) - 4.5f * usq;  // 3 + 4.5cu + 4.5cu^2 - 4.5u^2
+    return fmaf(cu, t, -1.5f * usq);          // cu * (...) - 1.5 u^2
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): gamma increment and finaliser.
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long s) {
+    unsigned long long z = s + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// Inlet noise xi in [-1, 1) for (seed, step, x, y): top 24 bits of a double hash, exact.
+__host__ __device__ __forceinline__ float inlet_xi(unsigned long long seed, long long step, int x, int y, int nx, int ny) {
+    unsigned long long idx = ((unsigned long long)step * (unsigned long long)ny + (unsigned long long)y) *
+                                 (unsigned long long)nx + (unsigned long long)x;
+    unsigned long long h = splitmix64(seed ^ splitmix64(idx));
+    return (float)(unsigned int)(h >> 40) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+enum { BC_PERIODIC = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_CONVECTIVE = 3 };
+
+// Everything a step kernel needs, passed by value.
+struct StepArgs {
+    const float *__restrict__ pin;   // S(t): [2][27][NN]
+    float *__restrict__ pout;        // S(t+1)
+    float *__restrict__ rho;         // post-stream rho_r, rho_b: [2][NN]
+    const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
+    float *__restrict__ hist_out;       // outflow plane f(N, t+1)
+    float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]
+    float *__restrict__ zout;           // incoming z=N populations (c_z = -1) on a free-slip top
+    const uint8_t *__restrict__ disc;   // inlet disc membership [ny][nx]
+    long long NN, plane;                // nodes, nx*ny
+    int nx, ny, nz, bc_zlo, bc_zhi;
+    float rho_r0, rho_b0, inv_rho_r0, inv_rho_b0;
+    float alpha_r, alpha_b, inv_nu_r, inv_nu_b;
+    float sigma, beta, eps2;
+    float gx, gy, gz;
+    float s0, s1, s2b, s3, s4, s5, s6;
+    float u_in, noise_amp, xc, yc;
+    unsigned long long seed;
+    long long step;  // index of the step being taken (state t -> t+1 uses t)
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+}  // namespace lbcm

@@ -1,0 +1,389 @@
+// lbcm_step.cu -- the per-time-step kernels of the colour-gradient central-moment LB
+// method (arXiv:1804.08923), FP32 populations and arithmetic, sm_103a.
+//
+// One step (state S(t) -> S(t+1)) is three launches on the context's stream:
+//   1. boundary_plane_kernel  incoming z = 0 populations (inlet disc / free-slip mirror),
+//                             free-slip top, and the convective outflow plane
+//                             f(N, t+1) = [f(N, t) + lambda f(N-1, t+1)] / (1 + lambda)
+//                             (Section IV.A).  One thread per (x, y).
+//   2. phase_field_kernel     pull-gathers the 54 post-stream populations of a node and
+//                             writes rho_r, rho_b (Section II, densities).  One thread
+//                             per node.
+//   3. collide_kernel         pull-gathers again, takes the isotropic gradients of phi and
+//                             rho from the densities of step 2 (end of Section II), and
+//                             applies the central-moment collision with the enhanced
+//                             equilibrium and GMRT forcing (Eqs. scoll, EES, Phi, ketF,
+//                             ketFd), the perturbation (Eq. perturb) and the recolouring
+//                             (Eqs. op3r, op3b); writes the 54 post-collision populations
+//                             of the node (pull scheme: streaming happens in the next
+//                             step's gathers).
+//
+// The collision applies T^-1 K T through the tensor-product central moments
+//   kappa_abc = sum_i f_i (c_ix - u_x)^a (c_iy - u_y)^b (c_iz - u_z)^c,  a, b, c in {0,1,2},
+// computed by three 1-D shifted sweeps and undone by three reverse sweeps.  The 27 rows
+// of the paper's moment set (Eq. momentSet) are, order by order, invertible combinations
+// of these; K holds one rate per order except order 2, where the trace relaxes with s_2b
+// and the deviatoric part with s_2nu.  Relaxing kappa with those rates is therefore the
+// same linear map as T^-1 K T (exact up to rounding).  The forcing is folded in:
+//   f* = f^e + F'/2 + T^-1 (I - K) T (f - f^e + F'/2)
+// which equals f - T^-1 K T (f - f^e) + T^-1 (I - K/2) T F' (Eqs. scoll and ketF).
+#include "lbcm_device.cuh"
+#include "lbcm_internal.h"
+
+namespace lbcm {
+
+// ------------------------------------------------------------------ boundary planes
+__global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    const long long P = a.plane, pxy = (long long)y * a.nx + x, NN = a.NN;
+    const int N = a.nz - 1;
+
+    if (a.bc_zlo == BC_INLET || a.bc_zlo == BC_FREESLIP) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            if (cz(i) != 1) continue;
+            const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
+            float vr, vb;
+            if (a.bc_zlo == BC_INLET && a.disc[(long long)ys * a.nx + xs]) {
+                // red equilibrium f^e(rho_r0, u_in) with alpha_r and Phi = 0, no blue
+                const float rx = (float)xs - a.xc, ry = (float)ys - a.yc;
+                const float r = sqrtf(rx * rx + ry * ry);
+                const float amp = a.noise_amp * a.u_in * inlet_xi(a.seed, a.step, xs, ys, a.nx, a.ny);
+                const float ux = r > 0.0f ? amp * rx / r : 0.0f;
+                const float uy = r > 0.0f ? amp * ry / r : 0.0f;
+                const float uz = a.u_in;
+                const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+                const float usq = ux * ux + uy * uy + uz * uz;
+                vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
+                vb = 0.0f;
+            } else {  // half-way specular reflection at z = -1/2
+                const long long src = (long long)ys * a.nx + xs;
+                vr = __ldg(a.pin + (long long)mirror_z(i) * NN + src);
+                vb = __ldg(a.pin + (long long)(27 + mirror_z(i)) * NN + src);
+            }
+            a.zin[(long long)zrank(i) * P + pxy] = vr;
+            a.zin[(long long)(9 + zrank(i)) * P + pxy] = vb;
+        }
+    }
+    if (a.bc_zhi == BC_FREESLIP) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            if (cz(i) != -1) continue;
+            const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
+            const long long src = ((long long)N * a.ny + ys) * a.nx + xs;
+            a.zout[(long long)zrank(i) * P + pxy] = __ldg(a.pin + (long long)mirror_z(i) * NN + src);
+            a.zout[(long long)(9 + zrank(i)) * P + pxy] = __ldg(a.pin + (long long)(27 + mirror_z(i)) * NN + src);
+        }
+    }
+    if (a.bc_zhi == BC_CONVECTIVE) {
+        // post-stream populations of node (x, y, N-1) at t+1 (N-1 >= 1: plain pulls)
+        const int z = N - 1;
+        float fr[27], fb[27];
+        float rho = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny), zs = z - cz(i);
+            const long long src = ((long long)zs * a.ny + ys) * a.nx + xs;
+            fr[i] = __ldg(a.pin + (long long)i * NN + src);
+            fb[i] = __ldg(a.pin + (long long)(27 + i) * NN + src);
+        }
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const float s = fr[i] + fb[i];
+            rho += s;
+            if (cz(i) != 0) jz += (float)cz(i) * s;
+        }
+        const float Fz = (rho - a.rho_b0) * a.gz;
+        float lam = (jz + 0.5f * Fz) / rho;  // u_z(x, y, N-1, t+1), Eq. (Momentum)
+        lam = fminf(fmaxf(lam, 0.0f), 1.0f);
+        const float inv = 1.0f / (1.0f + lam);
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const long long hr = (long long)i * P + pxy, hb = (long long)(27 + i) * P + pxy;
+            a.hist_out[hr] = (__ldg(a.hist_in + hr) + lam * fr[i]) * inv;
+            a.hist_out[hb] = (__ldg(a.hist_in + hb) + lam * fb[i]) * inv;
+        }
+    }
+}
+
+// Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
+// planes of this step substituted.  Branches are uniform across a warp (one z per warp).
+__device__ __forceinline__ void gather(const StepArgs &a, int x, int y, int z, float (&fr)[27], float (&fb)[27]) {
+    const long long NN = a.NN, P = a.plane, pxy = (long long)y * a.nx + x;
+    const int N = a.nz - 1;
+    const bool periodic_z = a.bc_zlo == BC_PERIODIC;
+    const bool lo = (z == 0) && !periodic_z;
+    const bool conv = (z == N) && a.bc_zhi == BC_CONVECTIVE;
+    const bool slip_hi = (z == N) && a.bc_zhi == BC_FREESLIP;
+    // row offsets for the three source planes / rows / columns
+    long long zo[3], yo[3];
+    int xo[3];
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        int zs = z - d;
+        if (periodic_z) zs = wrapi(zs, a.nz);
+        zs = min(max(zs, 0), N);  // out-of-range planes are never read (substituted below)
+        zo[d + 1] = (long long)zs * a.ny * a.nx;
+        yo[d + 1] = (long long)wrapi(y - d, a.ny) * a.nx;
+        xo[d + 1] = wrapi(x - d, a.nx);
+    }
+    if (conv) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            fr[i] = a.hist_out[(long long)i * P + pxy];
+            fb[i] = a.hist_out[(long long)(27 + i) * P + pxy];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        if (cz(i) == 1 && lo) {
+            fr[i] = a.zin[(long long)zrank(i) * P + pxy];
+            fb[i] = a.zin[(long long)(9 + zrank(i)) * P + pxy];
+        } else if (cz(i) == -1 && slip_hi) {
+            fr[i] = a.zout[(long long)zrank(i) * P + pxy];
+            fb[i] = a.zout[(long long)(9 + zrank(i)) * P + pxy];
+        } else {
+            const long long src = zo[cz(i) + 1] + yo[cy(i) + 1] + xo[cx(i) + 1];
+            fr[i] = __ldg(a.pin + (long long)i * NN + src);
+            fb[i] = __ldg(a.pin + (long long)(27 + i) * NN + src);
+        }
+    }
+}
+
+// --------------------------------------------------------------- phase field (K_A)
+__global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    float fr[27], fb[27];
+    gather(a, x, y, z, fr, fb);
+    float rr = 0.0f, rb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        rr += fr[i];
+        rb += fb[i];
+    }
+    const long long n = ((long long)z * a.ny + y) * a.nx + x;
+    a.rho[n] = rr;
+    a.rho[a.NN + n] = rb;
+}
+
+// 1-D shifted moment sweep: values at c = -1, 0, +1 -> central moments of order 0, 1, 2
+// about u:  m0 = sum v, m1 = sum v (c - u), m2 = sum v (c - u)^2.
+__device__ __forceinline__ void sweep_fwd(float &a0, float &a1, float &a2, float u) {
+    const float r0 = a0 + a1 + a2, r1 = a2 - a0, r2 = a2 + a0;
+    a0 = r0;
+    a1 = fmaf(-u, r0, r1);
+    a2 = fmaf(u, fmaf(u, r0, -2.0f * r1), r2);
+}
+// Inverse of sweep_fwd: raw moments r1 = m1 + u m0, r2 = m2 + 2u m1 + u^2 m0, then
+// v0 = r0 - r2, v+ = (r2 + r1)/2, v- = (r2 - r1)/2.
+__device__ __forceinline__ void sweep_inv(float &a0, float &a1, float &a2, float u) {
+    const float r0 = a0;
+    const float r1 = fmaf(u, a0, a1);
+    const float r2 = fmaf(u, fmaf(u, a0, 2.0f * a1), a2);
+    a1 = r0 - r2;
+    a0 = 0.5f * (r2 - r1);
+    a2 = 0.5f * (r2 + r1);
+}
+
+// ---------------------------------------------- collide, perturb, recolour (K_B)
+__global__ void __launch_bounds__(128) collide_kernel(StepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const long long NN = a.NN;
+    const int N = a.nz - 1;
+
+    // post-stream populations, colour-blind sum and densities (same order as K_A)
+    float f[27];
+    float rho_r = 0.0f, rho_b = 0.0f;
+    {
+        float fr[27], fb[27];
+        gather(a, x, y, z, fr, fb);
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            rho_r += fr[i];
+            rho_b += fb[i];
+            f[i] = fr[i] + fb[i];
+        }
+    }
+
+    // isotropic gradients of phi and rho: grad chi = 3 sum_j w_j chi(x + c_j) c_j, summed
+    // over the 13 pairs of opposite directions (j, j+1) as 3 w_j c_j (chi(x + c_j) -
+    // chi(x - c_j)): a uniform field gives exactly zero, and nearby values subtract exactly.
+    float gpx = 0.0f, gpy = 0.0f, gpz = 0.0f, grx = 0.0f, gry = 0.0f, grz = 0.0f;
+    {
+        const bool periodic_z = a.bc_zlo == BC_PERIODIC;
+        float ph[27], rh[27];
+#pragma unroll
+        for (int j = 1; j < 27; ++j) {
+            const int xn = wrapi(x + cx(j), a.nx), yn = wrapi(y + cy(j), a.ny);
+            int zn = z + cz(j);
+            float ra, rb;
+            bool ghost_in = false;
+            if (periodic_z) {
+                zn = wrapi(zn, a.nz);
+            } else if (zn < 0) {
+                zn = 0;  // mirror of z = 0 (free slip), or the inlet value inside the disc
+                ghost_in = a.bc_zlo == BC_INLET && a.disc[(long long)yn * a.nx + xn];
+            } else if (zn > N) {
+                zn = N;  // mirror of z = N
+            }
+            if (ghost_in) {
+                ra = a.rho_r0;
+                rb = 0.0f;
+            } else {
+                const long long m = ((long long)zn * a.ny + yn) * a.nx + xn;
+                ra = __ldg(a.rho + m);
+                rb = __ldg(a.rho + NN + m);
+            }
+            const float A = ra * a.inv_rho_r0, B = rb * a.inv_rho_b0;
+            ph[j] = (A - B) / (A + B);
+            rh[j] = ra + rb;
+        }
+#pragma unroll
+        for (int j = 1; j < 27; j += 2) {  // c_{j+1} = -c_j
+            const float w3 = 3.0f * wgt(j);
+            const float dp = ph[j] - ph[j + 1], dr = rh[j] - rh[j + 1];
+            if (cx(j) != 0) { gpx = fmaf(w3 * cx(j), dp, gpx); grx = fmaf(w3 * cx(j), dr, grx); }
+            if (cy(j) != 0) { gpy = fmaf(w3 * cy(j), dp, gpy); gry = fmaf(w3 * cy(j), dr, gry); }
+            if (cz(j) != 0) { gpz = fmaf(w3 * cz(j), dp, gpz); grz = fmaf(w3 * cz(j), dr, grz); }
+        }
+    }
+
+    // macroscopic velocity with the Guo half-force (Eq. Momentum), body force Eq. (bodyForceJet)
+    const float rho = rho_r + rho_b;
+    const float inv_rho = 1.0f / rho;
+    const float Fx = (rho - a.rho_b0) * a.gx, Fy = (rho - a.rho_b0) * a.gy, Fz = (rho - a.rho_b0) * a.gz;
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        if (cx(i) != 0) jx += (float)cx(i) * f[i];
+        if (cy(i) != 0) jy += (float)cy(i) * f[i];
+        if (cz(i) != 0) jz += (float)cz(i) * f[i];
+    }
+    const float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
+
+    // order parameter (Eq. order) and mixture parameters
+    const float An = rho_r * a.inv_rho_r0, Bn = rho_b * a.inv_rho_b0;
+    const float phi = (An - Bn) / (An + Bn);
+    const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
+    const float alpha = hp * a.alpha_r + hm * a.alpha_b;
+    const float one_m_alpha = 1.0f - alpha;
+    const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);  // harmonic mean
+    const float tau = 3.0f * nu + 0.5f;                           // Eq. (shear): 1/s_2nu
+    const float s2nu = 1.0f / tau;
+    const float Acoef = 2.25f * a.sigma / tau;                     // Eq. (sigma): A = 9 sigma / (4 tau)
+
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float ugr = ux * grx + uy * gry + uz * grz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+
+    // Delta = f - f^e + F'/2, scattered into the tensor-product layout
+    float m[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+        const float cg = (float)cx(i) * grx + (float)cy(i) * gry + (float)cz(i) * grz;
+        const float cF = (float)cx(i) * Fx + (float)cy(i) * Fy + (float)cz(i) * Fz;
+        const float Phi = csq(i) == 0 ? -3.0f * nu * ugr : phi_corr(i) * nu * cu * cg;
+        const float fe = rho * fmaf(wgt(i), eq_poly(cu, usq), varphi(i, alpha, one_m_alpha)) + Phi;
+        const float Fp = wgt(i) * (3.0f * (cF - uF) + 9.0f * cu * cF);
+        m[cell(i)] = f[i] - fe + 0.5f * Fp;
+    }
+
+    // forward central-moment transform: z, then y, then x sweeps
+#pragma unroll
+    for (int p = 0; p < 9; ++p) sweep_fwd(m[p * 3 + 0], m[p * 3 + 1], m[p * 3 + 2], uz);
+#pragma unroll
+    for (int a0 = 0; a0 < 3; ++a0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sweep_fwd(m[a0 * 9 + 0 + c], m[a0 * 9 + 3 + c], m[a0 * 9 + 6 + c], uy);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sweep_fwd(m[q], m[9 + q], m[18 + q], ux);
+
+    // relaxation: kappa <- (I - K') kappa, K' = K in the tensor-product basis
+    {
+#define KAP(p, q, r) m[(p) * 9 + (q) * 3 + (r)]
+        const float o0 = 1.0f - a.s0, o1 = 1.0f - a.s1, o2 = 1.0f - s2nu, o2b = 1.0f - a.s2b;
+        const float o3 = 1.0f - a.s3, o4 = 1.0f - a.s4, o5 = 1.0f - a.s5, o6 = 1.0f - a.s6;
+        KAP(0, 0, 0) *= o0;
+        KAP(1, 0, 0) *= o1; KAP(0, 1, 0) *= o1; KAP(0, 0, 1) *= o1;
+        KAP(1, 1, 0) *= o2; KAP(1, 0, 1) *= o2; KAP(0, 1, 1) *= o2;
+        {
+            const float tr = KAP(2, 0, 0) + KAP(0, 2, 0) + KAP(0, 0, 2);
+            const float d1 = KAP(2, 0, 0) - KAP(0, 2, 0), d2 = KAP(2, 0, 0) - KAP(0, 0, 2);
+            const float t = o2b * tr, e1 = o2 * d1, e2 = o2 * d2;
+            const float third = 1.0f / 3.0f;
+            KAP(2, 0, 0) = (t + e1 + e2) * third;
+            KAP(0, 2, 0) = (t - 2.0f * e1 + e2) * third;
+            KAP(0, 0, 2) = (t + e1 - 2.0f * e2) * third;
+        }
+        KAP(2, 1, 0) *= o3; KAP(2, 0, 1) *= o3; KAP(1, 2, 0) *= o3; KAP(0, 2, 1) *= o3;
+        KAP(1, 0, 2) *= o3; KAP(0, 1, 2) *= o3; KAP(1, 1, 1) *= o3;
+        KAP(2, 2, 0) *= o4; KAP(2, 0, 2) *= o4; KAP(0, 2, 2) *= o4;
+        KAP(2, 1, 1) *= o4; KAP(1, 2, 1) *= o4; KAP(1, 1, 2) *= o4;
+        KAP(2, 2, 1) *= o5; KAP(2, 1, 2) *= o5; KAP(1, 2, 2) *= o5;
+        KAP(2, 2, 2) *= o6;
+#undef KAP
+    }
+
+    // inverse transform: x, then y, then z sweeps
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sweep_inv(m[q], m[9 + q], m[18 + q], ux);
+#pragma unroll
+    for (int a0 = 0; a0 < 3; ++a0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sweep_inv(m[a0 * 9 + 0 + c], m[a0 * 9 + 3 + c], m[a0 * 9 + 6 + c], uy);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) sweep_inv(m[p * 3 + 0], m[p * 3 + 1], m[p * 3 + 2], uz);
+
+    // perturbation (Eq. perturb, squared numerator, both colours) and recolouring
+    const float g2 = gpx * gpx + gpy * gpy + gpz * gpz;
+    const float inv_gm = 1.0f / sqrtf(g2 + a.eps2);  // 1/|grad phi|_eps
+    const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
+    const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;  // beta rho_r rho_b / (rho |g|)
+    const float pert = Acoef * inv_gm;
+    const long long n = ((long long)z * a.ny + y) * a.nx + x;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+        const float cg = (float)cx(i) * grx + (float)cy(i) * gry + (float)cz(i) * grz;
+        const float cF = (float)cx(i) * Fx + (float)cy(i) * Fy + (float)cz(i) * Fz;
+        const float Phi = csq(i) == 0 ? -3.0f * nu * ugr : phi_corr(i) * nu * cu * cg;
+        const float fe = rho * fmaf(wgt(i), eq_poly(cu, usq), varphi(i, alpha, one_m_alpha)) + Phi;
+        const float Fp = wgt(i) * (3.0f * (cF - uF) + 9.0f * cu * cF);
+        const float cgp = (float)cx(i) * gpx + (float)cy(i) * gpy + (float)cz(i) * gpz;
+        float fs = fe + 0.5f * Fp + m[cell(i)];
+        fs += pert * (wgt(i) * cgp * cgp - bcoef(i) * g2);
+        const float seg = csq(i) == 0 ? 0.0f : seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
+        a.pout[(long long)i * NN + n] = fmaf(frac_r, fs, seg);
+        a.pout[(long long)(27 + i) * NN + n] = fmaf(frac_b, fs, -seg);
+    }
+}
+
+// ------------------------------------------------------------------------ launchers
+cudaError_t launch_step(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
+    if (ev) cudaEventRecord(ev[0], s);
+    if (a.bc_zlo != BC_PERIODIC || a.bc_zhi != BC_PERIODIC) {
+        dim3 b(32, 8), g((a.nx + 31) / 32, (a.ny + 7) / 8);
+        boundary_plane_kernel<<<g, b, 0, s>>>(a);
+        *launches += 1;
+    }
+    dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
+    if (ev) cudaEventRecord(ev[1], s);
+    phase_field_kernel<<<grd, blk, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[2], s);
+    collide_kernel<<<grd, blk, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[3], s);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace lbcm

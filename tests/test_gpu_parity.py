@@ -1,0 +1,258 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Error norm: max over colours, directions and nodes of |f_gpu - f_oracle| / (w_i max(rho_r0,
+rho_b0)); the FP32 bar is 1e-5 after 50 steps on smooth cases.  Sizes span several
+32x4 thread blocks with ragged tails in x and y.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_08923_gb300.build as b
+    b.build()
+    import paper_1804_08923_gb300 as lbm
+    return lbm
+
+
+def full_params(p):
+    base = dict(workloads.CONFIGS["droplet32"]["params"])
+    base.update(p)
+    return base
+
+
+def pair(lb, shape, params, bc=(0, 0)):
+    nz, ny, nx = shape
+    gpu = lb.Lattice((nx, ny, nz), params, bc=bc)
+    ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *bc), oracle.make_params(full_params(params)))
+    return gpu, ref
+
+
+def norm_err(gpu, ref, params):
+    got = gpu.populations(device=False).astype(np.float64)
+    w = oracle.weights()[None, :, None, None, None]
+    scale = w * max(params["rho_r0"], params["rho_b0"])
+    return np.abs(got - ref.S) / scale
+
+
+def run_both(gpu, ref, steps):
+    gpu.step(steps)
+    ref.step(steps)
+
+
+def test_droplet_periodic_parity(lb):
+    """Static droplet (Section III physics, tau = 1) on 20^3, 50 steps."""
+    shape = (20, 20, 20)
+    params = dict(rho_r0=1.0, rho_b0=1.0, nu_r=1 / 6, nu_b=1 / 6, sigma=0.01)
+    gpu, ref = pair(lb, shape, params)
+    gpu.init_droplet(6.0, 4.0)
+    ref.init_droplet(6.0, 4.0)
+    run_both(gpu, ref, 50)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+@pytest.mark.parametrize("seed,gamma,g", [(1, 2.0, (0.0, 0.0, 1e-5)), (2, 8.0, (1e-6, -2e-6, 3e-6))])
+def test_random_two_phase_parity(lb, seed, gamma, g):
+    """Random smooth two-phase state with density and viscosity contrast and gravity,
+    ragged 40x9x12 lattice, 50 steps."""
+    shape = (12, 9, 40)
+    params = dict(rho_r0=1.0, rho_b0=1.0 / gamma, nu_r=0.02, nu_b=0.08, sigma=0.003, g=g)
+    gpu, ref = pair(lb, shape, params)
+    fields = workloads.random_two_phase_fields(shape, seed, 1.0, 1.0 / gamma, u_amp=0.03)
+    gpu.init_fields(*fields)
+    ref.init_fields(*fields)
+    run_both(gpu, ref, 50)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+def test_general_relaxation_rates_parity(lb):
+    """Every relaxation group with its own rate (s0, s1 and s2b..s6 away from the paper's
+    values) exercises each branch of the moment-space relaxation."""
+    shape = (8, 6, 10)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.03, nu_b=0.06, sigma=0.002, s0=0.3, s1=0.6,
+                  s2b=1.3, s3=0.9, s4=1.1, s5=1.4, s6=0.8, g=(0.0, 2e-5, 0.0))
+    gpu, ref = pair(lb, shape, params)
+    fields = workloads.random_two_phase_fields(shape, 5, 1.0, 0.5, u_amp=0.04)
+    gpu.init_fields(*fields)
+    ref.init_fields(*fields)
+    run_both(gpu, ref, 20)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+def test_small_jet_parity(lb):
+    """Jet with inlet disc, radial noise, free slip around the disc and convective
+    outflow (Section IV.A) on 36x34x40 with the 96x96x384 jet's lattice parameters
+    (tau -> 0.5012), 50 steps."""
+    cfg = workloads.scaled_jet("jet96", 36, 34, 40, D=10)
+    params = cfg["params"]
+    shape = (40, 34, 36)
+    gpu, ref = pair(lb, shape, params, bc=cfg["bc"])
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 50)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+    h = gpu.history().astype(np.float64)
+    assert np.abs(h - ref.hist).max() / max(params["rho_r0"], params["rho_b0"]) < TOL
+    assert gpu.fields(device=False)["rho_r"].sum() > 0.5  # red has entered
+
+
+def test_jet_with_gravity_parity(lb):
+    """High-Re jet parameters (tau -> 0.5000384) with gravity along +z, 40 steps."""
+    cfg = workloads.scaled_jet("jet256", 24, 24, 32, D=8)
+    params = dict(cfg["params"])
+    params["g"] = (0.0, 0.0, 1e-4)  # stronger than the jet's so the force terms matter
+    shape = (32, 24, 24)
+    gpu, ref = pair(lb, shape, params, bc=cfg["bc"])
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 40)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+def test_free_slip_box_parity(lb):
+    """Free-slip walls at both z ends around a random two-phase state, 30 steps."""
+    shape = (10, 8, 12)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.05, nu_b=0.05, sigma=0.004)
+    gpu, ref = pair(lb, shape, params, bc=(lb.BC_FREESLIP, lb.BC_FREESLIP))
+    fields = workloads.random_two_phase_fields(shape, 9, 1.0, 0.5)
+    gpu.init_fields(*fields)
+    ref.init_fields(*fields)
+    run_both(gpu, ref, 30)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+def test_degenerate_lattices_parity(lb):
+    """Degenerate extents: a 1x32x1 shear wave (every neighbour wraps onto itself in x and
+    z), a single node, and the smallest convective column (nz = 3)."""
+    params = dict(rho_r0=1.0, rho_b0=1.0, nu_r=0.05, nu_b=0.05, sigma=0.0)
+    gpu, ref = pair(lb, (1, 32, 1), params)
+    f = workloads.shear_wave_fields((1, 32, 1), 1e-3)
+    gpu.init_fields(*[a.astype(np.float32) for a in f])
+    ref.init_fields(*[a.astype(np.float32) for a in f])
+    run_both(gpu, ref, 50)
+    assert norm_err(gpu, ref, params).max() < TOL
+    gpu, ref = pair(lb, (1, 1, 1), params)
+    gpu.init_uniform(0.7, 0.3, (0.01, 0.02, -0.01))
+    ref.init_fields(np.full((1, 1, 1), 0.7, np.float32), np.full((1, 1, 1), 0.3, np.float32),
+                    np.array([0.01, 0.02, -0.01], np.float32).reshape(3, 1, 1, 1))
+    run_both(gpu, ref, 10)
+    assert norm_err(gpu, ref, params).max() < TOL
+    p2 = dict(params, u_in=0.05, d_in=3.0, rho_b0=0.5)
+    gpu, ref = pair(lb, (3, 5, 5), p2, bc=(lb.BC_INLET, lb.BC_CONVECTIVE))
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 20)
+    assert norm_err(gpu, ref, p2).max() < TOL
+
+
+def test_full_size_jet_sampled_one_step(lb):
+    """At the benchmark's 96x96x384 jet (same launch configuration), one GPU step from the
+    GPU's own state matches the oracle's step from that state at sampled nodes: inlet and
+    outflow planes, lattice edges, interface and bulk."""
+    cfg = workloads.CONFIGS["jet96"]
+    nx, ny, nz = cfg["grid"]
+    params = cfg["params"]
+    gpu = lb.Lattice((nx, ny, nz), params, bc=cfg["bc"])
+    gpu.init_jet()
+    gpu.step(60)
+    S = gpu.populations(device=False).astype(np.float64)
+    H = gpu.history().astype(np.float64)
+    n0 = gpu.step_count
+    gpu.step(1)
+    got = gpu.populations(device=False)
+    ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *cfg["bc"]), oracle.make_params(full_params(params)))
+    ref.set_state(S, H, n0)
+    rng = np.random.default_rng(3)
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    for z in (0, 1, 2, nz - 2, nz - 1):
+        mask[z, rng.integers(0, ny, 40), rng.integers(0, nx, 40)] = 1
+    mask[0, ny // 2 - 8:ny // 2 + 8, nx // 2 - 8:nx // 2 + 8] = 1  # inlet disc
+    mask[:, 0, 0] = mask[:, ny - 1, nx - 1] = 1
+    mask[rng.integers(0, nz, 500), rng.integers(0, ny, 500), rng.integers(0, nx, 500)] = 1
+    mask[1:6, ny // 2 - 10:ny // 2 + 10, nx // 2] = 1  # jet interface region
+    ref.step(1, mask=mask)
+    sel = mask.astype(bool)
+    w = oracle.weights()[None, :, None]
+    e = np.abs(got[:, :, sel].astype(np.float64) - ref.S[:, :, sel]) / (w * max(params["rho_r0"], params["rho_b0"]))
+    assert e.max() < TOL, e.max()
+    assert np.isfinite(got).all()
+
+
+def test_mass_conservation_and_reduction(lb):
+    """lb_mass equals an FP64 sum of the populations, and a periodic run conserves the
+    colour masses to FP32 round-off."""
+    shape = (24, 20, 36)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.05, sigma=0.003)
+    gpu = lb.Lattice((36, 20, 24), params)
+    gpu.init_fields(*workloads.random_two_phase_fields(shape, 4, 1.0, 0.5))
+    m0 = gpu.mass()
+    S = gpu.populations(device=False).astype(np.float64)
+    assert np.allclose(m0, [S[0].sum(), S[1].sum()], rtol=1e-12, atol=0)
+    gpu.step(200)
+    m1 = gpu.mass()
+    assert np.all(np.abs(m1 - m0) / m0 < 2e-6), (m0, m1)
+    m2 = gpu.mass()
+    assert np.array_equal(m1, m2)  # deterministic reduction order
+
+
+def test_save_load_roundtrip_is_bitwise(lb):
+    cfg = workloads.scaled_jet("jet96", 32, 32, 24, D=8)
+    gpu = lb.Lattice((32, 32, 24), cfg["params"], bc=cfg["bc"])
+    gpu.init_jet()
+    gpu.step(7)
+    blob = gpu.save()
+    gpu.step(5)
+    a = gpu.populations(device=False)
+    gpu.load(blob)
+    assert gpu.step_count == 7
+    gpu.step(5)
+    assert np.array_equal(gpu.populations(device=False), a)
+
+
+def test_unstable_state_is_reported(lb):
+    """Fault injection on the host: a checkpoint carrying a NaN population makes the next
+    periodic mass check return LB_EUNSTABLE."""
+    shape = (8, 8, 8)
+    params = dict(rho_r0=1.0, rho_b0=1.0, nu_r=0.1, nu_b=0.1, sigma=0.001, check_every=2)
+    gpu = lb.Lattice((8, 8, 8), params)
+    gpu.init_droplet(2.5, 2.0)
+    gpu.step(2)
+    blob = bytearray(gpu.save())
+    hdr = len(blob) - 54 * 512 * 4 - 54 * 64 * 4
+    np.frombuffer(blob, dtype=np.float32, count=1, offset=hdr + 4 * 100)[:]  # readable
+    view = np.frombuffer(blob, dtype=np.float32, offset=hdr, count=54 * 512)
+    view = view.copy()
+    view[1234] = np.nan
+    blob[hdr:hdr + view.nbytes] = view.tobytes()
+    gpu.load(bytes(blob))
+    with pytest.raises(lb.LBError) as ei:
+        gpu.step(2)
+    assert ei.value.status == 4
+
+
+def test_host_errors(lb):
+    g = lb.Lattice((4, 4, 4), dict(rho_r0=1.0, rho_b0=1.0))
+    with pytest.raises(lb.LBError) as ei:
+        g.step(1)
+    assert ei.value.status == 6  # LB_ESTATE before init
+    with pytest.raises(lb.LBError):
+        g.init_droplet(-1.0, 4.0)
+    import ctypes as C
+    assert lb.library().lb_adjoint(g._ctx, 0, 10, None, None, 0) == 7
