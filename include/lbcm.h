@@ -148,6 +148,32 @@ LB_API lb_status lb_history(lb_ctx *ctx, float *out, int32_t on_device);
  * non-finite population makes the corresponding sum non-finite.  Synchronises. */
 LB_API lb_status lb_mass(lb_ctx *ctx, double out[2]);
 
+/* Colour masses without any device allocation.  The paper has no counterpart; this is a
+ * service for callers that cannot call cudaMalloc: code that keeps its own population
+ * arrays under a fixed device-memory budget claimed at start-up (a coupled solver, a
+ * process whose memory belongs to another allocator such as PyTorch's) and must not make
+ * the driver allocate behind its back, and that has no lb_ctx (whose buffers hold the
+ * scratch lb_mass uses).
+ *
+ * pop: device pointer to populations [2][27][nodes] (FP32, the lb_populations layout) on
+ * the current device.  out: device pointer receiving out[0] red, out[1] blue (FP64, the
+ * same fixed-order two-stage reduction as lb_mass, with LB_MASS_NOALLOC_CHUNK nodes per
+ * first-stage block).  stream: cudaStream_t the work is ordered on; nothing synchronises.
+ * nodes must lie in [1, LB_MASS_NOALLOC_MAX_NODES]; larger inputs return LB_EINVAL.
+ *
+ * The scratch is one file-scope device array of LB_MASS_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until process exit.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current and caches
+ * it; make that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents; every slot a call reads is written by the same call
+ * first, so nothing needs clearing.  Calls whose work overlaps on the GPU (other streams
+ * or other host threads) race on the array and must be serialised by the caller. */
+#define LB_MASS_NOALLOC_CHUNK 65536
+#define LB_MASS_NOALLOC_MAX_BLOCKS 4096
+#define LB_MASS_NOALLOC_MAX_NODES ((int64_t)LB_MASS_NOALLOC_CHUNK * LB_MASS_NOALLOC_MAX_BLOCKS)
+#define LB_MASS_NOALLOC_SCRATCH_BYTES ((2 * LB_MASS_NOALLOC_MAX_BLOCKS + 2) * 8)
+LB_API lb_status lb_mass_noalloc(const float *pop, int64_t nodes, double *out, void *stream);
+
 /* Checkpoint: lb_save writes the state (header, populations, history, step counter) to
  * host memory.  Pass buf = NULL to query the size in *nbytes.  lb_load restores a state
  * saved from a context with the same grid and storage.  Both synchronise. */

@@ -17,7 +17,7 @@ STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_EUNS
 
 # every entry point declared in include/lbcm.h
 EXPORTS = ("lb_params_default", "lb_buffer_sizes", "lb_create", "lb_create_with_buffers", "lb_init", "lb_step",
-           "lb_step_count", "lb_fields", "lb_populations", "lb_history", "lb_mass", "lb_save", "lb_load",
+           "lb_step_count", "lb_fields", "lb_populations", "lb_history", "lb_mass", "lb_mass_noalloc", "lb_save", "lb_load",
            "lb_profile_enable", "lb_profile_read", "lb_kernel_launches", "lb_adjoint", "lb_last_error",
            "lb_destroy")
 KERNEL_NAMES = ("boundary_plane_kernel", "phase_field_kernel", "collide_kernel")
@@ -73,6 +73,7 @@ def library(path: str = LIB_PATH):
         L.lb_populations.argtypes = [vp, fp, C.c_int32]
         L.lb_history.argtypes = [vp, fp, C.c_int32]
         L.lb_mass.argtypes = [vp, dp]
+        L.lb_mass_noalloc.argtypes = [vp, C.c_int64, vp, vp]
         L.lb_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.lb_load.argtypes = [vp, C.c_char_p, C.c_size_t]
         L.lb_profile_enable.argtypes = [vp, C.c_int32]

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -237,11 +238,20 @@ __global__ void __launch_bounds__(1024) mass_final_kernel(const double *__restri
     }
 }
 
+// Scratch of lb_mass_noalloc: first-stage partials of both colours, then the two results.
+static __device__ __align__(256) double g_mass_noalloc_scratch[2 * LB_MASS_NOALLOC_MAX_BLOCKS + 2];
+
 }  // namespace lbcm
 
 namespace {
 
 using namespace lbcm;
+
+// Device address of g_mass_noalloc_scratch per device, looked up once with that device
+// current (in host code the array's name is only a host-side stand-in).
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};
 
 lb_status setup_ctx(lb_ctx *c) {
     const lb_grid &g = c->g;
@@ -554,6 +564,36 @@ lb_status lb_history(lb_ctx *c, float *out, int32_t on_device) {
     LB_CUDA(cudaMemcpyAsync(out, c->hist[c->hcur], (size_t)54 * c->plane * sizeof(float),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_mass_noalloc(const float *pop, int64_t nodes, double *out, void *stream) {
+    if (!pop || !out) return fail(LB_EINVAL, "pop and out must be device pointers, not NULL");
+    if (nodes < 1 || nodes > LB_MASS_NOALLOC_MAX_NODES)
+        return fail(LB_EINVAL, "lb_mass_noalloc: nodes must lie in [1, " + std::to_string(LB_MASS_NOALLOC_MAX_NODES) +
+                                   "] (static scratch of " + std::to_string(LB_MASS_NOALLOC_MAX_BLOCKS) +
+                                   " blocks per colour); got " + std::to_string(nodes));
+    int dev = 0;
+    LB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(LB_EINVAL, "lb_mass_noalloc: device index out of range");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_mass_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_mass_noalloc_scratch)");
+            g_noalloc_addr[dev] = (double *)p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    const int nblocks = (int)((nodes + LB_MASS_NOALLOC_CHUNK - 1) / LB_MASS_NOALLOC_CHUNK);
+    cudaStream_t s = (cudaStream_t)stream;
+    mass_partial_kernel<<<dim3(nblocks, 2), kMassThreads, 0, s>>>(pop, nodes, scratch);
+    mass_final_kernel<<<1, 1024, 0, s>>>(scratch, nblocks, scratch + 2 * LB_MASS_NOALLOC_MAX_BLOCKS);
+    LB_CUDA(cudaGetLastError());
+    LB_CUDA(cudaMemcpyAsync(out, scratch + 2 * LB_MASS_NOALLOC_MAX_BLOCKS, 2 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
     return LB_OK;
 }
 
