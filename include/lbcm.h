@@ -90,9 +90,9 @@ LB_API void lb_params_default(lb_params *p);
 typedef struct lb_ctx lb_ctx;
 
 /* Number and byte sizes of the device buffers a context needs (at most LB_MAX_BUFFERS).
- * Buffer 0 and 1: population ping-pong, 54 * nodes * 4 bytes each; 2: densities
- * rho_r, rho_b of the current step; 3: outflow history ping-pong; 4: small tables and
- * reduction partials.  Returns LB_EINVAL for invalid grids or parameters. */
+ * Buffer 0 and 1: population ping-pong, 54 * nodes * 4 bytes each; 2: order parameter
+ * and total density of the current step; 3: outflow history ping-pong; 4: small tables
+ * and reduction partials.  Returns LB_EINVAL for invalid grids or parameters. */
 #define LB_MAX_BUFFERS 8
 LB_API lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *sizes_out, int32_t *n_out);
 

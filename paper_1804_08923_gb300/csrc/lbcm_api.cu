@@ -104,7 +104,7 @@ struct lb_ctx {
     size_t sizes[LB_MAX_BUFFERS] = {};
     int nbufs = 0;
     float *pop[2] = {nullptr, nullptr};
-    float *rho = nullptr;
+    float *phase = nullptr;
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -261,7 +261,7 @@ lb_status setup_ctx(lb_ctx *c) {
     const size_t hist_bytes = (size_t)54 * c->plane * sizeof(float);
     c->pop[0] = (float *)c->bufs[0];
     c->pop[1] = (float *)c->bufs[1];
-    c->rho = (float *)c->bufs[2];
+    c->phase = (float *)c->bufs[2];
     c->hist[0] = (float *)c->bufs[3];
     c->hist[1] = (float *)((char *)c->bufs[3] + align_up(hist_bytes));
     const AuxLayout L = aux_layout(g);
@@ -294,7 +294,7 @@ StepArgs make_args(const lb_ctx *c) {
     StepArgs a{};
     a.pin = c->pop[c->cur];
     a.pout = c->pop[c->cur ^ 1];
-    a.rho = c->rho;
+    a.phase = c->phase;
     a.hist_in = c->hist[c->hcur];
     a.hist_out = c->hist[c->hcur ^ 1];
     a.zin = c->zin;

@@ -81,13 +81,19 @@ __host__ __device__ __forceinline__ float inlet_xi(unsigned long long seed, long
     return (float)(unsigned int)(h >> 40) * (1.0f / 8388608.0f) - 1.0f;
 }
 
+// Order parameter of Eq. (order) from the colour densities (1/rho_k0 given).
+__device__ __forceinline__ float order_parameter(float rho_r, float rho_b, float inv_rho_r0, float inv_rho_b0) {
+    const float A = rho_r * inv_rho_r0, B = rho_b * inv_rho_b0;
+    return (A - B) / (A + B);
+}
+
 enum { BC_PERIODIC = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_CONVECTIVE = 3 };
 
 // Everything a step kernel needs, passed by value.
 struct StepArgs {
     const float *__restrict__ pin;   // S(t): [2][27][NN]
     float *__restrict__ pout;        // S(t+1)
-    float *__restrict__ rho;         // post-stream rho_r, rho_b: [2][NN]
+    float *__restrict__ phase;       // post-stream phi (Eq. order) and rho = rho_r + rho_b: [2][NN]
     const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
     float *__restrict__ hist_out;       // outflow plane f(N, t+1)
     float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]

@@ -7,10 +7,10 @@
 //                             f(N, t+1) = [f(N, t) + lambda f(N-1, t+1)] / (1 + lambda)
 //                             (Section IV.A).  One thread per (x, y).
 //   2. phase_field_kernel     pull-gathers the 54 post-stream populations of a node and
-//                             writes rho_r, rho_b (Section II, densities).  One thread
-//                             per node.
+//                             writes its order parameter phi (Eq. order) and total density
+//                             rho (Section II, densities).  One thread per node.
 //   3. collide_kernel         pull-gathers again, takes the isotropic gradients of phi and
-//                             rho from the densities of step 2 (end of Section II), and
+//                             rho from the fields of step 2 (end of Section II), and
 //                             applies the central-moment collision with the enhanced
 //                             equilibrium and GMRT forcing (Eqs. scoll, EES, Phi, ketF,
 //                             ketFd), the perturbation (Eq. perturb) and the recolouring
@@ -27,6 +27,15 @@
 // same linear map as T^-1 K T (exact up to rounding).  The forcing is folded in:
 //   f* = f^e + F'/2 + T^-1 (I - K) T (f - f^e + F'/2)
 // which equals f - T^-1 K T (f - f^e) + T^-1 (I - K/2) T F' (Eqs. scoll and ketF).
+//
+// With the paper's rates s3 = s4 = s5 = s6 = 1 (Section II, below Eq. bulk), (I - K) removes
+// every central moment of order three and above, so f* depends on f only through its
+// moments of order <= 2: mass, momentum and the raw second moment Pi(f).  Those of f^e and
+// F' have closed forms (Pi(f^e) = rho c_s^2 I + rho u u + nu (u g + g u + (u.g) I) with
+// c_s^2 = 9(1 - alpha)/19 and g = grad rho; Pi(F') = u F + F u), so collide_kernel needs no
+// per-direction Delta and no forward transform; it inverts the ten surviving central
+// moments with the same 1-D sweeps.  collide_general_kernel keeps the full 27-moment path
+// for any other rates.
 #include "lbcm_device.cuh"
 #include "lbcm_internal.h"
 
@@ -168,8 +177,51 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
         rb += fb[i];
     }
     const long long n = ((long long)z * a.ny + y) * a.nx + x;
-    a.rho[n] = rr;
-    a.rho[a.NN + n] = rb;
+    a.phase[n] = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
+    a.phase[a.NN + n] = rr + rb;
+}
+
+// Isotropic gradients of phi and rho (end of Section II): grad chi = 3 sum_j w_j chi(x + c_j)
+// c_j, summed over the 13 pairs of opposite directions (j, j+1) as 3 w_j c_j (chi(x + c_j) -
+// chi(x - c_j)), so that a uniform field gives exactly zero and nearby values subtract
+// exactly.  Ghosts: z = -1 is phi = 1, rho = rho_r0 inside the inlet disc and the mirror of
+// z = 0 elsewhere; z = N + 1 mirrors z = N.
+__device__ __forceinline__ void stencil_gradients(const StepArgs &a, int x, int y, int z, float &gpx, float &gpy,
+                                                  float &gpz, float &grx, float &gry, float &grz) {
+    const bool periodic_z = a.bc_zlo == BC_PERIODIC;
+    const int N = a.nz - 1;
+    float ph[27], rh[27];
+#pragma unroll
+    for (int j = 1; j < 27; ++j) {
+        const int xn = wrapi(x + cx(j), a.nx), yn = wrapi(y + cy(j), a.ny);
+        int zn = z + cz(j);
+        bool ghost_in = false;
+        if (periodic_z) {
+            zn = wrapi(zn, a.nz);
+        } else if (zn < 0) {
+            zn = 0;
+            ghost_in = a.bc_zlo == BC_INLET && a.disc[(long long)yn * a.nx + xn];
+        } else if (zn > N) {
+            zn = N;
+        }
+        if (ghost_in) {
+            ph[j] = 1.0f;
+            rh[j] = a.rho_r0;
+        } else {
+            const long long m = ((long long)zn * a.ny + yn) * a.nx + xn;
+            ph[j] = __ldg(a.phase + m);
+            rh[j] = __ldg(a.phase + a.NN + m);
+        }
+    }
+    gpx = gpy = gpz = grx = gry = grz = 0.0f;
+#pragma unroll
+    for (int j = 1; j < 27; j += 2) {  // c_{j+1} = -c_j
+        const float w3 = 3.0f * wgt(j);
+        const float dp = ph[j] - ph[j + 1], dr = rh[j] - rh[j + 1];
+        if (cx(j) != 0) { gpx = fmaf(w3 * cx(j), dp, gpx); grx = fmaf(w3 * cx(j), dr, grx); }
+        if (cy(j) != 0) { gpy = fmaf(w3 * cy(j), dp, gpy); gry = fmaf(w3 * cy(j), dr, gry); }
+        if (cz(j) != 0) { gpz = fmaf(w3 * cz(j), dp, gpz); grz = fmaf(w3 * cz(j), dr, grz); }
+    }
 }
 
 // 1-D shifted moment sweep: values at c = -1, 0, +1 -> central moments of order 0, 1, 2
@@ -191,8 +243,8 @@ __device__ __forceinline__ void sweep_inv(float &a0, float &a1, float &a2, float
     a2 = 0.5f * (r2 + r1);
 }
 
-// ---------------------------------------------- collide, perturb, recolour (K_B)
-__global__ void __launch_bounds__(128) collide_kernel(StepArgs a) {
+// ------------------------- collide, perturb, recolour (K_B), any relaxation rates
+__global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -214,48 +266,8 @@ __global__ void __launch_bounds__(128) collide_kernel(StepArgs a) {
         }
     }
 
-    // isotropic gradients of phi and rho: grad chi = 3 sum_j w_j chi(x + c_j) c_j, summed
-    // over the 13 pairs of opposite directions (j, j+1) as 3 w_j c_j (chi(x + c_j) -
-    // chi(x - c_j)): a uniform field gives exactly zero, and nearby values subtract exactly.
-    float gpx = 0.0f, gpy = 0.0f, gpz = 0.0f, grx = 0.0f, gry = 0.0f, grz = 0.0f;
-    {
-        const bool periodic_z = a.bc_zlo == BC_PERIODIC;
-        float ph[27], rh[27];
-#pragma unroll
-        for (int j = 1; j < 27; ++j) {
-            const int xn = wrapi(x + cx(j), a.nx), yn = wrapi(y + cy(j), a.ny);
-            int zn = z + cz(j);
-            float ra, rb;
-            bool ghost_in = false;
-            if (periodic_z) {
-                zn = wrapi(zn, a.nz);
-            } else if (zn < 0) {
-                zn = 0;  // mirror of z = 0 (free slip), or the inlet value inside the disc
-                ghost_in = a.bc_zlo == BC_INLET && a.disc[(long long)yn * a.nx + xn];
-            } else if (zn > N) {
-                zn = N;  // mirror of z = N
-            }
-            if (ghost_in) {
-                ra = a.rho_r0;
-                rb = 0.0f;
-            } else {
-                const long long m = ((long long)zn * a.ny + yn) * a.nx + xn;
-                ra = __ldg(a.rho + m);
-                rb = __ldg(a.rho + NN + m);
-            }
-            const float A = ra * a.inv_rho_r0, B = rb * a.inv_rho_b0;
-            ph[j] = (A - B) / (A + B);
-            rh[j] = ra + rb;
-        }
-#pragma unroll
-        for (int j = 1; j < 27; j += 2) {  // c_{j+1} = -c_j
-            const float w3 = 3.0f * wgt(j);
-            const float dp = ph[j] - ph[j + 1], dr = rh[j] - rh[j + 1];
-            if (cx(j) != 0) { gpx = fmaf(w3 * cx(j), dp, gpx); grx = fmaf(w3 * cx(j), dr, grx); }
-            if (cy(j) != 0) { gpy = fmaf(w3 * cy(j), dp, gpy); gry = fmaf(w3 * cy(j), dr, gry); }
-            if (cz(j) != 0) { gpz = fmaf(w3 * cz(j), dp, gpz); grz = fmaf(w3 * cz(j), dr, grz); }
-        }
-    }
+    float gpx, gpy, gpz, grx, gry, grz;
+    stencil_gradients(a, x, y, z, gpx, gpy, gpz, grx, gry, grz);
 
     // macroscopic velocity with the Guo half-force (Eq. Momentum), body force Eq. (bodyForceJet)
     const float rho = rho_r + rho_b;
@@ -271,8 +283,7 @@ __global__ void __launch_bounds__(128) collide_kernel(StepArgs a) {
     const float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
 
     // order parameter (Eq. order) and mixture parameters
-    const float An = rho_r * a.inv_rho_r0, Bn = rho_b * a.inv_rho_b0;
-    const float phi = (An - Bn) / (An + Bn);
+    const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
     const float alpha = hp * a.alpha_r + hm * a.alpha_b;
     const float one_m_alpha = 1.0f - alpha;
@@ -368,6 +379,170 @@ __global__ void __launch_bounds__(128) collide_kernel(StepArgs a) {
     }
 }
 
+// Coefficients of the inverse 1-D sweep: a value at c in {-1, 0, +1} from central moments
+// (m0, m1, m2) about u is G0[c] m0 + G1[c] m1 + G2[c] m2 with
+//   G0 = ((u^2 - u)/2, 1 - u^2, (u^2 + u)/2), G1 = (u - 1/2, -2u, u + 1/2), G2 = (1/2, -1, 1/2).
+struct InvAxis {
+    float g0[3], g1[3];
+    __device__ __forceinline__ explicit InvAxis(float u) {
+        const float u2 = u * u;
+        g0[0] = 0.5f * (u2 - u);
+        g0[1] = 1.0f - u2;
+        g0[2] = 0.5f * (u2 + u);
+        g1[0] = u - 0.5f;
+        g1[1] = -2.0f * u;
+        g1[2] = u + 0.5f;
+    }
+};
+__device__ __forceinline__ constexpr float g2c(int c) { return c == 0 ? -1.0f : 0.5f; }
+
+// -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
+template <bool kForce>
+__global__ void __launch_bounds__(128, 4) collide_kernel(StepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const long long NN = a.NN;
+
+    // post-stream populations reduced to the moments the collision needs
+    float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
+    {
+        float fr[27], fb[27];
+        gather(a, x, y, z, fr, fb);
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {  // same order as the phase-field kernel
+            rho_r += fr[i];
+            rho_b += fb[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const float f = fr[i] + fb[i];
+            sf += f;
+            if (cx(i) > 0) jx += f; else if (cx(i) < 0) jx -= f;
+            if (cy(i) > 0) jy += f; else if (cy(i) < 0) jy -= f;
+            if (cz(i) > 0) jz += f; else if (cz(i) < 0) jz -= f;
+            if (cx(i) != 0) pxx += f;
+            if (cy(i) != 0) pyy += f;
+            if (cz(i) != 0) pzz += f;
+            if (cx(i) * cy(i) > 0) pxy += f; else if (cx(i) * cy(i) < 0) pxy -= f;
+            if (cx(i) * cz(i) > 0) pxz += f; else if (cx(i) * cz(i) < 0) pxz -= f;
+            if (cy(i) * cz(i) > 0) pyz += f; else if (cy(i) * cz(i) < 0) pyz -= f;
+        }
+    }
+
+    float gpx, gpy, gpz, grx, gry, grz;
+    stencil_gradients(a, x, y, z, gpx, gpy, gpz, grx, gry, grz);
+
+    // macroscopic quantities (Eqs. Momentum, bodyForceJet, order) and mixture parameters
+    const float rho = rho_r + rho_b;
+    const float inv_rho = 1.0f / rho;
+    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+    if (kForce) {
+        const float fo = rho - a.rho_b0;
+        Fx = fo * a.gx; Fy = fo * a.gy; Fz = fo * a.gz;
+    }
+    const float jFx = fmaf(0.5f, Fx, jx), jFy = fmaf(0.5f, Fy, jy), jFz = fmaf(0.5f, Fz, jz);
+    const float ux = jFx * inv_rho, uy = jFy * inv_rho, uz = jFz * inv_rho;
+    const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
+    const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
+    const float alpha = hp * a.alpha_r + hm * a.alpha_b;
+    const float oma = 1.0f - alpha;
+    const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);
+    const float tau = 3.0f * nu + 0.5f;
+    const float s2nu = 1.0f / tau;
+    const float Acoef = 2.25f * a.sigma / tau;  // A = 9 sigma / (4 tau)
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float ugr = ux * grx + uy * gry + uz * grz;
+    const float uF = ux * Fx + uy * Fy + uz * Fz;
+
+    // moments of Delta = f - f^e + F'/2: mass, momentum, raw second moment
+    const float M = sf - rho;
+    const float dx = fmaf(-rho, ux, jFx), dy = fmaf(-rho, uy, jFy), dz = fmaf(-rho, uz, jFz);
+    const float cs2r = rho * oma * (9.0f / 19.0f);
+    float Dxx = pxx - (cs2r + rho * ux * ux + nu * (2.0f * ux * grx + ugr));
+    float Dyy = pyy - (cs2r + rho * uy * uy + nu * (2.0f * uy * gry + ugr));
+    float Dzz = pzz - (cs2r + rho * uz * uz + nu * (2.0f * uz * grz + ugr));
+    float Dxy = pxy - (rho * ux * uy + nu * (ux * gry + uy * grx));
+    float Dxz = pxz - (rho * ux * uz + nu * (ux * grz + uz * grx));
+    float Dyz = pyz - (rho * uy * uz + nu * (uy * grz + uz * gry));
+    if (kForce) {
+        Dxx += ux * Fx; Dyy += uy * Fy; Dzz += uz * Fz;
+        Dxy += 0.5f * (ux * Fy + uy * Fx); Dxz += 0.5f * (ux * Fz + uz * Fx); Dyz += 0.5f * (uy * Fz + uz * Fy);
+    }
+    // central moments of Delta, then (I - K') applied
+    const float k000 = (1.0f - a.s0) * M;
+    const float o1 = 1.0f - a.s1;
+    const float k100 = o1 * fmaf(-ux, M, dx), k010 = o1 * fmaf(-uy, M, dy), k001 = o1 * fmaf(-uz, M, dz);
+    const float o2 = 1.0f - s2nu;
+    const float cxx = Dxx - 2.0f * ux * dx + ux * ux * M;
+    const float cyy = Dyy - 2.0f * uy * dy + uy * uy * M;
+    const float czz = Dzz - 2.0f * uz * dz + uz * uz * M;
+    const float k110 = o2 * (Dxy - ux * dy - uy * dx + ux * uy * M);
+    const float k101 = o2 * (Dxz - ux * dz - uz * dx + ux * uz * M);
+    const float k011 = o2 * (Dyz - uy * dz - uz * dy + uy * uz * M);
+    float k200, k020, k002;
+    {
+        const float t = (1.0f - a.s2b) * (cxx + cyy + czz);
+        const float e1 = o2 * (cxx - cyy), e2 = o2 * (cxx - czz);
+        const float third = 1.0f / 3.0f;
+        k200 = (t + e1 + e2) * third;
+        k020 = (t - 2.0f * e1 + e2) * third;
+        k002 = (t + e1 - 2.0f * e2) * third;
+    }
+
+    // inverse transform of the ten surviving moments: z sweep, y sweep (x sweep per direction)
+    const InvAxis Ax(ux), Ay(uy), Az(uz);
+    // z sweep of the columns (p, q): values V_pq[cz]
+    float V00[3], V10[3], V01[3], V20[3], V02[3], V11[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        V00[c] = fmaf(Az.g0[c], k000, fmaf(Az.g1[c], k001, g2c(c - 1) * k002));
+        V10[c] = fmaf(Az.g0[c], k100, Az.g1[c] * k101);
+        V01[c] = fmaf(Az.g0[c], k010, Az.g1[c] * k011);
+        V20[c] = Az.g0[c] * k200;
+        V02[c] = Az.g0[c] * k020;
+        V11[c] = Az.g0[c] * k110;
+    }
+    // y sweep: W_p[cy][cz]
+    float W0[3][3], W1[3][3], W2[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            W0[b][c] = fmaf(Ay.g0[b], V00[c], fmaf(Ay.g1[b], V01[c], g2c(b - 1) * V02[c]));
+            W1[b][c] = fmaf(Ay.g0[b], V10[c], Ay.g1[b] * V11[c]);
+            W2[b][c] = Ay.g0[b] * V20[c];
+        }
+
+    // perturbation (Eq. perturb, squared numerator, both colours) and recolouring
+    const float g2 = gpx * gpx + gpy * gpy + gpz * gpz;
+    const float inv_gm = 1.0f / sqrtf(g2 + a.eps2);  // 1/|grad phi|_eps
+    const float pert = Acoef * inv_gm;
+    const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
+    const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
+    const long long n = ((long long)z * a.ny + y) * a.nx + x;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+        const float cgr = (float)cx(i) * grx + (float)cy(i) * gry + (float)cz(i) * grz;
+        const float cgp = (float)cx(i) * gpx + (float)cy(i) * gpy + (float)cz(i) * gpz;
+        const float Phi = csq(i) == 0 ? -3.0f * nu * ugr : phi_corr(i) * nu * cu * cgr;
+        float fs = rho * fmaf(wgt(i), eq_poly(cu, usq), varphi(i, alpha, oma)) + Phi;  // f^e_i
+        if (kForce) {
+            const float cF = (float)cx(i) * Fx + (float)cy(i) * Fy + (float)cz(i) * Fz;
+            fs = fmaf(0.5f * wgt(i), 3.0f * (cF - uF) + 9.0f * cu * cF, fs);  // + F'_i / 2
+        }
+        const int X = cx(i) + 1, Y = cy(i) + 1, Z = cz(i) + 1;
+        fs += fmaf(Ax.g0[X], W0[Y][Z], fmaf(Ax.g1[X], W1[Y][Z], g2c(cx(i)) * W2[Y][Z]));
+        fs = fmaf(pert, wgt(i) * cgp * cgp - bcoef(i) * g2, fs);
+        const float seg = csq(i) == 0 ? 0.0f : seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
+        a.pout[(long long)i * NN + n] = fmaf(frac_r, fs, seg);
+        a.pout[(long long)(27 + i) * NN + n] = fmaf(frac_b, fs, -seg);
+    }
+}
+
 // ------------------------------------------------------------------------ launchers
 cudaError_t launch_step(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
     if (ev) cudaEventRecord(ev[0], s);
@@ -380,7 +555,14 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long
     if (ev) cudaEventRecord(ev[1], s);
     phase_field_kernel<<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
-    collide_kernel<<<grd, blk, 0, s>>>(a);
+    const bool paper_rates = a.s3 == 1.0f && a.s4 == 1.0f && a.s5 == 1.0f && a.s6 == 1.0f;
+    const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
+    if (!paper_rates)
+        collide_general_kernel<<<grd, blk, 0, s>>>(a);
+    else if (force)
+        collide_kernel<true><<<grd, blk, 0, s>>>(a);
+    else
+        collide_kernel<false><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     *launches += 2;
     return cudaGetLastError();
