@@ -117,47 +117,62 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
     }
 }
 
+// 32-bit offsets of the node and of its three neighbouring columns, rows and planes:
+// xo[d+1] = x - d, yo[d+1] = (y - d) nx, zo[d+1] = (z - d) nx ny for d = -1, 0, 1, wrapped
+// periodically in x and y (and z if periodic), clamped to [0, N] in z otherwise.  The pull
+// source of direction i is zo[cz+1] + yo[cy+1] + xo[cx+1]; the neighbour x + c_j is
+// zo[1-cz] + yo[1-cy] + xo[1-cx].  nx ny nz < 2^31 keeps every offset in 32 bits.
+struct Nbr {
+    int xo[3], yo[3], zo[3];
+    int n, pxy;
+    __device__ __forceinline__ Nbr(const StepArgs &a, int x, int y, int z) {
+        const bool periodic_z = a.bc_zlo == BC_PERIODIC;
+        const int N = a.nz - 1, P = (int)a.plane;
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            int zs = z - d;
+            if (periodic_z) zs = wrapi(zs, a.nz);
+            zs = min(max(zs, 0), N);
+            zo[d + 1] = zs * P;
+            yo[d + 1] = wrapi(y - d, a.ny) * a.nx;
+            xo[d + 1] = wrapi(x - d, a.nx);
+        }
+        pxy = yo[1] + x;
+        n = zo[1] + pxy;
+    }
+    __device__ __forceinline__ int src(int i) const { return zo[cz(i) + 1] + yo[cy(i) + 1] + xo[cx(i) + 1]; }
+    __device__ __forceinline__ int nbr(int j) const { return zo[1 - cz(j)] + yo[1 - cy(j)] + xo[1 - cx(j)]; }
+};
+
 // Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
-__device__ __forceinline__ void gather(const StepArgs &a, int x, int y, int z, float (&fr)[27], float (&fb)[27]) {
-    const long long NN = a.NN, P = a.plane, pxy = (long long)y * a.nx + x;
+__device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, float (&fr)[27], float (&fb)[27]) {
+    const size_t NN = (size_t)a.NN, P = (size_t)a.plane;
     const int N = a.nz - 1;
     const bool periodic_z = a.bc_zlo == BC_PERIODIC;
     const bool lo = (z == 0) && !periodic_z;
     const bool conv = (z == N) && a.bc_zhi == BC_CONVECTIVE;
     const bool slip_hi = (z == N) && a.bc_zhi == BC_FREESLIP;
-    // row offsets for the three source planes / rows / columns
-    long long zo[3], yo[3];
-    int xo[3];
-#pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-        int zs = z - d;
-        if (periodic_z) zs = wrapi(zs, a.nz);
-        zs = min(max(zs, 0), N);  // out-of-range planes are never read (substituted below)
-        zo[d + 1] = (long long)zs * a.ny * a.nx;
-        yo[d + 1] = (long long)wrapi(y - d, a.ny) * a.nx;
-        xo[d + 1] = wrapi(x - d, a.nx);
-    }
     if (conv) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            fr[i] = a.hist_out[(long long)i * P + pxy];
-            fb[i] = a.hist_out[(long long)(27 + i) * P + pxy];
+            fr[i] = a.hist_out[i * P + nb.pxy];
+            fb[i] = a.hist_out[(27 + i) * P + nb.pxy];
         }
         return;
     }
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         if (cz(i) == 1 && lo) {
-            fr[i] = a.zin[(long long)zrank(i) * P + pxy];
-            fb[i] = a.zin[(long long)(9 + zrank(i)) * P + pxy];
+            fr[i] = a.zin[zrank(i) * P + nb.pxy];
+            fb[i] = a.zin[(9 + zrank(i)) * P + nb.pxy];
         } else if (cz(i) == -1 && slip_hi) {
-            fr[i] = a.zout[(long long)zrank(i) * P + pxy];
-            fb[i] = a.zout[(long long)(9 + zrank(i)) * P + pxy];
+            fr[i] = a.zout[zrank(i) * P + nb.pxy];
+            fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
         } else {
-            const long long src = zo[cz(i) + 1] + yo[cy(i) + 1] + xo[cx(i) + 1];
-            fr[i] = __ldg(a.pin + (long long)i * NN + src);
-            fb[i] = __ldg(a.pin + (long long)(27 + i) * NN + src);
+            const int src = nb.src(i);
+            fr[i] = __ldg(a.pin + i * NN + src);
+            fb[i] = __ldg(a.pin + (27 + i) * NN + src);
         }
     }
 }
@@ -168,17 +183,17 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
+    const Nbr nb(a, x, y, z);
     float fr[27], fb[27];
-    gather(a, x, y, z, fr, fb);
+    gather(a, nb, z, fr, fb);
     float rr = 0.0f, rb = 0.0f;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         rr += fr[i];
         rb += fb[i];
     }
-    const long long n = ((long long)z * a.ny + y) * a.nx + x;
-    a.phase[n] = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
-    a.phase[a.NN + n] = rr + rb;
+    a.phase[nb.n] = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
+    a.phase[(size_t)a.NN + nb.n] = rr + rb;
 }
 
 // Isotropic gradients of phi and rho (end of Section II): grad chi = 3 sum_j w_j chi(x + c_j)
@@ -186,31 +201,22 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
 // chi(x - c_j)), so that a uniform field gives exactly zero and nearby values subtract
 // exactly.  Ghosts: z = -1 is phi = 1, rho = rho_r0 inside the inlet disc and the mirror of
 // z = 0 elsewhere; z = N + 1 mirrors z = N.
-__device__ __forceinline__ void stencil_gradients(const StepArgs &a, int x, int y, int z, float &gpx, float &gpy,
+__device__ __forceinline__ void stencil_gradients(const StepArgs &a, const Nbr &nb, int z, float &gpx, float &gpy,
                                                   float &gpz, float &grx, float &gry, float &grz) {
-    const bool periodic_z = a.bc_zlo == BC_PERIODIC;
-    const int N = a.nz - 1;
+    const bool inlet_lo = z == 0 && a.bc_zlo == BC_INLET;
+    const float *__restrict__ ph_ = a.phase;
+    const float *__restrict__ rh_ = a.phase + (size_t)a.NN;
     float ph[27], rh[27];
 #pragma unroll
     for (int j = 1; j < 27; ++j) {
-        const int xn = wrapi(x + cx(j), a.nx), yn = wrapi(y + cy(j), a.ny);
-        int zn = z + cz(j);
-        bool ghost_in = false;
-        if (periodic_z) {
-            zn = wrapi(zn, a.nz);
-        } else if (zn < 0) {
-            zn = 0;
-            ghost_in = a.bc_zlo == BC_INLET && a.disc[(long long)yn * a.nx + xn];
-        } else if (zn > N) {
-            zn = N;
-        }
-        if (ghost_in) {
-            ph[j] = 1.0f;
-            rh[j] = a.rho_r0;
-        } else {
-            const long long m = ((long long)zn * a.ny + yn) * a.nx + xn;
-            ph[j] = __ldg(a.phase + m);
-            rh[j] = __ldg(a.phase + a.NN + m);
+        const int m = nb.nbr(j);  // ghost planes were clamped onto z = 0 / z = N (mirror)
+        ph[j] = __ldg(ph_ + m);
+        rh[j] = __ldg(rh_ + m);
+        if (cz(j) == -1 && inlet_lo) {
+            if (a.disc[nb.yo[1 - cy(j)] + nb.xo[1 - cx(j)]]) {  // z = -1 inside the inlet disc
+                ph[j] = 1.0f;
+                rh[j] = a.rho_r0;
+            }
         }
     }
     gpx = gpy = gpz = grx = gry = grz = 0.0f;
@@ -249,15 +255,15 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
-    const long long NN = a.NN;
-    const int N = a.nz - 1;
+    const size_t NN = (size_t)a.NN;
+    const Nbr nb(a, x, y, z);
 
     // post-stream populations, colour-blind sum and densities (same order as K_A)
     float f[27];
     float rho_r = 0.0f, rho_b = 0.0f;
     {
         float fr[27], fb[27];
-        gather(a, x, y, z, fr, fb);
+        gather(a, nb, z, fr, fb);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             rho_r += fr[i];
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     }
 
     float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients(a, x, y, z, gpx, gpy, gpz, grx, gry, grz);
+    stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
 
     // macroscopic velocity with the Guo half-force (Eq. Momentum), body force Eq. (bodyForceJet)
     const float rho = rho_r + rho_b;
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;  // beta rho_r rho_b / (rho |g|)
     const float pert = Acoef * inv_gm;
-    const long long n = ((long long)z * a.ny + y) * a.nx + x;
+    const int n = nb.n;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
@@ -374,10 +380,11 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
         float fs = fe + 0.5f * Fp + m[cell(i)];
         fs += pert * (wgt(i) * cgp * cgp - bcoef(i) * g2);
         const float seg = csq(i) == 0 ? 0.0f : seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
-        a.pout[(long long)i * NN + n] = fmaf(frac_r, fs, seg);
-        a.pout[(long long)(27 + i) * NN + n] = fmaf(frac_b, fs, -seg);
+        a.pout[i * NN + n] = fmaf(frac_r, fs, seg);
+        a.pout[(27 + i) * NN + n] = fmaf(frac_b, fs, -seg);
     }
 }
+
 
 // Coefficients of the inverse 1-D sweep: a value at c in {-1, 0, +1} from central moments
 // (m0, m1, m2) about u is G0[c] m0 + G1[c] m1 + G2[c] m2 with
@@ -398,42 +405,46 @@ __device__ __forceinline__ constexpr float g2c(int c) { return c == 0 ? -1.0f : 
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
 template <bool kForce>
-__global__ void __launch_bounds__(128, 4) collide_kernel(StepArgs a) {
+__global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
-    const long long NN = a.NN;
+    const size_t NN = (size_t)a.NN;
+    const Nbr nb(a, x, y, z);
 
     // post-stream populations reduced to the moments the collision needs
     float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
     {
         float fr[27], fb[27];
-        gather(a, x, y, z, fr, fb);
+        gather(a, nb, z, fr, fb);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {  // same order as the phase-field kernel
             rho_r += fr[i];
             rho_b += fb[i];
         }
+        // opposite pairs (i, i+1): odd moments take the difference, even ones the sum
+        sf = fr[0] + fb[0];
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            const float f = fr[i] + fb[i];
-            sf += f;
-            if (cx(i) > 0) jx += f; else if (cx(i) < 0) jx -= f;
-            if (cy(i) > 0) jy += f; else if (cy(i) < 0) jy -= f;
-            if (cz(i) > 0) jz += f; else if (cz(i) < 0) jz -= f;
-            if (cx(i) != 0) pxx += f;
-            if (cy(i) != 0) pyy += f;
-            if (cz(i) != 0) pzz += f;
-            if (cx(i) * cy(i) > 0) pxy += f; else if (cx(i) * cy(i) < 0) pxy -= f;
-            if (cx(i) * cz(i) > 0) pxz += f; else if (cx(i) * cz(i) < 0) pxz -= f;
-            if (cy(i) * cz(i) > 0) pyz += f; else if (cy(i) * cz(i) < 0) pyz -= f;
+        for (int i = 1; i < 27; i += 2) {
+            const float fp = fr[i] + fb[i], fm = fr[i + 1] + fb[i + 1];
+            const float s2 = fp + fm, d2 = fp - fm;
+            sf += s2;
+            if (cx(i) > 0) jx += d2; else if (cx(i) < 0) jx -= d2;
+            if (cy(i) > 0) jy += d2; else if (cy(i) < 0) jy -= d2;
+            if (cz(i) > 0) jz += d2; else if (cz(i) < 0) jz -= d2;
+            if (cx(i) != 0) pxx += s2;
+            if (cy(i) != 0) pyy += s2;
+            if (cz(i) != 0) pzz += s2;
+            if (cx(i) * cy(i) > 0) pxy += s2; else if (cx(i) * cy(i) < 0) pxy -= s2;
+            if (cx(i) * cz(i) > 0) pxz += s2; else if (cx(i) * cz(i) < 0) pxz -= s2;
+            if (cy(i) * cz(i) > 0) pyz += s2; else if (cy(i) * cz(i) < 0) pyz -= s2;
         }
     }
 
     float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients(a, x, y, z, gpx, gpy, gpz, grx, gry, grz);
+    stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
 
     // macroscopic quantities (Eqs. Momentum, bodyForceJet, order) and mixture parameters
     const float rho = rho_r + rho_b;
@@ -522,24 +533,47 @@ __global__ void __launch_bounds__(128, 4) collide_kernel(StepArgs a) {
     const float pert = Acoef * inv_gm;
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
-    const long long n = ((long long)z * a.ny + y) * a.nx + x;
+    const int n = nb.n;
+    float *const pout = a.pout;
+    // rest direction: no shift terms, no recolouring flux
+    {
+        float fs = rho * fmaf(wgt(0), -1.5f * usq, alpha) - 3.0f * nu * ugr;
+        if (kForce) fs = fmaf(0.5f * wgt(0), -3.0f * uF, fs);
+        fs += fmaf(Ax.g0[1], W0[1][1], fmaf(Ax.g1[1], W1[1][1], -W2[1][1]));
+        fs = fmaf(pert, -bcoef(0) * g2, fs);
+        pout[n] = frac_r * fs;
+        pout[27 * NN + n] = frac_b * fs;
+    }
+    // opposite pairs (i, i+1), c_{i+1} = -c_i: c.u, c.grad rho and c.grad phi change sign;
+    // f^e splits into an even part (rest weight, quadratic terms, Phi) and an odd part
+    // (linear and cubic terms), the perturbation is even and the recolouring flux odd.
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
+    for (int i = 1; i < 27; i += 2) {
         const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
         const float cgr = (float)cx(i) * grx + (float)cy(i) * gry + (float)cz(i) * grz;
         const float cgp = (float)cx(i) * gpx + (float)cy(i) * gpy + (float)cz(i) * gpz;
-        const float Phi = csq(i) == 0 ? -3.0f * nu * ugr : phi_corr(i) * nu * cu * cgr;
-        float fs = rho * fmaf(wgt(i), eq_poly(cu, usq), varphi(i, alpha, oma)) + Phi;  // f^e_i
+        const float h = 4.5f * cu;
+        const float ev = fmaf(h, cu, -1.5f * usq);                  // 9/2 cu^2 - 3/2 u^2
+        const float od = cu * fmaf(h, cu, fmaf(-4.5f, usq, 3.0f));  // 3 cu + 9/2 cu^3 - 9/2 cu u^2
+        const float rw = rho * wgt(i);
+        float even = fmaf(rw, ev, rho * varphi(i, alpha, oma));
+        even = fmaf(phi_corr(i) * nu * cu, cgr, even);                // Phi_i
+        even = fmaf(pert, wgt(i) * cgp * cgp - bcoef(i) * g2, even);  // perturbation
+        float odd = rw * od;
         if (kForce) {
             const float cF = (float)cx(i) * Fx + (float)cy(i) * Fy + (float)cz(i) * Fz;
-            fs = fmaf(0.5f * wgt(i), 3.0f * (cF - uF) + 9.0f * cu * cF, fs);  // + F'_i / 2
+            even = fmaf(0.5f * wgt(i), fmaf(9.0f * cu, cF, -3.0f * uF), even);  // F'/2, even part
+            odd = fmaf(1.5f * wgt(i), cF, odd);                                   // F'/2, odd part
         }
         const int X = cx(i) + 1, Y = cy(i) + 1, Z = cz(i) + 1;
-        fs += fmaf(Ax.g0[X], W0[Y][Z], fmaf(Ax.g1[X], W1[Y][Z], g2c(cx(i)) * W2[Y][Z]));
-        fs = fmaf(pert, wgt(i) * cgp * cgp - bcoef(i) * g2, fs);
-        const float seg = csq(i) == 0 ? 0.0f : seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
-        a.pout[(long long)i * NN + n] = fmaf(frac_r, fs, seg);
-        a.pout[(long long)(27 + i) * NN + n] = fmaf(frac_b, fs, -seg);
+        const float rp = fmaf(Ax.g0[X], W0[Y][Z], fmaf(Ax.g1[X], W1[Y][Z], g2c(cx(i)) * W2[Y][Z]));
+        const float rm = fmaf(Ax.g0[2 - X], W0[2 - Y][2 - Z], fmaf(Ax.g1[2 - X], W1[2 - Y][2 - Z], g2c(cx(i)) * W2[2 - Y][2 - Z]));
+        const float fsp = (even + odd) + rp, fsm = (even - odd) + rm;
+        const float seg = seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
+        pout[i * NN + n] = fmaf(frac_r, fsp, seg);
+        pout[(27 + i) * NN + n] = fmaf(frac_b, fsp, -seg);
+        pout[(i + 1) * NN + n] = fmaf(frac_r, fsm, -seg);
+        pout[(28 + i) * NN + n] = fmaf(frac_b, fsm, seg);
     }
 }
 
