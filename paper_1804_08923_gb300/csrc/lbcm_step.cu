@@ -368,21 +368,28 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;  // beta rho_r rho_b / (rho |g|)
     const float pert = Acoef * inv_gm;
     const int n = nb.n;
+    float sum_r = 0.0f, sum_b = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
+    for (int i = 1; i < 27; ++i) {  // the rest direction is the per-colour remainder below
         const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
         const float cg = (float)cx(i) * grx + (float)cy(i) * gry + (float)cz(i) * grz;
         const float cF = (float)cx(i) * Fx + (float)cy(i) * Fy + (float)cz(i) * Fz;
-        const float Phi = csq(i) == 0 ? -3.0f * nu * ugr : phi_corr(i) * nu * cu * cg;
+        const float Phi = phi_corr(i) * nu * cu * cg;
         const float fe = rho * fmaf(wgt(i), eq_poly(cu, usq), varphi(i, alpha, one_m_alpha)) + Phi;
         const float Fp = wgt(i) * (3.0f * (cF - uF) + 9.0f * cu * cF);
         const float cgp = (float)cx(i) * gpx + (float)cy(i) * gpy + (float)cz(i) * gpz;
         float fs = fe + 0.5f * Fp + m[cell(i)];
         fs += pert * (wgt(i) * cgp * cgp - bcoef(i) * g2);
-        const float seg = csq(i) == 0 ? 0.0f : seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
-        a.pout[i * NN + n] = fmaf(frac_r, fs, seg);
-        a.pout[(27 + i) * NN + n] = fmaf(frac_b, fs, -seg);
+        const float seg = seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
+        const float vr = fmaf(frac_r, fs, seg), vb = fmaf(frac_b, fs, -seg);
+        a.pout[i * NN + n] = vr;
+        a.pout[(27 + i) * NN + n] = vb;
+        sum_r += vr;
+        sum_b += vb;
     }
+    // rest direction as the per-colour remainder (see collide_kernel)
+    a.pout[n] = rho_r - sum_r;
+    a.pout[27 * NN + n] = rho_b - sum_b;
 }
 
 
@@ -535,15 +542,7 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
     const int n = nb.n;
     float *const pout = a.pout;
-    // rest direction: no shift terms, no recolouring flux
-    {
-        float fs = rho * fmaf(wgt(0), -1.5f * usq, alpha) - 3.0f * nu * ugr;
-        if (kForce) fs = fmaf(0.5f * wgt(0), -3.0f * uF, fs);
-        fs += fmaf(Ax.g0[1], W0[1][1], fmaf(Ax.g1[1], W1[1][1], -W2[1][1]));
-        fs = fmaf(pert, -bcoef(0) * g2, fs);
-        pout[n] = frac_r * fs;
-        pout[27 * NN + n] = frac_b * fs;
-    }
+    float sum_r = 0.0f, sum_b = 0.0f;  // moving populations written, per colour
     // opposite pairs (i, i+1), c_{i+1} = -c_i: c.u, c.grad rho and c.grad phi change sign;
     // f^e splits into an even part (rest weight, quadratic terms, Phi) and an odd part
     // (linear and cubic terms), the perturbation is even and the recolouring flux odd.
@@ -570,11 +569,21 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
         const float rm = fmaf(Ax.g0[2 - X], W0[2 - Y][2 - Z], fmaf(Ax.g1[2 - X], W1[2 - Y][2 - Z], g2c(cx(i)) * W2[2 - Y][2 - Z]));
         const float fsp = (even + odd) + rp, fsm = (even - odd) + rm;
         const float seg = seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
-        pout[i * NN + n] = fmaf(frac_r, fsp, seg);
-        pout[(27 + i) * NN + n] = fmaf(frac_b, fsp, -seg);
-        pout[(i + 1) * NN + n] = fmaf(frac_r, fsm, -seg);
-        pout[(28 + i) * NN + n] = fmaf(frac_b, fsm, seg);
+        const float rp_ = fmaf(frac_r, fsp, seg), bp_ = fmaf(frac_b, fsp, -seg);
+        const float rm_ = fmaf(frac_r, fsm, -seg), bm_ = fmaf(frac_b, fsm, seg);
+        pout[i * NN + n] = rp_;
+        pout[(27 + i) * NN + n] = bp_;
+        pout[(i + 1) * NN + n] = rm_;
+        pout[(28 + i) * NN + n] = bm_;
+        sum_r += rp_ + rm_;
+        sum_b += bp_ + bm_;
     }
+    // Rest direction.  In exact arithmetic the step keeps each colour's mass at this node
+    // (sum_i f_i^k* = rho_k), so the rest population is that mass minus the moving ones;
+    // this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32 rounding of the lattice
+    // constants from drifting the colour masses step after step.
+    pout[n] = rho_r - sum_r;
+    pout[27 * NN + n] = rho_b - sum_b;
 }
 
 // ------------------------------------------------------------------------ launchers

@@ -205,7 +205,7 @@ def test_mass_conservation_and_reduction(lb):
     m0 = gpu.mass()
     S = gpu.populations(device=False).astype(np.float64)
     assert np.allclose(m0, [S[0].sum(), S[1].sum()], rtol=1e-12, atol=0)
-    gpu.step(200)
+    gpu.step(1000)
     m1 = gpu.mass()
     assert np.all(np.abs(m1 - m0) / m0 < 2e-6), (m0, m1)
     m2 = gpu.mass()
