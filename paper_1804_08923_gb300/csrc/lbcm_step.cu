@@ -410,17 +410,13 @@ struct InvAxis {
 };
 __device__ __forceinline__ constexpr float g2c(int c) { return c == 0 ? -1.0f : 0.5f; }
 
-// -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
-template <bool kForce>
-__global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= a.nx || y >= a.ny) return;
-    const size_t NN = (size_t)a.NN;
-    const Nbr nb(a, x, y, z);
+// Moments of the post-stream populations of one node that the paper-rate collision needs:
+// colour densities, colour-blind mass, momentum and raw second moment.
+struct Moments {
+    float rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
+};
 
-    // post-stream populations reduced to the moments the collision needs
+__device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb, int z, Moments &m) {
     float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
     {
@@ -450,9 +446,17 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
         }
     }
 
-    float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    m = Moments{rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz};
+}
 
+// Collision, perturbation and recolouring of one node from its moments and gradients;
+// writes the 54 post-collision populations of node n.
+template <bool kForce>
+__device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, const Moments &mo, float gpx, float gpy,
+                                                     float gpz, float grx, float gry, float grz) {
+    const size_t NN = (size_t)a.NN;
+    const float rho_r = mo.rho_r, rho_b = mo.rho_b, sf = mo.sf, jx = mo.jx, jy = mo.jy, jz = mo.jz;
+    const float pxx = mo.pxx, pyy = mo.pyy, pzz = mo.pzz, pxy = mo.pxy, pxz = mo.pxz, pyz = mo.pyz;
     // macroscopic quantities (Eqs. Momentum, bodyForceJet, order) and mixture parameters
     const float rho = rho_r + rho_b;
     const float inv_rho = 1.0f / rho;
@@ -540,7 +544,6 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     const float pert = Acoef * inv_gm;
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
-    const int n = nb.n;
     float *const pout = a.pout;
     float sum_r = 0.0f, sum_b = 0.0f;  // moving populations written, per colour
     // opposite pairs (i, i+1), c_{i+1} = -c_i: c.u, c.grad rho and c.grad phi change sign;
@@ -586,6 +589,22 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     pout[27 * NN + n] = rho_b - sum_b;
 }
 
+// -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
+template <bool kForce>
+__global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const Nbr nb(a, x, y, z);
+    Moments mo;
+    gather_moments(a, nb, z, mo);
+    float gpx, gpy, gpz, grx, gry, grz;
+    stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    collide_from_moments<kForce>(a, nb.n, mo, gpx, gpy, gpz, grx, gry, grz);
+}
+
+
 // ------------------------------------------------------------------------ launchers
 cudaError_t launch_step(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
     if (ev) cudaEventRecord(ev[0], s);
@@ -594,20 +613,20 @@ cudaError_t launch_step(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long
         boundary_plane_kernel<<<g, b, 0, s>>>(a);
         *launches += 1;
     }
-    dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
-    if (ev) cudaEventRecord(ev[1], s);
-    phase_field_kernel<<<grd, blk, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[2], s);
     const bool paper_rates = a.s3 == 1.0f && a.s4 == 1.0f && a.s5 == 1.0f && a.s6 == 1.0f;
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
+    if (ev) cudaEventRecord(ev[1], s);
+    dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
+    phase_field_kernel<<<grd, blk, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[2], s);
     if (!paper_rates)
         collide_general_kernel<<<grd, blk, 0, s>>>(a);
     else if (force)
         collide_kernel<true><<<grd, blk, 0, s>>>(a);
     else
         collide_kernel<false><<<grd, blk, 0, s>>>(a);
-    if (ev) cudaEventRecord(ev[3], s);
     *launches += 2;
+    if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 
