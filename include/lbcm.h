@@ -64,7 +64,13 @@ typedef struct {
     int32_t bc_zlo, bc_zhi;
 } lb_grid;
 
-typedef enum { LB_STORE_FP32 = 0 } lb_storage;
+/* Population storage.  FP32: every population in single precision.  FP16: the 26 moving
+ * populations of each colour are stored in half precision as deviations from the storing
+ * node's rest equilibrium, h_i^k = f_i^k - rho_k varphi_i(alpha_k) (Eq. varphi_ik), the rest
+ * population in single precision; it takes each colour's remainder of the moving ones as
+ * they are read back, so per-node colour mass is kept to FP32 rounding.  Arithmetic is FP32
+ * in both. */
+typedef enum { LB_STORE_FP32 = 0, LB_STORE_FP16 = 1 } lb_storage;
 
 typedef struct {
     double rho_r0, rho_b0;  /* initial densities (Eq. order); gamma = rho_r0/rho_b0 >= 19/27 */

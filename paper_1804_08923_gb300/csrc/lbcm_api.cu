@@ -39,6 +39,11 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// Bytes of one population buffer: FP32 float2[27][NN]; FP16 float2 rest[NN] + __half2[26][NN].
+size_t pop_buffer_bytes(size_t nn, int storage) {
+    return storage == LB_STORE_FP16 ? 8 * nn + 4 * 26 * nn : 8 * 27 * nn;
+}
+
 struct AuxLayout {
     size_t disc, zin, zout, partial, total;
 };
@@ -82,7 +87,8 @@ lb_status validate(const lb_grid *g, const lb_params *p) {
     for (double v : s)
         if (!(v >= 0.0 && v < 2.0)) return fail(LB_EINVAL, "relaxation rates must lie in [0, 2)");
     if (!(p->eps_grad >= 0) || !std::isfinite(p->eps_grad)) return fail(LB_EINVAL, "eps_grad must be finite and >= 0");
-    if (p->storage != LB_STORE_FP32) return fail(LB_EINVAL, "storage must be LB_STORE_FP32");
+    if (p->storage != LB_STORE_FP32 && p->storage != LB_STORE_FP16)
+        return fail(LB_EINVAL, "storage must be LB_STORE_FP32 or LB_STORE_FP16");
     if (p->check_every < 0) return fail(LB_EINVAL, "check_every must be >= 0");
     if (g->bc_zlo == LB_BC_INLET) {
         if (!(p->d_in >= 0) || !std::isfinite(p->d_in) || !std::isfinite(p->u_in) || !std::isfinite(p->noise_amp))
@@ -103,8 +109,9 @@ struct lb_ctx {
     void *bufs[LB_MAX_BUFFERS] = {};
     size_t sizes[LB_MAX_BUFFERS] = {};
     int nbufs = 0;
-    float *pop[2] = {nullptr, nullptr};
-    float *phase = nullptr;
+    void *pop[2] = {nullptr, nullptr};
+    float2 *phase = nullptr;
+    float2 *shift[2] = {nullptr, nullptr};  // FP16: shift densities paired with pop[0], pop[1]
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -121,76 +128,112 @@ struct lb_ctx {
 namespace lbcm {
 
 // ------------------------------------------------------------ initial populations
-// f_i^k = rho_k [varphi_i(alpha_k) + w_i P(c_i.u, u^2)]  (Eq. EES per colour, Phi = 0)
-__global__ void init_kernel(float *__restrict__ pop, float *__restrict__ hist, const float *__restrict__ fr,
-                            const float *__restrict__ fb, const float *__restrict__ fu, int kind, int nx, int ny, int nz,
-                            float a0, float a1, float a2, float a3, float a4, float rho_r0, float rho_b0,
-                            float alpha_r, float alpha_b) {
+// f_i^k = rho_k [varphi_i(alpha_k) + w_i P(c_i.u, u^2)]  (Eq. EES per colour, Phi = 0); the
+// rest population takes each colour's remainder of the stored moving ones.
+struct InitArgs {
+    void *pop;
+    float2 *shift;
+    float *hist;
+    const float *fr, *fb, *fu;
+    int kind, nx, ny, nz;
+    float a0, a1, a2, a3, a4, rho_r0, rho_b0, alpha_r, alpha_b;
+};
+
+template <int S>
+__global__ void init_kernel(InitArgs ia, StepArgs sa) {
+    const int nx = ia.nx, ny = ia.ny, nz = ia.nz;
     const long long NN = (long long)nx * ny * nz;
+    sa.pout = ia.pop;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
         float rr, rb, ux = 0.0f, uy = 0.0f, uz = 0.0f;
-        if (kind == LB_INIT_UNIFORM) {
-            rr = a0; rb = a1; ux = a2; uy = a3; uz = a4;
-        } else if (kind == LB_INIT_DROPLET) {
+        if (ia.kind == LB_INIT_UNIFORM) {
+            rr = ia.a0; rb = ia.a1; ux = ia.a2; uy = ia.a3; uz = ia.a4;
+        } else if (ia.kind == LB_INIT_DROPLET) {
             // Section III: rho_r = rho_r0/2 [1 - tanh(2(r-R)/W)], rho_b = rho_b0/2 [1 + tanh(...)]
             const float dx = x - 0.5f * (nx - 1), dy = y - 0.5f * (ny - 1), dz = z - 0.5f * (nz - 1);
             const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float t = tanhf(2.0f * (r - a0) / a1);
-            rr = 0.5f * rho_r0 * (1.0f - t);
-            rb = 0.5f * rho_b0 * (1.0f + t);
-        } else if (kind == LB_INIT_JET) {
-            rr = 0.0f; rb = rho_b0;
+            const float t = tanhf(2.0f * (r - ia.a0) / ia.a1);
+            rr = 0.5f * ia.rho_r0 * (1.0f - t);
+            rb = 0.5f * ia.rho_b0 * (1.0f + t);
+        } else if (ia.kind == LB_INIT_JET) {
+            rr = 0.0f; rb = ia.rho_b0;
         } else {
-            rr = fr[n]; rb = fb[n]; ux = fu[n]; uy = fu[NN + n]; uz = fu[2 * NN + n];
+            rr = ia.fr[n]; rb = ia.fb[n]; ux = ia.fu[n]; uy = ia.fu[NN + n]; uz = ia.fu[2 * NN + n];
         }
+        const float2 own = make_float2(rr, rb);
+        if (S == STORE_FP16) ia.shift[n] = own;
         const float usq = ux * ux + uy * uy + uz * uz;
+        float sr = 0.0f, sb = 0.0f;
+        const bool top = z == nz - 1;
+        const long long h = (long long)y * nx + x, P = (long long)nx * ny;
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {
+        for (int i = 1; i < 27; ++i) {
             const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
             const float pw = wgt(i) * eq_poly(cu, usq);
-            const float vr = rr * (varphi(i, alpha_r, 1.0f - alpha_r) + pw);
-            const float vb = rb * (varphi(i, alpha_b, 1.0f - alpha_b) + pw);
-            pop[(long long)i * NN + n] = vr;
-            pop[(long long)(27 + i) * NN + n] = vb;
-            if (z == nz - 1) {
-                const long long h = (long long)y * nx + x, P = (long long)nx * ny;
-                hist[(long long)i * P + h] = vr;
-                hist[(long long)(27 + i) * P + h] = vb;
+            const float2 f = make_float2(rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw),
+                                         rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw));
+            const float2 d = store_pop<S>(sa, i, (int)n, f, own);
+            sr += d.x;
+            sb += d.y;
+            if (top) {
+                ia.hist[(long long)i * P + h] = d.x;
+                ia.hist[(long long)(27 + i) * P + h] = d.y;
             }
+        }
+        const float2 f0 = make_float2(rr - sr, rb - sb);
+        store_pop<S>(sa, 0, (int)n, f0, own);
+        if (top) {
+            ia.hist[h] = f0.x;
+            ia.hist[27 * P + h] = f0.y;
         }
     }
 }
 
 // ------------------------------------------------------------------- fields
-__global__ void fields_kernel(const float *__restrict__ pop, float *o_rr, float *o_rb,
-                              float *o_phi, float *o_ux, float *o_uy, float *o_uz, float *o_p, long long NN,
-                              float inv_rho_r0, float inv_rho_b0, float rho_b0, float gx, float gy, float gz,
-                              float alpha_r, float alpha_b) {
+struct FieldOut {
+    float *o[LB_NFIELDS];
+};
+
+template <int S>
+__global__ void fields_kernel(StepArgs sa, FieldOut fo, float gx, float gy, float gz) {
+    const long long NN = sa.NN;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
         float rr = 0.0f, rb = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            const float a = __ldg(pop + (long long)i * NN + n), b = __ldg(pop + (long long)(27 + i) * NN + n);
-            rr += a;
-            rb += b;
-            if (cx(i) != 0) jx += cx(i) * (a + b);
-            if (cy(i) != 0) jy += cy(i) * (a + b);
-            if (cz(i) != 0) jz += cz(i) * (a + b);
+            const float2 v = load_pop<S>(sa, i, (int)n);
+            rr += v.x;
+            rb += v.y;
+            if (cx(i) != 0) jx += cx(i) * (v.x + v.y);
+            if (cy(i) != 0) jy += cy(i) * (v.x + v.y);
+            if (cz(i) != 0) jz += cz(i) * (v.x + v.y);
         }
         const float rho = rr + rb;
-        const float A = rr * inv_rho_r0, B = rb * inv_rho_b0;
-        const float phi = (A - B) / (A + B);
-        const float fo = rho - rho_b0;
-        if (o_rr) o_rr[n] = rr;
-        if (o_rb) o_rb[n] = rb;
-        if (o_phi) o_phi[n] = phi;
-        if (o_ux) o_ux[n] = (jx - 0.5f * fo * gx) / rho;
-        if (o_uy) o_uy[n] = (jy - 0.5f * fo * gy) / rho;
-        if (o_uz) o_uz[n] = (jz - 0.5f * fo * gz) / rho;
-        if (o_p) {
-            const float alpha = 0.5f * (1.0f + phi) * alpha_r + 0.5f * (1.0f - phi) * alpha_b;
-            o_p[n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (press)
+        const float phi = order_parameter(rr, rb, sa.inv_rho_r0, sa.inv_rho_b0);
+        const float fc = rho - sa.rho_b0;
+        if (fo.o[LB_FIELD_RHO_R]) fo.o[LB_FIELD_RHO_R][n] = rr;
+        if (fo.o[LB_FIELD_RHO_B]) fo.o[LB_FIELD_RHO_B][n] = rb;
+        if (fo.o[LB_FIELD_PHI]) fo.o[LB_FIELD_PHI][n] = phi;
+        if (fo.o[LB_FIELD_UX]) fo.o[LB_FIELD_UX][n] = (jx - 0.5f * fc * gx) / rho;
+        if (fo.o[LB_FIELD_UY]) fo.o[LB_FIELD_UY][n] = (jy - 0.5f * fc * gy) / rho;
+        if (fo.o[LB_FIELD_UZ]) fo.o[LB_FIELD_UZ][n] = (jz - 0.5f * fc * gz) / rho;
+        if (fo.o[LB_FIELD_P]) {
+            const float alpha = 0.5f * (1.0f + phi) * sa.alpha_r + 0.5f * (1.0f - phi) * sa.alpha_b;
+            fo.o[LB_FIELD_P][n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (press)
+        }
+    }
+}
+
+// Decoded populations of colour k in the canonical layout out[i][n] (27 x NN floats).
+template <int S>
+__global__ void canonical_kernel(StepArgs sa, int k, float *__restrict__ out) {
+    const long long NN = sa.NN;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const float2 v = load_pop<S>(sa, i, (int)n);
+            out[(long long)i * NN + n] = k == 0 ? v.x : v.y;
         }
     }
 }
@@ -208,6 +251,33 @@ __global__ void __launch_bounds__(kMassThreads) mass_partial_kernel(const float 
     for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) acc += (double)__ldg(pop + (long long)(27 * k + i) * NN + n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double warp_sums[kMassThreads / 32];
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kMassThreads / 32; ++w) t += warp_sums[w];
+        partial[k * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// Same first stage over a context's own population storage (decoded).
+template <int S>
+__global__ void __launch_bounds__(kMassThreads) mass_partial_store_kernel(StepArgs sa, double *__restrict__ partial) {
+    const int k = blockIdx.y;
+    const long long NN = sa.NN;
+    const long long per = (NN + gridDim.x - 1) / gridDim.x;
+    const long long n0 = blockIdx.x * per, n1 = min(NN, n0 + per);
+    double acc = 0.0;
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const float2 v = load_pop<S>(sa, i, (int)n);
+            acc += (double)(k == 0 ? v.x : v.y);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -257,11 +327,15 @@ lb_status setup_ctx(lb_ctx *c) {
     const lb_grid &g = c->g;
     c->nn = (long long)g.nx * g.ny * g.nz;
     c->plane = (long long)g.nx * g.ny;
-    const size_t pop_bytes = (size_t)54 * c->nn * sizeof(float);
     const size_t hist_bytes = (size_t)54 * c->plane * sizeof(float);
-    c->pop[0] = (float *)c->bufs[0];
-    c->pop[1] = (float *)c->bufs[1];
-    c->phase = (float *)c->bufs[2];
+    c->pop[0] = c->bufs[0];
+    c->pop[1] = c->bufs[1];
+    c->phase = (float2 *)c->bufs[2];
+    if (c->p.storage == LB_STORE_FP16) {
+        const size_t pb = align_up(8 * (size_t)c->nn);
+        c->shift[0] = (float2 *)((char *)c->bufs[2] + pb);
+        c->shift[1] = (float2 *)((char *)c->bufs[2] + 2 * pb);
+    }
     c->hist[0] = (float *)c->bufs[3];
     c->hist[1] = (float *)((char *)c->bufs[3] + align_up(hist_bytes));
     const AuxLayout L = aux_layout(g);
@@ -270,7 +344,6 @@ lb_status setup_ctx(lb_ctx *c) {
     c->zin = (float *)(aux + L.zin);
     c->zout = (float *)(aux + L.zout);
     c->partial = (double *)(aux + L.partial);
-    (void)pop_bytes;
     // inlet disc membership, decided in FP64 on the host:
     // (2x - (nx-1))^2 + (2y - (ny-1))^2 < D^2  <=>  (x - x_c)^2 + (y - y_c)^2 < (D/2)^2
     std::vector<uint8_t> disc((size_t)c->plane, 0);
@@ -294,6 +367,8 @@ StepArgs make_args(const lb_ctx *c) {
     StepArgs a{};
     a.pin = c->pop[c->cur];
     a.pout = c->pop[c->cur ^ 1];
+    a.rin = c->shift[c->cur];
+    a.rout = c->shift[c->cur ^ 1];
     a.phase = c->phase;
     a.hist_in = c->hist[c->hcur];
     a.hist_out = c->hist[c->hcur ^ 1];
@@ -317,13 +392,25 @@ StepArgs make_args(const lb_ctx *c) {
     a.s4 = (float)p.s4; a.s5 = (float)p.s5; a.s6 = (float)p.s6;
     a.u_in = (float)p.u_in; a.noise_amp = (float)p.noise_amp;
     a.xc = (float)(0.5 * (g.nx - 1)); a.yc = (float)(0.5 * (g.ny - 1));
+    // FP16 shift weights varphi_i(alpha_k) by speed class (Eq. varphi_ik), one rounding
+    const double kq[4] = {0.0, 2.0 / 19.0, 1.0 / 38.0, 1.0 / 152.0};
+    const double alpha_r = 1.0 - (1.0 - alpha_b) / (p.rho_r0 / p.rho_b0);
+    for (int q = 0; q < 4; ++q) {
+        a.shift_r[q] = (float)(kq[q] * (1.0 - alpha_r));
+        a.shift_b[q] = (float)(kq[q] * (1.0 - alpha_b));
+    }
     a.seed = p.seed;
     a.step = c->step;
     return a;
 }
 
-lb_status run_mass(lb_ctx *c, const float *pop, double out[2]) {
-    mass_partial_kernel<<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(pop, c->nn, c->partial);
+// FP64 colour masses of the current state (store-aware first stage).
+lb_status run_mass(lb_ctx *c, double out[2]) {
+    const StepArgs sa = make_args(c);  // pin / rin = the current state
+    if (c->p.storage == LB_STORE_FP16)
+        mass_partial_store_kernel<STORE_FP16><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
+    else
+        mass_partial_store_kernel<STORE_FP32><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
     mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->partial, kMassBlocks, c->partial + 2 * kMassBlocks);
     c->launches += 2;
     LB_CUDA(cudaGetLastError());
@@ -362,9 +449,9 @@ lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *
     if (s != LB_OK) return s;
     if (!sizes_out || !n_out) return fail(LB_EINVAL, "sizes_out and n_out must not be NULL");
     const size_t nn = (size_t)grid->nx * grid->ny * grid->nz, plane = (size_t)grid->nx * grid->ny;
-    sizes_out[0] = align_up(54 * nn * sizeof(float));
+    sizes_out[0] = align_up(pop_buffer_bytes(nn, params->storage));
     sizes_out[1] = sizes_out[0];
-    sizes_out[2] = align_up(2 * nn * sizeof(float));
+    sizes_out[2] = align_up(8 * nn) * (params->storage == LB_STORE_FP16 ? 3 : 1);  // phase (+ FP16 shift ping-pong)
     sizes_out[3] = 2 * align_up(54 * plane * sizeof(float));
     sizes_out[4] = aux_layout(*grid).total;
     *n_out = 5;
@@ -475,7 +562,7 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
         if (fields_on_device) {
             fr = rho_r; fb = rho_b; fu = u;
         } else {
-            float *stage = c->pop[1];
+            float *stage = (float *)c->pop[1];
             const size_t nb = (size_t)c->nn * sizeof(float);
             LB_CUDA(cudaMemcpyAsync(stage, rho_r, nb, cudaMemcpyHostToDevice, c->stream));
             LB_CUDA(cudaMemcpyAsync(stage + c->nn, rho_b, nb, cudaMemcpyHostToDevice, c->stream));
@@ -483,11 +570,13 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
             fr = stage; fb = stage + c->nn; fu = stage + 2 * c->nn;
         }
     }
-    const double alpha_b = 8.0 / 27.0;
-    const double alpha_r = 1.0 - (1.0 - alpha_b) / (c->p.rho_r0 / c->p.rho_b0);
-    init_kernel<<<grid_for(c->nn, 256), 256, 0, c->stream>>>(
-        c->pop[0], c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz, a[0], a[1], a[2], a[3], a[4],
-        (float)c->p.rho_r0, (float)c->p.rho_b0, (float)alpha_r, (float)alpha_b);
+    const StepArgs sa = make_args(c);  // shift weights and sizes (cur = 0)
+    InitArgs ia{c->pop[0], c->shift[0], c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz,
+                a[0], a[1], a[2], a[3], a[4], sa.rho_r0, sa.rho_b0, sa.alpha_r, sa.alpha_b};
+    if (c->p.storage == LB_STORE_FP16)
+        init_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
+    else
+        init_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
     c->launches += 1;
     LB_CUDA(cudaGetLastError());
     if (kind == LB_INIT_FIELDS && !fields_on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
@@ -504,14 +593,14 @@ lb_status lb_step(lb_ctx *c, int64_t n) {
         StepArgs a = make_args(c);
         cudaEvent_t *ev = nullptr;
         if (c->prof_used < c->prof_cap) ev = &c->prof_ev[4 * (size_t)c->prof_used++];
-        cudaError_t e = launch_step(a, c->stream, ev, &c->launches);
+        cudaError_t e = launch_step(a, c->p.storage, c->stream, ev, &c->launches);
         if (e != cudaSuccess) return cuda_fail(e, "launch_step");
         c->cur ^= 1;
         if (c->g.bc_zhi == LB_BC_CONVECTIVE) c->hcur ^= 1;
         c->step += 1;
         if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
             double m[2];
-            lb_status st = run_mass(c, c->pop[c->cur], m);
+            lb_status st = run_mass(c, m);
             if (st != LB_OK) return st;
             if (!std::isfinite(m[0]) || !std::isfinite(m[1]))
                 return fail(LB_EUNSTABLE, "non-finite colour mass at step " + std::to_string(c->step));
@@ -527,18 +616,19 @@ lb_status lb_fields(lb_ctx *c, uint32_t mask, float *const *outs, int32_t on_dev
     if (!c->initialized) return fail(LB_ESTATE, "lb_fields before lb_init/lb_load");
     if (mask >> LB_NFIELDS) return fail(LB_EINVAL, "unknown field bit in mask");
     float *dst[LB_NFIELDS] = {};
-    float *stage = c->pop[c->cur ^ 1];
+    float *stage = (float *)c->pop[c->cur ^ 1];  // the idle population buffer stages host outputs
     for (int j = 0; j < LB_NFIELDS; ++j) {
         if (!(mask & (1u << j))) continue;
         if (!outs[j]) return fail(LB_EINVAL, "outs[" + std::to_string(j) + "] is NULL but selected");
         dst[j] = on_device ? outs[j] : stage + (long long)j * c->nn;
     }
-    const double alpha_b = 8.0 / 27.0;
-    const double alpha_r = 1.0 - (1.0 - alpha_b) / (c->p.rho_r0 / c->p.rho_b0);
-    fields_kernel<<<grid_for(c->nn, 256), 256, 0, c->stream>>>(
-        c->pop[c->cur], dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], c->nn,
-        (float)(1.0 / c->p.rho_r0), (float)(1.0 / c->p.rho_b0), (float)c->p.rho_b0, (float)c->p.g[0],
-        (float)c->p.g[1], (float)c->p.g[2], (float)alpha_r, (float)alpha_b);
+    const StepArgs sa = make_args(c);
+    FieldOut fo;
+    for (int j = 0; j < LB_NFIELDS; ++j) fo.o[j] = dst[j];
+    if (c->p.storage == LB_STORE_FP16)
+        fields_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, fo, sa.gx, sa.gy, sa.gz);
+    else
+        fields_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, fo, sa.gx, sa.gy, sa.gz);
     c->launches += 1;
     LB_CUDA(cudaGetLastError());
     if (!on_device) {
@@ -552,8 +642,22 @@ lb_status lb_fields(lb_ctx *c, uint32_t mask, float *const *outs, int32_t on_dev
 lb_status lb_populations(lb_ctx *c, float *out, int32_t on_device) {
     if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
     if (!c->initialized) return fail(LB_ESTATE, "lb_populations before lb_init/lb_load");
-    LB_CUDA(cudaMemcpyAsync(out, c->pop[c->cur], (size_t)54 * c->nn * sizeof(float),
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    // decode one colour at a time (27 x nodes floats); host output is staged in the idle
+    // population buffer, which holds at least one colour in either storage
+    const StepArgs sa = make_args(c);
+    float *stage = (float *)c->pop[c->cur ^ 1];
+    const size_t cbytes = (size_t)27 * c->nn * sizeof(float);
+    for (int k = 0; k < 2; ++k) {
+        float *dst = on_device ? out + (size_t)k * 27 * c->nn : stage;
+        if (c->p.storage == LB_STORE_FP16)
+            canonical_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, k, dst);
+        else
+            canonical_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, k, dst);
+        c->launches += 1;
+        LB_CUDA(cudaGetLastError());
+        if (!on_device)
+            LB_CUDA(cudaMemcpyAsync(out + (size_t)k * 27 * c->nn, stage, cbytes, cudaMemcpyDeviceToHost, c->stream));
+    }
     if (!on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
     return LB_OK;
 }
@@ -600,7 +704,7 @@ lb_status lb_mass_noalloc(const float *pop, int64_t nodes, double *out, void *st
 lb_status lb_mass(lb_ctx *c, double out[2]) {
     if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
     if (!c->initialized) return fail(LB_ESTATE, "lb_mass before lb_init/lb_load");
-    return run_mass(c, c->pop[c->cur], out);
+    return run_mass(c, out);
 }
 
 struct SaveHeader {
@@ -610,21 +714,27 @@ struct SaveHeader {
     uint64_t pop_bytes, hist_bytes;
 };
 
+// Checkpoint layout: header, the raw current population buffer (internal storage layout),
+// for FP16 storage the shift densities paired with it, then the outflow history plane.
+static size_t shift_bytes(const lb_ctx *c) { return c->p.storage == LB_STORE_FP16 ? 8 * (size_t)c->nn : 0; }
+
 lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     if (!c || !nbytes) return fail(LB_EINVAL, "ctx and nbytes must not be NULL");
     if (!c->initialized) return fail(LB_ESTATE, "lb_save before lb_init/lb_load");
-    const size_t pb = (size_t)54 * c->nn * sizeof(float), hb = (size_t)54 * c->plane * sizeof(float);
-    const size_t total = sizeof(SaveHeader) + pb + hb;
+    const size_t pb = pop_buffer_bytes(c->nn, c->p.storage), sb = shift_bytes(c);
+    const size_t hb = (size_t)54 * c->plane * sizeof(float);
+    const size_t total = sizeof(SaveHeader) + pb + sb + hb;
     if (!buf) {
         *nbytes = total;
         return LB_OK;
     }
     if (*nbytes < total) return fail(LB_EINVAL, "checkpoint buffer too small");
-    SaveHeader h{kMagic, c->g.nx, c->g.ny, c->g.nz, c->p.storage, c->step, pb, hb};
+    SaveHeader h{kMagic, c->g.nx, c->g.ny, c->g.nz, c->p.storage, c->step, pb + sb, hb};
     std::memcpy(buf, &h, sizeof(h));
     char *p = (char *)buf + sizeof(h);
     LB_CUDA(cudaMemcpyAsync(p, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
-    LB_CUDA(cudaMemcpyAsync(p + pb, c->hist[c->hcur], hb, cudaMemcpyDeviceToHost, c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->shift[c->cur], sb, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaMemcpyAsync(p + pb + sb, c->hist[c->hcur], hb, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     *nbytes = total;
     return LB_OK;
@@ -635,15 +745,17 @@ lb_status lb_load(lb_ctx *c, const void *buf, size_t nbytes) {
     if (nbytes < sizeof(SaveHeader)) return fail(LB_EINVAL, "checkpoint too small");
     SaveHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    const size_t pb = (size_t)54 * c->nn * sizeof(float), hb = (size_t)54 * c->plane * sizeof(float);
+    const size_t pb = pop_buffer_bytes(c->nn, c->p.storage), sb = shift_bytes(c);
+    const size_t hb = (size_t)54 * c->plane * sizeof(float);
     if (h.magic != kMagic || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.storage != c->p.storage ||
-        h.pop_bytes != pb || h.hist_bytes != hb || nbytes < sizeof(h) + pb + hb)
+        h.pop_bytes != pb + sb || h.hist_bytes != hb || nbytes < sizeof(h) + pb + sb + hb)
         return fail(LB_EINVAL, "checkpoint does not match this context (grid, storage or size)");
     const char *p = (const char *)buf + sizeof(h);
     c->cur = 0;
     c->hcur = 0;
     LB_CUDA(cudaMemcpyAsync(c->pop[0], p, pb, cudaMemcpyHostToDevice, c->stream));
-    LB_CUDA(cudaMemcpyAsync(c->hist[0], p + pb, hb, cudaMemcpyHostToDevice, c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(c->shift[0], p + pb, sb, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaMemcpyAsync(c->hist[0], p + pb + sb, hb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = h.step;
     c->initialized = true;

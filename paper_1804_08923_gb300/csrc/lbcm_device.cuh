@@ -5,6 +5,7 @@
 // indices fold into immediates and the 27-vectors live in registers.
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbcm {
@@ -89,11 +90,20 @@ __device__ __forceinline__ float order_parameter(float rho_r, float rho_b, float
 
 enum { BC_PERIODIC = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_CONVECTIVE = 3 };
 
+// Population storage.  FP32: float2 pop[27][NN], (red, blue) of direction i at node n.
+// FP16: float2 rest[NN] (direction 0, FP32) followed by __half2 mov[26][NN] holding, for
+// i >= 1, h_i^k = f_i^k - rho_k(y) varphi_i(alpha_k), the deviation from the rest
+// equilibrium of the node y that stored it; rho_k(y) comes from the shift-density buffer
+// that pairs with the population buffer.
+enum { STORE_FP32 = 0, STORE_FP16 = 1 };
+
 // Everything a step kernel needs, passed by value.
 struct StepArgs {
-    const float *__restrict__ pin;   // S(t): [2][27][NN]
-    float *__restrict__ pout;        // S(t+1)
-    float *__restrict__ phase;       // post-stream phi (Eq. order) and rho = rho_r + rho_b: [2][NN]
+    const void *__restrict__ pin;       // S(t)
+    void *__restrict__ pout;            // S(t+1)
+    const float2 *__restrict__ rin;     // FP16: shift densities (rho_r, rho_b) of S(t)
+    float2 *__restrict__ rout;          // FP16: shift densities of S(t+1)
+    float2 *__restrict__ phase;         // post-stream (phi, rho) of step t+1
     const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
     float *__restrict__ hist_out;       // outflow plane f(N, t+1)
     float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]
@@ -107,9 +117,52 @@ struct StepArgs {
     float gx, gy, gz;
     float s0, s1, s2b, s3, s4, s5, s6;
     float u_in, noise_amp, xc, yc;
+    float shift_r[4], shift_b[4];       // varphi_i(alpha_k) by speed class |c|^2 = 1..3 (FP16 shift)
     unsigned long long seed;
     long long step;  // index of the step being taken (state t -> t+1 uses t)
 };
+
+// Shift weight varphi_i(alpha_k) of the FP16 encoding (same value at encode and decode).
+__device__ __forceinline__ float2 shift_w(const StepArgs &a, int i) {
+    return make_float2(a.shift_r[csq(i)], a.shift_b[csq(i)]);
+}
+
+// Populations (red, blue) of direction i stored at node src, decoded to FP32.
+template <int S>
+__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src) {
+    if constexpr (S == STORE_FP32) {
+        return __ldg(reinterpret_cast<const float2 *>(a.pin) + (size_t)i * a.NN + src);
+    } else {
+        const float2 *rest = reinterpret_cast<const float2 *>(a.pin);
+        if (i == 0) return __ldg(rest + src);
+        const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
+        const float2 h = __half22float2(__ldg(mov + (size_t)(i - 1) * a.NN + src));
+        const float2 r = __ldg(a.rin + src);
+        const float2 w = shift_w(a, i);
+        return make_float2(fmaf(r.x, w.x, h.x), fmaf(r.y, w.y, h.y));
+    }
+}
+
+// Store populations f of direction i at node n (own shift densities rho); returns the values
+// a later load_pop will decode, so the caller can account for the storage rounding.
+template <int S>
+__device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, float2 f, float2 rho) {
+    if constexpr (S == STORE_FP32) {
+        reinterpret_cast<float2 *>(a.pout)[(size_t)i * a.NN + n] = f;
+        return f;
+    } else {
+        float2 *rest = reinterpret_cast<float2 *>(a.pout);
+        if (i == 0) {
+            rest[n] = f;
+            return f;
+        }
+        const float2 w = shift_w(a, i);
+        const __half2 h = __floats2half2_rn(fmaf(-rho.x, w.x, f.x), fmaf(-rho.y, w.y, f.y));
+        reinterpret_cast<__half2 *>(rest + a.NN)[(size_t)(i - 1) * a.NN + n] = h;
+        const float2 hf = __half22float2(h);
+        return make_float2(fmaf(rho.x, w.x, hf.x), fmaf(rho.y, w.y, hf.y));
+    }
+}
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 

@@ -42,11 +42,12 @@
 namespace lbcm {
 
 // ------------------------------------------------------------------ boundary planes
+template <int S>
 __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    const long long P = a.plane, pxy = (long long)y * a.nx + x, NN = a.NN;
+    const long long P = a.plane, pxy = (long long)y * a.nx + x;
     const int N = a.nz - 1;
 
     if (a.bc_zlo == BC_INLET || a.bc_zlo == BC_FREESLIP) {
@@ -68,9 +69,9 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
                 vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
                 vb = 0.0f;
             } else {  // half-way specular reflection at z = -1/2
-                const long long src = (long long)ys * a.nx + xs;
-                vr = __ldg(a.pin + (long long)mirror_z(i) * NN + src);
-                vb = __ldg(a.pin + (long long)(27 + mirror_z(i)) * NN + src);
+                const float2 v = load_pop<S>(a, mirror_z(i), ys * a.nx + xs);
+                vr = v.x;
+                vb = v.y;
             }
             a.zin[(long long)zrank(i) * P + pxy] = vr;
             a.zin[(long long)(9 + zrank(i)) * P + pxy] = vb;
@@ -81,9 +82,9 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
         for (int i = 0; i < 27; ++i) {
             if (cz(i) != -1) continue;
             const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
-            const long long src = ((long long)N * a.ny + ys) * a.nx + xs;
-            a.zout[(long long)zrank(i) * P + pxy] = __ldg(a.pin + (long long)mirror_z(i) * NN + src);
-            a.zout[(long long)(9 + zrank(i)) * P + pxy] = __ldg(a.pin + (long long)(27 + mirror_z(i)) * NN + src);
+            const float2 v = load_pop<S>(a, mirror_z(i), (N * a.ny + ys) * a.nx + xs);
+            a.zout[(long long)zrank(i) * P + pxy] = v.x;
+            a.zout[(long long)(9 + zrank(i)) * P + pxy] = v.y;
         }
     }
     if (a.bc_zhi == BC_CONVECTIVE) {
@@ -94,9 +95,9 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny), zs = z - cz(i);
-            const long long src = ((long long)zs * a.ny + ys) * a.nx + xs;
-            fr[i] = __ldg(a.pin + (long long)i * NN + src);
-            fb[i] = __ldg(a.pin + (long long)(27 + i) * NN + src);
+            const float2 v = load_pop<S>(a, i, (zs * a.ny + ys) * a.nx + xs);
+            fr[i] = v.x;
+            fb[i] = v.y;
         }
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
@@ -146,8 +147,9 @@ struct Nbr {
 
 // Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
+template <int S>
 __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, float (&fr)[27], float (&fb)[27]) {
-    const size_t NN = (size_t)a.NN, P = (size_t)a.plane;
+    const size_t P = (size_t)a.plane;
     const int N = a.nz - 1;
     const bool periodic_z = a.bc_zlo == BC_PERIODIC;
     const bool lo = (z == 0) && !periodic_z;
@@ -170,14 +172,15 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
             fr[i] = a.zout[zrank(i) * P + nb.pxy];
             fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
         } else {
-            const int src = nb.src(i);
-            fr[i] = __ldg(a.pin + i * NN + src);
-            fb[i] = __ldg(a.pin + (27 + i) * NN + src);
+            const float2 v = load_pop<S>(a, i, nb.src(i));
+            fr[i] = v.x;
+            fb[i] = v.y;
         }
     }
 }
 
 // --------------------------------------------------------------- phase field (K_A)
+template <int S>
 __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -185,15 +188,15 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     if (x >= a.nx || y >= a.ny) return;
     const Nbr nb(a, x, y, z);
     float fr[27], fb[27];
-    gather(a, nb, z, fr, fb);
+    gather<S>(a, nb, z, fr, fb);
     float rr = 0.0f, rb = 0.0f;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         rr += fr[i];
         rb += fb[i];
     }
-    a.phase[nb.n] = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
-    a.phase[(size_t)a.NN + nb.n] = rr + rb;
+    a.phase[nb.n] = make_float2(order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0), rr + rb);
+    if constexpr (S == STORE_FP16) a.rout[nb.n] = make_float2(rr, rb);  // shift densities of S(t+1)
 }
 
 // Isotropic gradients of phi and rho (end of Section II): grad chi = 3 sum_j w_j chi(x + c_j)
@@ -204,14 +207,12 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
 __device__ __forceinline__ void stencil_gradients(const StepArgs &a, const Nbr &nb, int z, float &gpx, float &gpy,
                                                   float &gpz, float &grx, float &gry, float &grz) {
     const bool inlet_lo = z == 0 && a.bc_zlo == BC_INLET;
-    const float *__restrict__ ph_ = a.phase;
-    const float *__restrict__ rh_ = a.phase + (size_t)a.NN;
     float ph[27], rh[27];
 #pragma unroll
     for (int j = 1; j < 27; ++j) {
-        const int m = nb.nbr(j);  // ghost planes were clamped onto z = 0 / z = N (mirror)
-        ph[j] = __ldg(ph_ + m);
-        rh[j] = __ldg(rh_ + m);
+        const float2 v = __ldg(a.phase + nb.nbr(j));  // ghost planes were clamped onto z = 0 / z = N (mirror)
+        ph[j] = v.x;
+        rh[j] = v.y;
         if (cz(j) == -1 && inlet_lo) {
             if (a.disc[nb.yo[1 - cy(j)] + nb.xo[1 - cx(j)]]) {  // z = -1 inside the inlet disc
                 ph[j] = 1.0f;
@@ -250,12 +251,12 @@ __device__ __forceinline__ void sweep_inv(float &a0, float &a1, float &a2, float
 }
 
 // ------------------------- collide, perturb, recolour (K_B), any relaxation rates
+template <int S>
 __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
-    const size_t NN = (size_t)a.NN;
     const Nbr nb(a, x, y, z);
 
     // post-stream populations, colour-blind sum and densities (same order as K_A)
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     float rho_r = 0.0f, rho_b = 0.0f;
     {
         float fr[27], fb[27];
-        gather(a, nb, z, fr, fb);
+        gather<S>(a, nb, z, fr, fb);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             rho_r += fr[i];
@@ -381,15 +382,13 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
         float fs = fe + 0.5f * Fp + m[cell(i)];
         fs += pert * (wgt(i) * cgp * cgp - bcoef(i) * g2);
         const float seg = seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
-        const float vr = fmaf(frac_r, fs, seg), vb = fmaf(frac_b, fs, -seg);
-        a.pout[i * NN + n] = vr;
-        a.pout[(27 + i) * NN + n] = vb;
-        sum_r += vr;
-        sum_b += vb;
+        const float2 d = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fs, seg), fmaf(frac_b, fs, -seg)),
+                                      make_float2(rho_r, rho_b));
+        sum_r += d.x;
+        sum_b += d.y;
     }
-    // rest direction as the per-colour remainder (see collide_kernel)
-    a.pout[n] = rho_r - sum_r;
-    a.pout[27 * NN + n] = rho_b - sum_b;
+    // rest direction as the per-colour remainder (see collide_from_moments)
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(rho_r, rho_b));
 }
 
 
@@ -416,12 +415,13 @@ struct Moments {
     float rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
 };
 
+template <int S>
 __device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb, int z, Moments &m) {
     float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
     {
         float fr[27], fb[27];
-        gather(a, nb, z, fr, fb);
+        gather<S>(a, nb, z, fr, fb);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {  // same order as the phase-field kernel
             rho_r += fr[i];
@@ -451,10 +451,9 @@ __device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb,
 
 // Collision, perturbation and recolouring of one node from its moments and gradients;
 // writes the 54 post-collision populations of node n.
-template <bool kForce>
+template <bool kForce, int S>
 __device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, const Moments &mo, float gpx, float gpy,
                                                      float gpz, float grx, float gry, float grz) {
-    const size_t NN = (size_t)a.NN;
     const float rho_r = mo.rho_r, rho_b = mo.rho_b, sf = mo.sf, jx = mo.jx, jy = mo.jy, jz = mo.jz;
     const float pxx = mo.pxx, pyy = mo.pyy, pzz = mo.pzz, pxy = mo.pxy, pxz = mo.pxz, pyz = mo.pyz;
     // macroscopic quantities (Eqs. Momentum, bodyForceJet, order) and mixture parameters
@@ -544,8 +543,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, c
     const float pert = Acoef * inv_gm;
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
-    float *const pout = a.pout;
-    float sum_r = 0.0f, sum_b = 0.0f;  // moving populations written, per colour
+    float sum_r = 0.0f, sum_b = 0.0f;  // moving populations written (as read back), per colour
     // opposite pairs (i, i+1), c_{i+1} = -c_i: c.u, c.grad rho and c.grad phi change sign;
     // f^e splits into an even part (rest weight, quadratic terms, Phi) and an odd part
     // (linear and cubic terms), the perturbation is even and the recolouring flux odd.
@@ -572,25 +570,22 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, c
         const float rm = fmaf(Ax.g0[2 - X], W0[2 - Y][2 - Z], fmaf(Ax.g1[2 - X], W1[2 - Y][2 - Z], g2c(cx(i)) * W2[2 - Y][2 - Z]));
         const float fsp = (even + odd) + rp, fsm = (even - odd) + rm;
         const float seg = seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
-        const float rp_ = fmaf(frac_r, fsp, seg), bp_ = fmaf(frac_b, fsp, -seg);
-        const float rm_ = fmaf(frac_r, fsm, -seg), bm_ = fmaf(frac_b, fsm, seg);
-        pout[i * NN + n] = rp_;
-        pout[(27 + i) * NN + n] = bp_;
-        pout[(i + 1) * NN + n] = rm_;
-        pout[(28 + i) * NN + n] = bm_;
-        sum_r += rp_ + rm_;
-        sum_b += bp_ + bm_;
+        const float2 own = make_float2(rho_r, rho_b);
+        const float2 dp_ = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fsp, seg), fmaf(frac_b, fsp, -seg)), own);
+        const float2 dm_ = store_pop<S>(a, i + 1, n, make_float2(fmaf(frac_r, fsm, -seg), fmaf(frac_b, fsm, seg)), own);
+        sum_r += dp_.x + dm_.x;
+        sum_b += dp_.y + dm_.y;
     }
     // Rest direction.  In exact arithmetic the step keeps each colour's mass at this node
-    // (sum_i f_i^k* = rho_k), so the rest population is that mass minus the moving ones;
-    // this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32 rounding of the lattice
-    // constants from drifting the colour masses step after step.
-    pout[n] = rho_r - sum_r;
-    pout[27 * NN + n] = rho_b - sum_b;
+    // (sum_i f_i^k* = rho_k), so the rest population is that mass minus the moving ones as
+    // they will be read back; this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32
+    // rounding of the lattice constants and any storage rounding from drifting the colour
+    // masses step after step.
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(rho_r, rho_b));
 }
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
-template <bool kForce>
+template <bool kForce, int S>
 __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -598,35 +593,43 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     if (x >= a.nx || y >= a.ny) return;
     const Nbr nb(a, x, y, z);
     Moments mo;
-    gather_moments(a, nb, z, mo);
+    gather_moments<S>(a, nb, z, mo);
     float gpx, gpy, gpz, grx, gry, grz;
     stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
-    collide_from_moments<kForce>(a, nb.n, mo, gpx, gpy, gpz, grx, gry, grz);
+    collide_from_moments<kForce, S>(a, nb.n, mo, gpx, gpy, gpz, grx, gry, grz);
 }
 
 
 // ------------------------------------------------------------------------ launchers
-cudaError_t launch_step(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
+template <int S>
+static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
     if (ev) cudaEventRecord(ev[0], s);
     if (a.bc_zlo != BC_PERIODIC || a.bc_zhi != BC_PERIODIC) {
         dim3 b(32, 8), g((a.nx + 31) / 32, (a.ny + 7) / 8);
-        boundary_plane_kernel<<<g, b, 0, s>>>(a);
+        boundary_plane_kernel<S><<<g, b, 0, s>>>(a);
         *launches += 1;
     }
     const bool paper_rates = a.s3 == 1.0f && a.s4 == 1.0f && a.s5 == 1.0f && a.s6 == 1.0f;
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
-    if (ev) cudaEventRecord(ev[1], s);
     dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
-    phase_field_kernel<<<grd, blk, 0, s>>>(a);
+    if (ev) cudaEventRecord(ev[1], s);
+    phase_field_kernel<S><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
     if (!paper_rates)
-        collide_general_kernel<<<grd, blk, 0, s>>>(a);
+        collide_general_kernel<S><<<grd, blk, 0, s>>>(a);
     else if (force)
-        collide_kernel<true><<<grd, blk, 0, s>>>(a);
+        collide_kernel<true, S><<<grd, blk, 0, s>>>(a);
     else
-        collide_kernel<false><<<grd, blk, 0, s>>>(a);
-    *launches += 2;
+        collide_kernel<false, S><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
+    *launches += 2;
+}
+
+cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
+    if (storage == STORE_FP16)
+        launch_step_s<STORE_FP16>(a, s, ev, launches);
+    else
+        launch_step_s<STORE_FP32>(a, s, ev, launches);
     return cudaGetLastError();
 }
 

@@ -256,3 +256,68 @@ def test_host_errors(lb):
         g.init_droplet(-1.0, 4.0)
     import ctypes as C
     assert lb.library().lb_adjoint(g._ctx, 0, 10, None, None, 0) == 7
+
+
+# ------------------------------------------------------------------ FP16 storage
+# Half precision keeps 11 significant bits: a stored deviation h from the rest equilibrium
+# carries a relative rounding of 2^-12, and h is at most a fraction of w_i rho.  The bar for
+# populations after 50 steps is therefore 5e-3 of w_i max(rho_k0) (the FP32 bar is 1e-5).
+TOL16 = 5e-3
+
+
+@pytest.mark.parametrize("case", ["droplet", "two_phase", "jet"])
+def test_fp16_storage_parity(lb, case):
+    if case == "droplet":
+        shape, bc = (20, 20, 20), (0, 0)
+        params = dict(rho_r0=1.0, rho_b0=1.0, nu_r=1 / 6, nu_b=1 / 6, sigma=0.01)
+    elif case == "two_phase":
+        shape, bc = (12, 9, 40), (0, 0)
+        params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.08, sigma=0.003, g=(0.0, 0.0, 1e-5))
+    else:
+        cfg = workloads.scaled_jet("jet96", 36, 34, 40, D=10)
+        shape, bc, params = (40, 34, 36), cfg["bc"], dict(cfg["params"])
+    gpu, ref = pair(lb, shape, dict(params, storage=1), bc=bc)
+    if case == "droplet":
+        gpu.init_droplet(6.0, 4.0)
+        ref.init_droplet(6.0, 4.0)
+    elif case == "two_phase":
+        fields = workloads.random_two_phase_fields(shape, 1, 1.0, 0.5, u_amp=0.03)
+        gpu.init_fields(*fields)
+        ref.init_fields(*fields)
+    else:
+        gpu.init_jet()
+        ref.init_jet()
+    run_both(gpu, ref, 50)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL16, e.max()
+    F = gpu.fields(device=False)
+    R = ref.fields()
+    assert np.abs(F["phi"] - R["phi"]).max() < 2e-3
+    u_scale = max(np.abs(R["u"]).max(), 1e-3)
+    for d, nm in enumerate(("ux", "uy", "uz")):
+        assert np.abs(F[nm] - R["u"][d]).max() / u_scale < 2e-2
+
+
+def test_fp16_storage_conserves_colour_mass(lb):
+    """The FP32 rest population absorbs the half-precision rounding of the moving ones."""
+    shape = (24, 20, 36)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.05, sigma=0.003, storage=1)
+    gpu = lb.Lattice((36, 20, 24), params)
+    gpu.init_fields(*workloads.random_two_phase_fields(shape, 4, 1.0, 0.5))
+    m0 = gpu.mass()
+    gpu.step(1000)
+    m1 = gpu.mass()
+    assert np.all(np.abs(m1 - m0) / m0 < 2e-6), (m0, m1)
+
+
+def test_fp16_save_load_roundtrip_is_bitwise(lb):
+    cfg = workloads.scaled_jet("jet96", 32, 32, 24, D=8)
+    gpu = lb.Lattice((32, 32, 24), dict(cfg["params"], storage=1), bc=cfg["bc"])
+    gpu.init_jet()
+    gpu.step(7)
+    blob = gpu.save()
+    gpu.step(5)
+    a = gpu.populations(device=False)
+    gpu.load(blob)
+    gpu.step(5)
+    assert np.array_equal(gpu.populations(device=False), a)
