@@ -35,6 +35,31 @@ METRIC = "MLUPS & % HBM peak, FP32 vs FP16-storage at stated error; adjoint/forw
 # rho_r, rho_b; the phase-field kernel reads 54 populations and writes rho_r, rho_b.
 BYTES_STEP = 448
 BYTES_KERNEL = {"collide_kernel": 440, "phase_field_kernel": 224}
+# FP16 storage: 26 half2 (4 B) + one float2 rest (8 B) = 112 B of populations per node; the
+# phase entries are float4 (16 B).  Collide: read 112 + own phase of the previous and current
+# step 32, write 112; phase field: read 112 + own previous phase 16, write 16.
+BYTES_STEP_FP16 = 112 + 112 + 16 + 16
+BYTES_KERNEL_FP16 = {"collide_kernel": 256, "phase_field_kernel": 144}
+
+
+def fp16_error(lb, cfg, steps):
+    """FP16 against FP32 storage on the same workload after `steps` steps: relative L2 error
+    of the velocity and largest change of the order parameter."""
+    import torch
+    out = {}
+    lats = [lb.Lattice(cfg["grid"], dict(cfg["params"], storage=s), bc=cfg["bc"]) for s in (0, 1)]
+    for l in lats:
+        l.init_jet() if cfg["init"]["kind"] == "jet" else l.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
+        l.step(steps)
+    F = [l.fields(names=("phi", "ux", "uy", "uz")) for l in lats]
+    du = torch.stack([F[1][k] - F[0][k] for k in ("ux", "uy", "uz")]).double()
+    u32 = torch.stack([F[0][k] for k in ("ux", "uy", "uz")]).double()
+    out = {"steps": steps, "rel_u_l2": float(du.norm() / u32.norm()),
+           "max_abs_dphi": float((F[1]["phi"] - F[0]["phi"]).abs().max())}
+    for l in lats:
+        l.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def measured_peaks():
@@ -194,6 +219,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="jet96")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--error-steps", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     cfg = workloads.CONFIGS[args.config]
@@ -282,6 +309,42 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": f"host fields -> lb_init, {args.steps} x lb_step, lb_fields -> host (pinned)"}
 
+    # ---- FP16-shifted storage on the same workload: throughput, roofline, and error vs FP32
+    fp16 = None
+    if not args.no_fp16:
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        h = lb.Lattice(cfg["grid"], dict(cfg["params"], storage=1), bc=cfg["bc"])
+        h.init_jet() if cfg["init"]["kind"] == "jet" else h.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
+        h.step(args.warmup)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(h.stream)
+        h.step(args.steps)
+        f1.record(h.stream)
+        barrier()
+        ms16 = max_over_ranks(f0.elapsed_time(f1))
+        h.profile_enable(args.steps)
+        h.step(args.steps)
+        p16 = h.profile_read()
+        h.profile_enable(0)
+        c_ms = p16["collide_kernel"][0] / max(p16["collide_kernel"][1], 1)
+        h.close()
+        del h
+        torch.cuda.empty_cache()
+        fp16 = {"value": nodes * args.steps * world / (ms16 * 1e-3) / 1e6, "unit": "MLUPS",
+                "ms_per_step": ms16 / args.steps, "storage": "moving populations as half-precision deviations "
+                "from the reading node's rest equilibrium, rest population FP32",
+                "bytes_per_node_algorithmic": BYTES_STEP_FP16,
+                "roofline": {"bound": "hbm", "kernel": "collide_kernel<fp16>",
+                             "achieved": BYTES_KERNEL_FP16["collide_kernel"] * nodes / (c_ms * 1e-3) / 1e9,
+                             "peak": peak, "unit": "GB/s",
+                             "frac": BYTES_KERNEL_FP16["collide_kernel"] * nodes / (c_ms * 1e-3) / 1e9 / peak,
+                             "algorithmic_bytes_per_node": BYTES_KERNEL_FP16["collide_kernel"], "traffic": None},
+                "kernels": {name: {"avg_ms": t / max(n, 1), "launches": n} for name, (t, n) in p16.items() if n},
+                "error_vs_fp32": fp16_error(lb, cfg, args.error_steps)}
+
     if rank == 0:
         base = None
         if world == 1 and not args.no_cpu_baseline:
@@ -293,7 +356,7 @@ def main():
                 "bytes_per_node_algorithmic": BYTES_STEP,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
-                "fp16_storage": None, "adjoint_forward_ratio": None}
+                "fp16_storage": fp16, "adjoint_forward_ratio": None}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -110,8 +110,8 @@ struct lb_ctx {
     size_t sizes[LB_MAX_BUFFERS] = {};
     int nbufs = 0;
     void *pop[2] = {nullptr, nullptr};
-    float2 *phase = nullptr;
-    float2 *shift[2] = {nullptr, nullptr};  // FP16: shift densities paired with pop[0], pop[1]
+    float2 *phase = nullptr;               // FP32: (phi, rho) of the current step
+    float4 *ph4[2] = {nullptr, nullptr};   // FP16: (phi, rho, rho_r, rho_b) paired with pop[0], pop[1]
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -131,49 +131,68 @@ namespace lbcm {
 // f_i^k = rho_k [varphi_i(alpha_k) + w_i P(c_i.u, u^2)]  (Eq. EES per colour, Phi = 0); the
 // rest population takes each colour's remainder of the stored moving ones.
 struct InitArgs {
-    void *pop;
-    float2 *shift;
     float *hist;
     const float *fr, *fb, *fu;
     int kind, nx, ny, nz;
     float a0, a1, a2, a3, a4, rho_r0, rho_b0, alpha_r, alpha_b;
 };
 
-template <int S>
-__global__ void init_kernel(InitArgs ia, StepArgs sa) {
+__device__ __forceinline__ Nbr node_nbr(const StepArgs &a, long long n) {
+    return Nbr(a, (int)(n % a.nx), (int)((n / a.nx) % a.ny), (int)(n / a.plane));
+}
+
+// Fields (rho_r, rho_b, u) of node n of the initial state.
+__device__ __forceinline__ void init_fields_at(const InitArgs &ia, long long n, float &rr, float &rb, float &ux,
+                                               float &uy, float &uz) {
     const int nx = ia.nx, ny = ia.ny, nz = ia.nz;
     const long long NN = (long long)nx * ny * nz;
-    sa.pout = ia.pop;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    ux = uy = uz = 0.0f;
+    if (ia.kind == LB_INIT_UNIFORM) {
+        rr = ia.a0; rb = ia.a1; ux = ia.a2; uy = ia.a3; uz = ia.a4;
+    } else if (ia.kind == LB_INIT_DROPLET) {
+        // Section III: rho_r = rho_r0/2 [1 - tanh(2(r-R)/W)], rho_b = rho_b0/2 [1 + tanh(...)]
+        const float dx = x - 0.5f * (nx - 1), dy = y - 0.5f * (ny - 1), dz = z - 0.5f * (nz - 1);
+        const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float t = tanhf(2.0f * (r - ia.a0) / ia.a1);
+        rr = 0.5f * ia.rho_r0 * (1.0f - t);
+        rb = 0.5f * ia.rho_b0 * (1.0f + t);
+    } else if (ia.kind == LB_INIT_JET) {
+        rr = 0.0f; rb = ia.rho_b0;
+    } else {
+        rr = ia.fr[n]; rb = ia.fb[n]; ux = ia.fu[n]; uy = ia.fu[NN + n]; uz = ia.fu[2 * NN + n];
+    }
+}
+
+// FP16: phase entries (phi, rho, rho_r, rho_b) of the initial state, which its populations
+// are encoded for.
+__global__ void init_phase_kernel(InitArgs ia, float4 *__restrict__ ph, float inv_rho_r0, float inv_rho_b0) {
+    const long long NN = (long long)ia.nx * ia.ny * ia.nz;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
-        float rr, rb, ux = 0.0f, uy = 0.0f, uz = 0.0f;
-        if (ia.kind == LB_INIT_UNIFORM) {
-            rr = ia.a0; rb = ia.a1; ux = ia.a2; uy = ia.a3; uz = ia.a4;
-        } else if (ia.kind == LB_INIT_DROPLET) {
-            // Section III: rho_r = rho_r0/2 [1 - tanh(2(r-R)/W)], rho_b = rho_b0/2 [1 + tanh(...)]
-            const float dx = x - 0.5f * (nx - 1), dy = y - 0.5f * (ny - 1), dz = z - 0.5f * (nz - 1);
-            const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float t = tanhf(2.0f * (r - ia.a0) / ia.a1);
-            rr = 0.5f * ia.rho_r0 * (1.0f - t);
-            rb = 0.5f * ia.rho_b0 * (1.0f + t);
-        } else if (ia.kind == LB_INIT_JET) {
-            rr = 0.0f; rb = ia.rho_b0;
-        } else {
-            rr = ia.fr[n]; rb = ia.fb[n]; ux = ia.fu[n]; uy = ia.fu[NN + n]; uz = ia.fu[2 * NN + n];
-        }
-        const float2 own = make_float2(rr, rb);
-        if (S == STORE_FP16) ia.shift[n] = own;
+        float rr, rb, ux, uy, uz;
+        init_fields_at(ia, n, rr, rb, ux, uy, uz);
+        ph[n] = make_float4(order_parameter(rr, rb, inv_rho_r0, inv_rho_b0), rr + rb, rr, rb);
+    }
+}
+
+template <int S>
+__global__ void init_kernel(InitArgs ia, StepArgs sa) {
+    const long long NN = sa.NN;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+        float rr, rb, ux, uy, uz;
+        init_fields_at(ia, n, rr, rb, ux, uy, uz);
+        const Nbr nb = node_nbr(sa, n);
         const float usq = ux * ux + uy * uy + uz * uz;
         float sr = 0.0f, sb = 0.0f;
-        const bool top = z == nz - 1;
-        const long long h = (long long)y * nx + x, P = (long long)nx * ny;
+        const bool top = nb.zo[1] == (ia.nz - 1) * (int)sa.plane;
+        const long long h = nb.pxy, P = sa.plane;
 #pragma unroll
         for (int i = 1; i < 27; ++i) {
             const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
             const float pw = wgt(i) * eq_poly(cu, usq);
             const float2 f = make_float2(rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw),
                                          rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw));
-            const float2 d = store_pop<S>(sa, i, (int)n, f, own);
+            const float2 d = store_pop<S>(sa, i, (int)n, f, dest_shift<S>(sa, nb, i));
             sr += d.x;
             sb += d.y;
             if (top) {
@@ -182,7 +201,7 @@ __global__ void init_kernel(InitArgs ia, StepArgs sa) {
             }
         }
         const float2 f0 = make_float2(rr - sr, rb - sb);
-        store_pop<S>(sa, 0, (int)n, f0, own);
+        store_pop<S>(sa, 0, (int)n, f0, make_float2(0.0f, 0.0f));
         if (top) {
             ia.hist[h] = f0.x;
             ia.hist[27 * P + h] = f0.y;
@@ -199,10 +218,11 @@ template <int S>
 __global__ void fields_kernel(StepArgs sa, FieldOut fo, float gx, float gy, float gz) {
     const long long NN = sa.NN;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+        const Nbr nb = node_nbr(sa, n);
         float rr = 0.0f, rb = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            const float2 v = load_pop<S>(sa, i, (int)n);
+            const float2 v = stored_pop<S>(sa, nb, i);
             rr += v.x;
             rb += v.y;
             if (cx(i) != 0) jx += cx(i) * (v.x + v.y);
@@ -230,9 +250,10 @@ template <int S>
 __global__ void canonical_kernel(StepArgs sa, int k, float *__restrict__ out) {
     const long long NN = sa.NN;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
+        const Nbr nb = node_nbr(sa, n);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            const float2 v = load_pop<S>(sa, i, (int)n);
+            const float2 v = stored_pop<S>(sa, nb, i);
             out[(long long)i * NN + n] = k == 0 ? v.x : v.y;
         }
     }
@@ -273,9 +294,10 @@ __global__ void __launch_bounds__(kMassThreads) mass_partial_store_kernel(StepAr
     const long long n0 = blockIdx.x * per, n1 = min(NN, n0 + per);
     double acc = 0.0;
     for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+        const Nbr nb = node_nbr(sa, n);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            const float2 v = load_pop<S>(sa, i, (int)n);
+            const float2 v = stored_pop<S>(sa, nb, i);
             acc += (double)(k == 0 ? v.x : v.y);
         }
     }
@@ -330,11 +352,11 @@ lb_status setup_ctx(lb_ctx *c) {
     const size_t hist_bytes = (size_t)54 * c->plane * sizeof(float);
     c->pop[0] = c->bufs[0];
     c->pop[1] = c->bufs[1];
-    c->phase = (float2 *)c->bufs[2];
     if (c->p.storage == LB_STORE_FP16) {
-        const size_t pb = align_up(8 * (size_t)c->nn);
-        c->shift[0] = (float2 *)((char *)c->bufs[2] + pb);
-        c->shift[1] = (float2 *)((char *)c->bufs[2] + 2 * pb);
+        c->ph4[0] = (float4 *)c->bufs[2];
+        c->ph4[1] = (float4 *)((char *)c->bufs[2] + align_up(16 * (size_t)c->nn));
+    } else {
+        c->phase = (float2 *)c->bufs[2];
     }
     c->hist[0] = (float *)c->bufs[3];
     c->hist[1] = (float *)((char *)c->bufs[3] + align_up(hist_bytes));
@@ -367,9 +389,9 @@ StepArgs make_args(const lb_ctx *c) {
     StepArgs a{};
     a.pin = c->pop[c->cur];
     a.pout = c->pop[c->cur ^ 1];
-    a.rin = c->shift[c->cur];
-    a.rout = c->shift[c->cur ^ 1];
     a.phase = c->phase;
+    a.ph_prev = c->ph4[c->cur];
+    a.ph_cur = c->ph4[c->cur ^ 1];
     a.hist_in = c->hist[c->hcur];
     a.hist_out = c->hist[c->hcur ^ 1];
     a.zin = c->zin;
@@ -405,8 +427,17 @@ StepArgs make_args(const lb_ctx *c) {
 }
 
 // FP64 colour masses of the current state (store-aware first stage).
+// Step arguments describing the current state for diagnostics: pin = the current
+// populations, ph_cur = the phase entries they were encoded for (FP16).
+StepArgs state_args(const lb_ctx *c) {
+    StepArgs a = make_args(c);
+    a.ph_cur = c->ph4[c->cur];
+    a.ph_prev = c->ph4[c->cur];
+    return a;
+}
+
 lb_status run_mass(lb_ctx *c, double out[2]) {
-    const StepArgs sa = make_args(c);  // pin / rin = the current state
+    const StepArgs sa = state_args(c);
     if (c->p.storage == LB_STORE_FP16)
         mass_partial_store_kernel<STORE_FP16><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
     else
@@ -451,7 +482,7 @@ lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *
     const size_t nn = (size_t)grid->nx * grid->ny * grid->nz, plane = (size_t)grid->nx * grid->ny;
     sizes_out[0] = align_up(pop_buffer_bytes(nn, params->storage));
     sizes_out[1] = sizes_out[0];
-    sizes_out[2] = align_up(8 * nn) * (params->storage == LB_STORE_FP16 ? 3 : 1);  // phase (+ FP16 shift ping-pong)
+    sizes_out[2] = params->storage == LB_STORE_FP16 ? 2 * align_up(16 * nn) : align_up(8 * nn);  // phase field
     sizes_out[3] = 2 * align_up(54 * plane * sizeof(float));
     sizes_out[4] = aux_layout(*grid).total;
     *n_out = 5;
@@ -570,14 +601,19 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
             fr = stage; fb = stage + c->nn; fu = stage + 2 * c->nn;
         }
     }
-    const StepArgs sa = make_args(c);  // shift weights and sizes (cur = 0)
-    InitArgs ia{c->pop[0], c->shift[0], c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz,
+    StepArgs sa = make_args(c);  // cur = 0: the state is written into pop[0] / ph4[0]
+    sa.pout = c->pop[0];
+    sa.ph_cur = c->ph4[0];
+    InitArgs ia{c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz,
                 a[0], a[1], a[2], a[3], a[4], sa.rho_r0, sa.rho_b0, sa.alpha_r, sa.alpha_b};
-    if (c->p.storage == LB_STORE_FP16)
+    if (c->p.storage == LB_STORE_FP16) {
+        init_phase_kernel<<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, c->ph4[0], sa.inv_rho_r0, sa.inv_rho_b0);
         init_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
-    else
+        c->launches += 2;
+    } else {
         init_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
-    c->launches += 1;
+        c->launches += 1;
+    }
     LB_CUDA(cudaGetLastError());
     if (kind == LB_INIT_FIELDS && !fields_on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = 0;
@@ -622,7 +658,7 @@ lb_status lb_fields(lb_ctx *c, uint32_t mask, float *const *outs, int32_t on_dev
         if (!outs[j]) return fail(LB_EINVAL, "outs[" + std::to_string(j) + "] is NULL but selected");
         dst[j] = on_device ? outs[j] : stage + (long long)j * c->nn;
     }
-    const StepArgs sa = make_args(c);
+    const StepArgs sa = state_args(c);
     FieldOut fo;
     for (int j = 0; j < LB_NFIELDS; ++j) fo.o[j] = dst[j];
     if (c->p.storage == LB_STORE_FP16)
@@ -644,7 +680,7 @@ lb_status lb_populations(lb_ctx *c, float *out, int32_t on_device) {
     if (!c->initialized) return fail(LB_ESTATE, "lb_populations before lb_init/lb_load");
     // decode one colour at a time (27 x nodes floats); host output is staged in the idle
     // population buffer, which holds at least one colour in either storage
-    const StepArgs sa = make_args(c);
+    const StepArgs sa = state_args(c);
     float *stage = (float *)c->pop[c->cur ^ 1];
     const size_t cbytes = (size_t)27 * c->nn * sizeof(float);
     for (int k = 0; k < 2; ++k) {
@@ -715,8 +751,8 @@ struct SaveHeader {
 };
 
 // Checkpoint layout: header, the raw current population buffer (internal storage layout),
-// for FP16 storage the shift densities paired with it, then the outflow history plane.
-static size_t shift_bytes(const lb_ctx *c) { return c->p.storage == LB_STORE_FP16 ? 8 * (size_t)c->nn : 0; }
+// for FP16 storage the phase entries it was encoded for, then the outflow history plane.
+static size_t shift_bytes(const lb_ctx *c) { return c->p.storage == LB_STORE_FP16 ? 16 * (size_t)c->nn : 0; }
 
 lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     if (!c || !nbytes) return fail(LB_EINVAL, "ctx and nbytes must not be NULL");
@@ -733,7 +769,7 @@ lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     std::memcpy(buf, &h, sizeof(h));
     char *p = (char *)buf + sizeof(h);
     LB_CUDA(cudaMemcpyAsync(p, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
-    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->shift[c->cur], sb, cudaMemcpyDeviceToHost, c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->ph4[c->cur], sb, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaMemcpyAsync(p + pb + sb, c->hist[c->hcur], hb, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     *nbytes = total;
@@ -754,7 +790,7 @@ lb_status lb_load(lb_ctx *c, const void *buf, size_t nbytes) {
     c->cur = 0;
     c->hcur = 0;
     LB_CUDA(cudaMemcpyAsync(c->pop[0], p, pb, cudaMemcpyHostToDevice, c->stream));
-    if (sb) LB_CUDA(cudaMemcpyAsync(c->shift[0], p + pb, sb, cudaMemcpyHostToDevice, c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(c->ph4[0], p + pb, sb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaMemcpyAsync(c->hist[0], p + pb + sb, hb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = h.step;

@@ -92,18 +92,19 @@ enum { BC_PERIODIC = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_CONVECTIVE = 3 };
 
 // Population storage.  FP32: float2 pop[27][NN], (red, blue) of direction i at node n.
 // FP16: float2 rest[NN] (direction 0, FP32) followed by __half2 mov[26][NN] holding, for
-// i >= 1, h_i^k = f_i^k - rho_k(y) varphi_i(alpha_k), the deviation from the rest
-// equilibrium of the node y that stored it; rho_k(y) comes from the shift-density buffer
-// that pairs with the population buffer.
+// i >= 1, h_i^k = f_i^k - rho_k(d) varphi_i(alpha_k): the deviation from the rest
+// equilibrium of the node d = y + c_i that will read it (pull streaming), so that a node
+// decodes everything it gathers with its own colour densities.  Those come from a float4
+// (phi, rho, rho_r, rho_b) phase buffer that pairs with each population buffer.
 enum { STORE_FP32 = 0, STORE_FP16 = 1 };
 
 // Everything a step kernel needs, passed by value.
 struct StepArgs {
     const void *__restrict__ pin;       // S(t)
     void *__restrict__ pout;            // S(t+1)
-    const float2 *__restrict__ rin;     // FP16: shift densities (rho_r, rho_b) of S(t)
-    float2 *__restrict__ rout;          // FP16: shift densities of S(t+1)
-    float2 *__restrict__ phase;         // post-stream (phi, rho) of step t+1
+    float2 *__restrict__ phase;         // FP32 storage: post-stream (phi, rho) of step t+1
+    const float4 *__restrict__ ph_prev; // FP16: (phi, rho, rho_r, rho_b) that S(t) was encoded with
+    float4 *__restrict__ ph_cur;        // FP16: post-stream (phi, rho, rho_r, rho_b) of step t+1
     const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
     float *__restrict__ hist_out;       // outflow plane f(N, t+1)
     float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]
@@ -127,9 +128,10 @@ __device__ __forceinline__ float2 shift_w(const StepArgs &a, int i) {
     return make_float2(a.shift_r[csq(i)], a.shift_b[csq(i)]);
 }
 
-// Populations (red, blue) of direction i stored at node src, decoded to FP32.
+// Populations (red, blue) of direction i stored at node src, decoded to FP32; for FP16,
+// own = (rho_r, rho_b) of the reading node, the node the value was encoded for.
 template <int S>
-__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src) {
+__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, float2 own) {
     if constexpr (S == STORE_FP32) {
         return __ldg(reinterpret_cast<const float2 *>(a.pin) + (size_t)i * a.NN + src);
     } else {
@@ -137,16 +139,27 @@ __device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src) {
         if (i == 0) return __ldg(rest + src);
         const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
         const float2 h = __half22float2(__ldg(mov + (size_t)(i - 1) * a.NN + src));
-        const float2 r = __ldg(a.rin + src);
         const float2 w = shift_w(a, i);
-        return make_float2(fmaf(r.x, w.x, h.x), fmaf(r.y, w.y, h.y));
+        return make_float2(fmaf(own.x, w.x, h.x), fmaf(own.y, w.y, h.y));
     }
 }
 
-// Store populations f of direction i at node n (own shift densities rho); returns the values
-// a later load_pop will decode, so the caller can account for the storage rounding.
+// Colour densities a node decodes its gathered populations with (FP16; unused for FP32).
 template <int S>
-__device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, float2 f, float2 rho) {
+__device__ __forceinline__ float2 reader_shift(const StepArgs &a, int n) {
+    if constexpr (S == STORE_FP32) {
+        return make_float2(0.0f, 0.0f);
+    } else {
+        const float4 v = __ldg(a.ph_prev + n);
+        return make_float2(v.z, v.w);
+    }
+}
+
+// Store populations f of direction i at node n; dest = (rho_r, rho_b) of the node n + c_i
+// that will read them (FP16).  Returns the values that node will decode, so the caller can
+// account for the storage rounding.
+template <int S>
+__device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, float2 f, float2 dest) {
     if constexpr (S == STORE_FP32) {
         reinterpret_cast<float2 *>(a.pout)[(size_t)i * a.NN + n] = f;
         return f;
@@ -157,13 +170,58 @@ __device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, flo
             return f;
         }
         const float2 w = shift_w(a, i);
-        const __half2 h = __floats2half2_rn(fmaf(-rho.x, w.x, f.x), fmaf(-rho.y, w.y, f.y));
+        const __half2 h = __floats2half2_rn(fmaf(-dest.x, w.x, f.x), fmaf(-dest.y, w.y, f.y));
         reinterpret_cast<__half2 *>(rest + a.NN)[(size_t)(i - 1) * a.NN + n] = h;
         const float2 hf = __half22float2(h);
-        return make_float2(fmaf(rho.x, w.x, hf.x), fmaf(rho.y, w.y, hf.y));
+        return make_float2(fmaf(dest.x, w.x, hf.x), fmaf(dest.y, w.y, hf.y));
     }
 }
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// 32-bit offsets of the node and of its three neighbouring columns, rows and planes:
+// xo[d+1] = x - d, yo[d+1] = (y - d) nx, zo[d+1] = (z - d) nx ny for d = -1, 0, 1, wrapped
+// periodically in x and y (and z if periodic), clamped to [0, N] in z otherwise.  The pull
+// source of direction i is zo[cz+1] + yo[cy+1] + xo[cx+1]; the neighbour x + c_j is
+// zo[1-cz] + yo[1-cy] + xo[1-cx].  nx ny nz < 2^31 keeps every offset in 32 bits.
+struct Nbr {
+    int xo[3], yo[3], zo[3];
+    int n, pxy;
+    __device__ __forceinline__ Nbr(const StepArgs &a, int x, int y, int z) {
+        const bool periodic_z = a.bc_zlo == BC_PERIODIC;
+        const int N = a.nz - 1, P = (int)a.plane;
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            int zs = z - d;
+            if (periodic_z) zs = wrapi(zs, a.nz);
+            zs = min(max(zs, 0), N);
+            zo[d + 1] = zs * P;
+            yo[d + 1] = wrapi(y - d, a.ny) * a.nx;
+            xo[d + 1] = wrapi(x - d, a.nx);
+        }
+        pxy = yo[1] + x;
+        n = zo[1] + pxy;
+    }
+    __device__ __forceinline__ int src(int i) const { return zo[cz(i) + 1] + yo[cy(i) + 1] + xo[cx(i) + 1]; }
+    __device__ __forceinline__ int nbr(int j) const { return zo[1 - cz(j)] + yo[1 - cy(j)] + xo[1 - cx(j)]; }
+};
+
+// Colour densities of the node that will read direction i from node nb.n (FP16 encoding).
+template <int S>
+__device__ __forceinline__ float2 dest_shift(const StepArgs &a, const Nbr &nb, int i) {
+    if constexpr (S == STORE_FP32) {
+        return make_float2(0.0f, 0.0f);
+    } else {
+        const float4 v = __ldg(a.ph_cur + nb.nbr(i));
+        return make_float2(v.z, v.w);
+    }
+}
+
+// Populations (red, blue) of direction i stored at node nb.n, decoded (for FP16 with the
+// densities of the node that reads them; a.ph_cur must pair with a.pin).
+template <int S>
+__device__ __forceinline__ float2 stored_pop(const StepArgs &a, const Nbr &nb, int i) {
+    return load_pop<S>(a, i, nb.n, dest_shift<S>(a, nb, i));
+}
 
 }  // namespace lbcm

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
                 vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
                 vb = 0.0f;
             } else {  // half-way specular reflection at z = -1/2
-                const float2 v = load_pop<S>(a, mirror_z(i), ys * a.nx + xs);
+                const float2 v = load_pop<S>(a, mirror_z(i), ys * a.nx + xs, reader_shift<S>(a, (int)pxy));
                 vr = v.x;
                 vb = v.y;
             }
@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
         for (int i = 0; i < 27; ++i) {
             if (cz(i) != -1) continue;
             const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
-            const float2 v = load_pop<S>(a, mirror_z(i), (N * a.ny + ys) * a.nx + xs);
+            const float2 v = load_pop<S>(a, mirror_z(i), (N * a.ny + ys) * a.nx + xs,
+                                         reader_shift<S>(a, N * (int)P + (int)pxy));
             a.zout[(long long)zrank(i) * P + pxy] = v.x;
             a.zout[(long long)(9 + zrank(i)) * P + pxy] = v.y;
         }
@@ -90,12 +91,13 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
     if (a.bc_zhi == BC_CONVECTIVE) {
         // post-stream populations of node (x, y, N-1) at t+1 (N-1 >= 1: plain pulls)
         const int z = N - 1;
+        const float2 own = reader_shift<S>(a, z * (int)P + (int)pxy);
         float fr[27], fb[27];
         float rho = 0.0f, jz = 0.0f;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny), zs = z - cz(i);
-            const float2 v = load_pop<S>(a, i, (zs * a.ny + ys) * a.nx + xs);
+            const float2 v = load_pop<S>(a, i, (zs * a.ny + ys) * a.nx + xs, own);
             fr[i] = v.x;
             fb[i] = v.y;
         }
@@ -118,33 +120,6 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
     }
 }
 
-// 32-bit offsets of the node and of its three neighbouring columns, rows and planes:
-// xo[d+1] = x - d, yo[d+1] = (y - d) nx, zo[d+1] = (z - d) nx ny for d = -1, 0, 1, wrapped
-// periodically in x and y (and z if periodic), clamped to [0, N] in z otherwise.  The pull
-// source of direction i is zo[cz+1] + yo[cy+1] + xo[cx+1]; the neighbour x + c_j is
-// zo[1-cz] + yo[1-cy] + xo[1-cx].  nx ny nz < 2^31 keeps every offset in 32 bits.
-struct Nbr {
-    int xo[3], yo[3], zo[3];
-    int n, pxy;
-    __device__ __forceinline__ Nbr(const StepArgs &a, int x, int y, int z) {
-        const bool periodic_z = a.bc_zlo == BC_PERIODIC;
-        const int N = a.nz - 1, P = (int)a.plane;
-#pragma unroll
-        for (int d = -1; d <= 1; ++d) {
-            int zs = z - d;
-            if (periodic_z) zs = wrapi(zs, a.nz);
-            zs = min(max(zs, 0), N);
-            zo[d + 1] = zs * P;
-            yo[d + 1] = wrapi(y - d, a.ny) * a.nx;
-            xo[d + 1] = wrapi(x - d, a.nx);
-        }
-        pxy = yo[1] + x;
-        n = zo[1] + pxy;
-    }
-    __device__ __forceinline__ int src(int i) const { return zo[cz(i) + 1] + yo[cy(i) + 1] + xo[cx(i) + 1]; }
-    __device__ __forceinline__ int nbr(int j) const { return zo[1 - cz(j)] + yo[1 - cy(j)] + xo[1 - cx(j)]; }
-};
-
 // Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
 template <int S>
@@ -163,6 +138,7 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
         }
         return;
     }
+    const float2 own = reader_shift<S>(a, nb.n);
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         if (cz(i) == 1 && lo) {
@@ -172,7 +148,7 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
             fr[i] = a.zout[zrank(i) * P + nb.pxy];
             fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
         } else {
-            const float2 v = load_pop<S>(a, i, nb.src(i));
+            const float2 v = load_pop<S>(a, i, nb.src(i), own);
             fr[i] = v.x;
             fb[i] = v.y;
         }
@@ -195,8 +171,11 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
         rr += fr[i];
         rb += fb[i];
     }
-    a.phase[nb.n] = make_float2(order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0), rr + rb);
-    if constexpr (S == STORE_FP16) a.rout[nb.n] = make_float2(rr, rb);  // shift densities of S(t+1)
+    const float ph = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
+    if constexpr (S == STORE_FP32)
+        a.phase[nb.n] = make_float2(ph, rr + rb);
+    else
+        a.ph_cur[nb.n] = make_float4(ph, rr + rb, rr, rb);  // also the FP16 shift densities of S(t+1)
 }
 
 // Isotropic gradients of phi and rho (end of Section II): grad chi = 3 sum_j w_j chi(x + c_j)
@@ -204,15 +183,23 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
 // chi(x - c_j)), so that a uniform field gives exactly zero and nearby values subtract
 // exactly.  Ghosts: z = -1 is phi = 1, rho = rho_r0 inside the inlet disc and the mirror of
 // z = 0 elsewhere; z = N + 1 mirrors z = N.
+template <int S>
 __device__ __forceinline__ void stencil_gradients(const StepArgs &a, const Nbr &nb, int z, float &gpx, float &gpy,
                                                   float &gpz, float &grx, float &gry, float &grz) {
     const bool inlet_lo = z == 0 && a.bc_zlo == BC_INLET;
     float ph[27], rh[27];
 #pragma unroll
     for (int j = 1; j < 27; ++j) {
-        const float2 v = __ldg(a.phase + nb.nbr(j));  // ghost planes were clamped onto z = 0 / z = N (mirror)
-        ph[j] = v.x;
-        rh[j] = v.y;
+        // ghost planes were clamped onto z = 0 / z = N (mirror)
+        if constexpr (S == STORE_FP32) {
+            const float2 v = __ldg(a.phase + nb.nbr(j));
+            ph[j] = v.x;
+            rh[j] = v.y;
+        } else {
+            const float4 v = __ldg(a.ph_cur + nb.nbr(j));
+            ph[j] = v.x;
+            rh[j] = v.y;
+        }
         if (cz(j) == -1 && inlet_lo) {
             if (a.disc[nb.yo[1 - cy(j)] + nb.xo[1 - cx(j)]]) {  // z = -1 inside the inlet disc
                 ph[j] = 1.0f;
@@ -274,7 +261,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     }
 
     float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
 
     // macroscopic velocity with the Guo half-force (Eq. Momentum), body force Eq. (bodyForceJet)
     const float rho = rho_r + rho_b;
@@ -383,12 +370,12 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
         fs += pert * (wgt(i) * cgp * cgp - bcoef(i) * g2);
         const float seg = seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
         const float2 d = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fs, seg), fmaf(frac_b, fs, -seg)),
-                                      make_float2(rho_r, rho_b));
+                                      dest_shift<S>(a, nb, i));
         sum_r += d.x;
         sum_b += d.y;
     }
     // rest direction as the per-colour remainder (see collide_from_moments)
-    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(rho_r, rho_b));
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(0.0f, 0.0f));
 }
 
 
@@ -452,8 +439,9 @@ __device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb,
 // Collision, perturbation and recolouring of one node from its moments and gradients;
 // writes the 54 post-collision populations of node n.
 template <bool kForce, int S>
-__device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, const Moments &mo, float gpx, float gpy,
-                                                     float gpz, float grx, float gry, float grz) {
+__device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nbr &nb, const Moments &mo, float gpx,
+                                                     float gpy, float gpz, float grx, float gry, float grz) {
+    const int n = nb.n;
     const float rho_r = mo.rho_r, rho_b = mo.rho_b, sf = mo.sf, jx = mo.jx, jy = mo.jy, jz = mo.jz;
     const float pxx = mo.pxx, pyy = mo.pyy, pzz = mo.pzz, pxy = mo.pxy, pxz = mo.pxz, pyz = mo.pyz;
     // macroscopic quantities (Eqs. Momentum, bodyForceJet, order) and mixture parameters
@@ -570,9 +558,10 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, c
         const float rm = fmaf(Ax.g0[2 - X], W0[2 - Y][2 - Z], fmaf(Ax.g1[2 - X], W1[2 - Y][2 - Z], g2c(cx(i)) * W2[2 - Y][2 - Z]));
         const float fsp = (even + odd) + rp, fsm = (even - odd) + rm;
         const float seg = seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
-        const float2 own = make_float2(rho_r, rho_b);
-        const float2 dp_ = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fsp, seg), fmaf(frac_b, fsp, -seg)), own);
-        const float2 dm_ = store_pop<S>(a, i + 1, n, make_float2(fmaf(frac_r, fsm, -seg), fmaf(frac_b, fsm, seg)), own);
+        const float2 dp_ = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fsp, seg), fmaf(frac_b, fsp, -seg)),
+                                        dest_shift<S>(a, nb, i));
+        const float2 dm_ = store_pop<S>(a, i + 1, n, make_float2(fmaf(frac_r, fsm, -seg), fmaf(frac_b, fsm, seg)),
+                                        dest_shift<S>(a, nb, i + 1));
         sum_r += dp_.x + dm_.x;
         sum_b += dp_.y + dm_.y;
     }
@@ -581,12 +570,12 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, int n, c
     // they will be read back; this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32
     // rounding of the lattice constants and any storage rounding from drifting the colour
     // masses step after step.
-    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(rho_r, rho_b));
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(0.0f, 0.0f));
 }
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
 template <bool kForce, int S>
-__global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
+__global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -595,8 +584,8 @@ __global__ void __launch_bounds__(128, 6) collide_kernel(StepArgs a) {
     Moments mo;
     gather_moments<S>(a, nb, z, mo);
     float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
-    collide_from_moments<kForce, S>(a, nb.n, mo, gpx, gpy, gpz, grx, gry, grz);
+    stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    collide_from_moments<kForce, S>(a, nb, mo, gpx, gpy, gpz, grx, gry, grz);
 }
 
 
