@@ -203,6 +203,21 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def reduce_max(v, dist, device):
+    """Largest value over the ranks (the slowest rank times the job); identity without a group."""
+    if dist is None or not dist.is_initialized():
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank, steps, world, ms_max):
+    """Whole-job throughput: every rank advances its own lattice (replicas, weak scaling)."""
+    return nodes_per_rank * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def config_block(cfg):
     nx, ny, nz = cfg["grid"]
     return {"workload": f"{cfg['name']}: {cfg['text']}", "lattice": [nx, ny, nz], "nodes": nx * ny * nz,
@@ -251,11 +266,7 @@ def main():
             torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, "cuda")
 
     # ---- warm-up, then the timed region (device events on the library's stream)
     lat.step(args.warmup)
@@ -270,7 +281,7 @@ def main():
     launches = lat.kernel_launches - l0
     ms = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms / args.steps
-    value = nodes * args.steps * world / (ms * 1e-3) / 1e6
+    value = job_mlups(nodes, args.steps, world, ms)
     clocks = clk.summary()
 
     # ---- per-kernel durations over a second timed pass of the same length
