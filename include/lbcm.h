@@ -87,6 +87,10 @@ typedef struct {
     double eps_grad;        /* regulariser: |grad phi| -> sqrt(|grad phi|^2 + eps^2) */
     int32_t storage;        /* lb_storage */
     int32_t check_every;    /* every so many steps lb_step checks the colour masses (0 = never) */
+    double fourier[16];     /* inlet profile u_z = u_in [1 + sum_{m=1..8} (a_m cos m theta + b_m sin m theta)],
+                               theta the polar angle of the inlet column about the disc centre;
+                               stored a_1, b_1, ..., a_8, b_8 (not in the paper: the parameters the
+                               adjoint differentiates); all 0 = the paper's uniform inlet */
 } lb_params;
 
 /* Fills *p with the paper's defaults: rho_r0 = rho_b0 = 1, nu = 1/6, sigma = 0, beta = 0.7,

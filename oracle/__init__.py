@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("s0", C.c_double), ("s1", C.c_double), ("s2b", C.c_double),
                 ("s3", C.c_double), ("s4", C.c_double), ("s5", C.c_double), ("s6", C.c_double),
                 ("u_in", C.c_double), ("d_in", C.c_double), ("noise_amp", C.c_double),
-                ("seed", C.c_uint64), ("eps_grad", C.c_double), ("alpha_b", C.c_double)]
+                ("seed", C.c_uint64), ("eps_grad", C.c_double), ("alpha_b", C.c_double),
+                ("fourier", C.c_double * 16)]
 
 
 def build(force: bool = False) -> str:
@@ -194,6 +195,9 @@ def make_params(d: dict) -> Params:
     p.seed = d.get("seed", 0)
     p.eps_grad = d.get("eps_grad", 1e-6)
     p.alpha_b = d.get("alpha_b", 8.0 / 27.0)
+    fr = list(d.get("fourier", ())) + [0.0] * 16
+    for m in range(16):
+        p.fourier[m] = fr[m]
     return p
 
 

@@ -50,6 +50,9 @@
  *       mirror of z = 0 elsewhere (or on a free-slip wall); z = N + 1 mirrors z = N.
  *   R10 Initial populations from fields (rho_r, rho_b, u):
  *       f_i^k = rho_k [varphi_i(alpha_k) + w_i(3 cu + 9/2 cu^2 - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2)].
+ *   R11 Inlet profile (not in the paper, whose inlet is uniform; the parameters the
+ *       adjoint differentiates): u_z = u_j0 [1 + sum_{m=1..8} (a_m cos m theta + b_m sin m theta)]
+ *       with theta the polar angle of the source column about the disc centre (0 at the centre).
  */
 #include <math.h>
 #include <stdint.h>
@@ -82,6 +85,7 @@ typedef struct {
     uint64_t seed;               /* inlet noise seed */
     double eps_grad;             /* |grad phi| regulariser (R3) */
     double alpha_b;              /* 8/27 in the paper */
+    double fourier[16];          /* inlet profile: a_1, b_1, ..., a_8, b_8 (R11) */
 } orc_params;
 
 static double weight(int i) {
@@ -352,7 +356,10 @@ static void inlet_velocity(const orc_grid *g, const orc_params *p, int64_t step,
     double a = p->noise_amp * p->u_in * xi;
     u[0] = r > 0.0 ? a * rx / r : 0.0;
     u[1] = r > 0.0 ? a * ry / r : 0.0;
-    u[2] = p->u_in;
+    double theta = atan2(ry, rx), prof = 1.0;
+    for (int m = 1; m <= 8; ++m)
+        prof += p->fourier[2 * (m - 1)] * cos(m * theta) + p->fourier[2 * m - 1] * sin(m * theta);
+    u[2] = p->u_in * prof;
 }
 
 static double alpha_red(const orc_params *p) {

@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("s4", C.c_double), ("s5", C.c_double), ("s6", C.c_double),
                 ("u_in", C.c_double), ("d_in", C.c_double), ("noise_amp", C.c_double),
                 ("seed", C.c_uint64), ("eps_grad", C.c_double), ("storage", C.c_int32),
-                ("check_every", C.c_int32)]
+                ("check_every", C.c_int32), ("fourier", C.c_double * 16)]
 
 
 _lock = threading.Lock()
@@ -110,6 +110,10 @@ def make_params(d: dict) -> Params:
     for k, v in d.items():
         if k == "g":
             p.g[0], p.g[1], p.g[2] = v
+        elif k == "fourier":
+            vals = list(v) + [0.0] * 16
+            for m in range(16):
+                p.fourier[m] = float(vals[m])
         elif k in ("seed", "storage", "check_every"):
             setattr(p, k, int(v))
         elif k in dict(Params._fields_):

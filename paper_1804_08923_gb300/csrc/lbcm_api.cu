@@ -93,6 +93,8 @@ lb_status validate(const lb_grid *g, const lb_params *p) {
     if (g->bc_zlo == LB_BC_INLET) {
         if (!(p->d_in >= 0) || !std::isfinite(p->d_in) || !std::isfinite(p->u_in) || !std::isfinite(p->noise_amp))
             return fail(LB_EINVAL, "inlet parameters must be finite, d_in >= 0");
+        for (int m = 0; m < 16; ++m)
+            if (!std::isfinite(p->fourier[m])) return fail(LB_EINVAL, "inlet profile coefficients must be finite");
     }
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return fail(LB_EINVAL, "gravity must be finite");
@@ -421,6 +423,7 @@ StepArgs make_args(const lb_ctx *c) {
         a.shift_r[q] = (float)(kq[q] * (1.0 - alpha_r));
         a.shift_b[q] = (float)(kq[q] * (1.0 - alpha_b));
     }
+    for (int m = 0; m < 16; ++m) a.fourier[m] = (float)p.fourier[m];
     a.seed = p.seed;
     a.step = c->step;
     return a;

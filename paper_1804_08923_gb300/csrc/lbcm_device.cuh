@@ -82,6 +82,35 @@ __host__ __device__ __forceinline__ float inlet_xi(unsigned long long seed, long
     return (float)(unsigned int)(h >> 40) * (1.0f / 8388608.0f) - 1.0f;
 }
 
+// Inlet velocity at source column (xs, ys) of the disc: plug u_in times the Fourier profile
+// 1 + sum_m (a_m cos m theta + b_m sin m theta) along z, plus the radial noise a u_in xi rhat.
+// cos m theta, sin m theta come from the angle-addition recurrence on the unit offset.
+struct InletVel {
+    float ux, uy, uz;
+    float cm[9], sm[9];  // cos m theta, sin m theta for m = 0..8
+};
+
+__device__ __forceinline__ void inlet_velocity(float u_in, float noise_amp, const float *fourier, float xc, float yc,
+                                               unsigned long long seed, long long step, int xs, int ys, int nx, int ny,
+                                               InletVel &v) {
+    const float rx = (float)xs - xc, ry = (float)ys - yc;
+    const float r = sqrtf(rx * rx + ry * ry);
+    const float c1 = r > 0.0f ? rx / r : 1.0f, s1 = r > 0.0f ? ry / r : 0.0f;
+    const float amp = noise_amp * u_in * inlet_xi(seed, step, xs, ys, nx, ny);
+    v.ux = r > 0.0f ? amp * rx / r : 0.0f;
+    v.uy = r > 0.0f ? amp * ry / r : 0.0f;
+    v.cm[0] = 1.0f;
+    v.sm[0] = 0.0f;
+    float prof = 1.0f;
+#pragma unroll
+    for (int m = 1; m <= 8; ++m) {
+        v.cm[m] = v.cm[m - 1] * c1 - v.sm[m - 1] * s1;
+        v.sm[m] = v.sm[m - 1] * c1 + v.cm[m - 1] * s1;
+        prof = fmaf(fourier[2 * (m - 1)], v.cm[m], fmaf(fourier[2 * m - 1], v.sm[m], prof));
+    }
+    v.uz = u_in * prof;
+}
+
 // Order parameter of Eq. (order) from the colour densities (1/rho_k0 given).
 __device__ __forceinline__ float order_parameter(float rho_r, float rho_b, float inv_rho_r0, float inv_rho_b0) {
     const float A = rho_r * inv_rho_r0, B = rho_b * inv_rho_b0;
@@ -119,6 +148,7 @@ struct StepArgs {
     float s0, s1, s2b, s3, s4, s5, s6;
     float u_in, noise_amp, xc, yc;
     float shift_r[4], shift_b[4];       // varphi_i(alpha_k) by speed class |c|^2 = 1..3 (FP16 shift)
+    float fourier[16];                  // inlet profile coefficients a_1, b_1, ..., a_8, b_8
     unsigned long long seed;
     long long step;  // index of the step being taken (state t -> t+1 uses t)
 };

@@ -58,12 +58,9 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
             float vr, vb;
             if (a.bc_zlo == BC_INLET && a.disc[(long long)ys * a.nx + xs]) {
                 // red equilibrium f^e(rho_r0, u_in) with alpha_r and Phi = 0, no blue
-                const float rx = (float)xs - a.xc, ry = (float)ys - a.yc;
-                const float r = sqrtf(rx * rx + ry * ry);
-                const float amp = a.noise_amp * a.u_in * inlet_xi(a.seed, a.step, xs, ys, a.nx, a.ny);
-                const float ux = r > 0.0f ? amp * rx / r : 0.0f;
-                const float uy = r > 0.0f ? amp * ry / r : 0.0f;
-                const float uz = a.u_in;
+                InletVel iv;
+                inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
+                const float ux = iv.ux, uy = iv.uy, uz = iv.uz;
                 const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
                 const float usq = ux * ux + uy * uy + uz * uz;
                 vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));

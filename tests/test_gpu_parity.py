@@ -111,6 +111,22 @@ def test_small_jet_parity(lb):
     assert gpu.fields(device=False)["rho_r"].sum() > 0.5  # red has entered
 
 
+def test_jet_inlet_profile_parity(lb):
+    """Inlet with a nonuniform profile 1 + sum_m (a_m cos m theta + b_m sin m theta) over all
+    eight modes (the parameters the adjoint differentiates), 40 steps."""
+    cfg = workloads.scaled_jet("jet96", 28, 26, 30, D=12)
+    params = dict(cfg["params"])
+    rng = np.random.default_rng(11)
+    params["fourier"] = tuple(0.15 * rng.standard_normal(16) / np.repeat(np.arange(1, 9), 2))
+    shape = (30, 26, 28)
+    gpu, ref = pair(lb, shape, params, bc=cfg["bc"])
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 40)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
 def test_jet_with_gravity_parity(lb):
     """High-Re jet parameters (tau -> 0.5000384) with gravity along +z, 40 steps."""
     cfg = workloads.scaled_jet("jet256", 24, 24, 32, D=8)

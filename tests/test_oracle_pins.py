@@ -373,6 +373,37 @@ def test_inlet_populations_are_red_equilibrium():
     assert checked > 20
 
 
+@pytest.mark.parametrize("m,kind", [(1, "cos"), (3, "sin"), (8, "cos")])
+def test_inlet_fourier_profile(m, kind):
+    """A single inlet mode: u_z at source column (dx, dy) is u_j0 (1 + a Re or Im of
+    ((dx + i dy)/r)^m), the m-th harmonic of the polar angle written as a complex power; at
+    the disc centre (r = 0) the angle is taken as 0."""
+    nx = ny = 9
+    shape = (3, ny, nx)
+    uj, amp, D = 0.04, 0.3, 7.0
+    four = [0.0] * 16
+    four[2 * (m - 1) + (kind == "sin")] = amp
+    lat = make_lattice(shape, bc=(oracle.BC_INLET, oracle.BC_CONVECTIVE), rho_b0=0.5,
+                       u_in=uj, d_in=D, noise_amp=0.0, fourier=four)
+    lat.init_jet()
+    f, _ = lat.stream()
+    alpha_r = 1 - (1 - 8 / 27) / 2.0
+    i = int(np.where((C[:, 0] == 0) & (C[:, 1] == 0) & (C[:, 2] == 1))[0][0])
+    seen = set()
+    for y in range(ny):
+        for x in range(nx):
+            dx, dy = x - (nx - 1) / 2, y - (ny - 1) / 2
+            if (2 * dx) ** 2 + (2 * dy) ** 2 >= D * D:
+                continue
+            z = complex(dx, dy)
+            h = (z / abs(z)) ** m if abs(z) > 0 else 1.0 + 0j
+            uz = uj * (1 + amp * (h.real if kind == "cos" else h.imag))
+            fe = oracle.equilibrium(1.0, np.array([0.0, 0.0, uz]), alpha_r, 0.1, [0, 0, 0])
+            assert abs(f[0, i, 0, y, x] - fe[i]) < 1e-15
+            seen.add(round(uz, 12))
+    assert len(seen) >= 2  # the profile really varies over the disc
+
+
 # --------------------------------------------------------------------------- physics
 @pytest.mark.parametrize("gamma,nu,tol", [(1.0, 1 / 6, 1e-4), (2.0, 1 / 6, 1e-4), (1.0, 0.05, 0.01), (8.0, 0.02, 0.01)])
 def test_shear_wave_decay_gives_viscosity(gamma, nu, tol):
