@@ -202,11 +202,41 @@ LB_API lb_status lb_profile_read(lb_ctx *ctx, double *ms, int64_t *launches, int
 /* Total number of kernels this context has launched since creation. */
 LB_API int64_t lb_kernel_launches(const lb_ctx *ctx);
 
-/* Discrete adjoint of lb_step (gradient of an objective at step T with respect to
- * inlet velocity, sigma, viscosity and inlet profile).  Not provided by this build:
- * returns LB_ENOTIMPL. */
+/* Replaces the parameters of an existing context (same grid and storage; the state is kept).
+ * Validated like lb_create; LB_EINVAL leaves the context unchanged. */
+LB_API lb_status lb_set_params(lb_ctx *ctx, const lb_params *params);
+
+/* ---------------------------------------------------------------- discrete adjoint
+ * Gradient of an objective J(S(T)) of the state T steps ahead with respect to the inlet
+ * velocity u_in, sigma, nu_r, nu_b and the 16 inlet profile coefficients (not in the paper:
+ * reverse-mode differentiation of the step of Section II with the boundaries of Section
+ * IV.A, transposed by hand).  The forward pass runs T steps from the context's state,
+ * keeping a checkpoint every k steps; the reverse pass recomputes each k-step segment from
+ * its checkpoint and steps back through it, so device memory holds about T/k + k states.
+ * Adjoint arithmetic is FP32, parameter gradients are accumulated in FP64.
+ *
+ * objective:
+ *   LB_OBJ_INTERFACE_AREA  J = sum over nodes with 1 <= z <= nz-2 of sqrt(|grad phi|^2 + eps^2),
+ *                          grad phi the isotropic stencil of the order parameter (Eq. order) of
+ *                          rho_k = sum_i S_i^k; obj_args[0] = eps > 0.
+ *   LB_OBJ_PENETRATION     J = delta log sum_n H(phi_n) exp(z_n / delta), H(phi) = ((1 + phi)/2)^2,
+ *                          a smooth maximum of z over the red region (H = 1 in pure red, 0 in
+ *                          pure blue); obj_args[0] = delta > 0.
+ * obj_args[1] and obj_args[3] unused (0); obj_args[2] = checkpoint interval k (0: ceil(sqrt(T))).
+ * grad_out (n_grad >= LB_ADJ_NOUT doubles): [0] J, [1] dJ/du_in, [2] dJ/dsigma, [3] dJ/dnu_r,
+ *   [4] dJ/dnu_b, [5 + 2(m-1)] dJ/da_m, [6 + 2(m-1)] dJ/db_m for m = 1..8.
+ * On return the context holds S(T) (as after lb_step(T)).  Requires FP32 storage and
+ * s3 = s4 = s5 = s6 = 1 (LB_EINVAL otherwise); LB_ENOMEM if the workspace cannot be had. */
+enum { LB_OBJ_INTERFACE_AREA = 0, LB_OBJ_PENETRATION = 1 };
+#define LB_ADJ_NARGS 4
+#define LB_ADJ_NOUT 21
 LB_API lb_status lb_adjoint(lb_ctx *ctx, int32_t objective, int64_t T, const double *obj_args,
-                     double *grad_out, int32_t n_grad);
+                            double *grad_out, int32_t n_grad);
+
+/* dJ/dS(t0) of the last lb_adjoint, S(t0) the state it started from (the outflow history
+ * held fixed), as 54 nx ny nz floats in the canonical layout [k][i][z][y][x].  out is device
+ * memory if on_device, else host memory.  LB_ESTATE without a preceding lb_adjoint. */
+LB_API lb_status lb_adjoint_state(lb_ctx *ctx, float *out, int32_t on_device);
 
 /* Message for the last failing call made by this thread ("" if none). */
 LB_API const char *lb_last_error(void);

@@ -87,6 +87,8 @@ def lib():
         L.orc_droplet_fields.argtypes = [gp, pp, C.c_double, C.c_double, dp, dp]
         L.orc_fields.argtypes = [gp, pp, dp, dp, dp, dp, dp, dp]
         L.orc_mass.argtypes = [gp, dp, dp]
+        L.orc_objective.argtypes = [gp, pp, dp, C.c_int, dp]
+        L.orc_objective.restype = C.c_double
         L.orc_velocity_set.argtypes = [C.POINTER(C.c_int32)]
         L.orc_weights.argtypes = [dp]
         L.orc_num_threads.restype = C.c_int
@@ -267,3 +269,11 @@ class Lattice:
         out = np.zeros(2)
         lib().orc_mass(C.byref(self.g), _p(self.S), _p(out))
         return out
+
+    def objective(self, kind: str, args=(1e-3,)):
+        """Adjoint objective of the current state (reading R12): "area" (args = eps) or
+        "penetration" (args = delta)."""
+        a = np.zeros(4)
+        a[: len(args)] = args
+        k = {"area": 0, "penetration": 1}[kind]
+        return float(lib().orc_objective(C.byref(self.g), C.byref(self.p), _p(self.S), k, _p(a)))

@@ -53,6 +53,12 @@
  *   R11 Inlet profile (not in the paper, whose inlet is uniform; the parameters the
  *       adjoint differentiates): u_z = u_j0 [1 + sum_{m=1..8} (a_m cos m theta + b_m sin m theta)]
  *       with theta the polar angle of the source column about the disc centre (0 at the centre).
+ *   R12 Objectives of the adjoint (not in the paper), on the order parameter phi of a state's
+ *       colour densities rho_k = sum_i S_i^k: the interface area sum of sqrt(|grad phi|^2 + eps^2)
+ *       over 1 <= z <= nz-2 (isotropic stencil, x and y periodic), and the penetration length
+ *       as a smooth maximum, delta log sum_n H(phi_n) exp(z_n / delta), with the redness weight
+ *       H = ((1 + phi)/2)^2: 1 in pure red, 0 in pure blue (no tail that the exponential weight
+ *       of distant blue nodes would amplify), smooth in between.
  */
 #include <math.h>
 #include <stdint.h>
@@ -630,4 +636,44 @@ void orc_mass(const orc_grid *g, const double *S, double *out) {
             }
         out[k] = s + c;
     }
+}
+
+/* ------------------------------------------------------ adjoint objectives (R12) */
+double orc_objective(const orc_grid *g, const orc_params *p, const double *S, int kind, const double *args) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const size_t nn = (size_t)nx * ny * nz;
+    double *phi = (double *)malloc(sizeof(double) * nn);
+    if (!phi) return NAN;
+    for (size_t n = 0; n < nn; ++n) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 27; ++i) { a += S[pidx(g, 0, i, n)]; b += S[pidx(g, 1, i, n)]; }
+        phi[n] = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
+    }
+    double J = 0.0;
+    if (kind == 0) {
+        double eps = args[0];
+        for (int z = 1; z <= nz - 2; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    double gr[3] = {0, 0, 0};
+                    for (int j = 0; j < 27; ++j) {
+                        double v = phi[nidx(g, wrap(x + CX[j], nx), wrap(y + CY[j], ny), z + CZ[j])];
+                        gr[0] += 3.0 * weight(j) * CX[j] * v;
+                        gr[1] += 3.0 * weight(j) * CY[j] * v;
+                        gr[2] += 3.0 * weight(j) * CZ[j] * v;
+                    }
+                    J += sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+                }
+    } else {
+        double delta = args[0], N = nz - 1, sum = 0.0;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    double h = 0.5 * (1.0 + phi[nidx(g, x, y, z)]), H = h * h;
+                    sum += H * exp((z - N) / delta);
+                }
+        J = N + delta * log(sum);
+    }
+    free(phi);
+    return J;
 }

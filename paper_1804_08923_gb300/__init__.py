@@ -18,7 +18,11 @@ from ._abi import (BC_CONVECTIVE, BC_FREESLIP, BC_INLET, BC_PERIODIC, FIELD_NAME
                    INIT_JET, INIT_UNIFORM, LBError, library, make_grid, make_params)
 
 __all__ = ["Lattice", "LBError", "library", "make_grid", "make_params", "BC_PERIODIC", "BC_FREESLIP",
-           "BC_INLET", "BC_CONVECTIVE", "FIELD_NAMES"]
+           "BC_INLET", "BC_CONVECTIVE", "FIELD_NAMES", "GRAD_NAMES", "OBJECTIVES"]
+
+# order of the gradient entries lb_adjoint returns after J
+GRAD_NAMES = ("u_in", "sigma", "nu_r", "nu_b") + tuple(f"{ab}{m}" for m in range(1, 9) for ab in "ab")
+OBJECTIVES = {"area": 0, "penetration": 1}
 
 
 def _torch():
@@ -44,6 +48,7 @@ class Lattice:
         self.shape = (self.nz, self.ny, self.nx)
         self.nodes = self.nx * self.ny * self.nz
         self._g = make_grid(self.nx, self.ny, self.nz, *bc)
+        self.params = dict(params)
         self._p = make_params(params)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -178,6 +183,38 @@ class Lattice:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.lb_kernel_launches(self._ctx))
+
+    # ------------------------------------------------------------------ parameters, adjoint
+    def set_params(self, **changes):
+        """Changes lb_params fields of the context (grid, storage and state are kept)."""
+        params = dict(self.params)
+        params.update(changes)
+        p = make_params(params)
+        _abi.check(self.lib.lb_set_params(self._ctx, C.byref(p)))
+        self.params, self._p = params, p
+
+    def adjoint(self, T: int, objective: str = "area", args=(1e-3,), checkpoint: int = 0):
+        """Runs T steps and returns (J, grad): J the objective of the state T steps ahead and
+        grad (float64, 20) its gradient w.r.t. GRAD_NAMES.  checkpoint = segment length
+        (0: ceil(sqrt(T)))."""
+        a = list(args)[:2] + [0.0] * (2 - len(list(args)[:2]))
+        obj_args = (C.c_double * 4)(a[0], a[1], float(checkpoint), 0.0)
+        out = (C.c_double * _abi.ADJ_NOUT)()
+        _abi.check(self.lib.lb_adjoint(self._ctx, C.c_int32(OBJECTIVES[objective]), C.c_int64(int(T)), obj_args,
+                                       out, C.c_int32(_abi.ADJ_NOUT)))
+        return float(out[0]), np.array(out[1:], dtype=np.float64)
+
+    def adjoint_state(self, device=False):
+        """dJ/dS of the state the last adjoint started from, shape (2, 27, nz, ny, nx), float32."""
+        torch = _torch()
+        shp = (2, 27) + self.shape
+        if device:
+            t = torch.empty(shp, dtype=torch.float32, device=self.device)
+            _abi.check(self.lib.lb_adjoint_state(self._ctx, C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_float)), 1))
+            return t
+        a = np.empty(shp, dtype=np.float32)
+        _abi.check(self.lib.lb_adjoint_state(self._ctx, a.ctypes.data_as(C.POINTER(C.c_float)), 0))
+        return a
 
     def load(self, blob: bytes):
         _abi.check(self.lib.lb_load(self._ctx, blob, C.c_size_t(len(blob))))

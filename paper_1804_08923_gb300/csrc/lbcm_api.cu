@@ -125,6 +125,20 @@ struct lb_ctx {
     long long launches = 0;
     std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded step
     int prof_cap = 0, prof_used = 0;
+    // discrete-adjoint workspace (one device allocation, grown on demand)
+    struct {
+        void *base = nullptr;
+        size_t bytes = 0;
+        float2 *ckpt_pop = nullptr, *seg_pop = nullptr, *seg_phase = nullptr, *lp[2] = {}, *lr[2] = {}, *lgb = nullptr,
+               *objph = nullptr;
+        float *ckpt_hist = nullptr, *seg_zin = nullptr, *seg_zout = nullptr, *seg_hist = nullptr, *lc = nullptr,
+              *li = nullptr, *lh[2] = {};
+        float4 *lga = nullptr;
+        double *acc_coll = nullptr, *acc_inlet = nullptr, *acc_obj = nullptr, *out = nullptr;
+        long long nblk_coll = 0, nblk_inlet = 0;
+        int cl = 0;
+        bool valid = false;
+    } adj;
 };
 
 namespace lbcm {
@@ -347,6 +361,26 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double *g_noalloc_addr[kMaxDevices] = {};
 
+// Inlet disc membership for the current d_in, and cleared boundary planes.
+lb_status upload_disc(lb_ctx *c) {
+    const lb_grid &g = c->g;
+    // inlet disc membership, decided in FP64 on the host:
+    // (2x - (nx-1))^2 + (2y - (ny-1))^2 < D^2  <=>  (x - x_c)^2 + (y - y_c)^2 < (D/2)^2
+    std::vector<uint8_t> disc((size_t)c->plane, 0);
+    if (g.bc_zlo == LB_BC_INLET) {
+        for (int y = 0; y < g.ny; ++y)
+            for (int x = 0; x < g.nx; ++x) {
+                const double dx = 2.0 * x - (g.nx - 1), dy = 2.0 * y - (g.ny - 1);
+                disc[(size_t)y * g.nx + x] = dx * dx + dy * dy < c->p.d_in * c->p.d_in;
+            }
+    }
+    LB_CUDA(cudaMemcpyAsync(c->disc, disc.data(), disc.size(), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaMemsetAsync(c->zin, 0, 18 * c->plane * sizeof(float), c->stream));
+    LB_CUDA(cudaMemsetAsync(c->zout, 0, 18 * c->plane * sizeof(float), c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
 lb_status setup_ctx(lb_ctx *c) {
     const lb_grid &g = c->g;
     c->nn = (long long)g.nx * g.ny * g.nz;
@@ -368,21 +402,7 @@ lb_status setup_ctx(lb_ctx *c) {
     c->zin = (float *)(aux + L.zin);
     c->zout = (float *)(aux + L.zout);
     c->partial = (double *)(aux + L.partial);
-    // inlet disc membership, decided in FP64 on the host:
-    // (2x - (nx-1))^2 + (2y - (ny-1))^2 < D^2  <=>  (x - x_c)^2 + (y - y_c)^2 < (D/2)^2
-    std::vector<uint8_t> disc((size_t)c->plane, 0);
-    if (g.bc_zlo == LB_BC_INLET) {
-        for (int y = 0; y < g.ny; ++y)
-            for (int x = 0; x < g.nx; ++x) {
-                const double dx = 2.0 * x - (g.nx - 1), dy = 2.0 * y - (g.ny - 1);
-                disc[(size_t)y * g.nx + x] = dx * dx + dy * dy < c->p.d_in * c->p.d_in;
-            }
-    }
-    LB_CUDA(cudaMemcpyAsync(c->disc, disc.data(), disc.size(), cudaMemcpyHostToDevice, c->stream));
-    LB_CUDA(cudaMemsetAsync(c->zin, 0, 18 * c->plane * sizeof(float), c->stream));
-    LB_CUDA(cudaMemsetAsync(c->zout, 0, 18 * c->plane * sizeof(float), c->stream));
-    LB_CUDA(cudaStreamSynchronize(c->stream));
-    return LB_OK;
+    return upload_disc(c);
 }
 
 StepArgs make_args(const lb_ctx *c) {
@@ -559,10 +579,21 @@ static void free_profile(lb_ctx *c) {
 void lb_destroy(lb_ctx *c) {
     if (!c) return;
     free_profile(c);
+    if (c->adj.base) cudaFree(c->adj.base);
     if (c->owns)
         for (int j = 0; j < c->nbufs; ++j)
             if (c->bufs[j]) cudaFree(c->bufs[j]);
     delete c;
+}
+
+lb_status lb_set_params(lb_ctx *c, const lb_params *params) {
+    if (!c || !params) return fail(LB_EINVAL, "ctx and params must not be NULL");
+    lb_status s = validate(&c->g, params);
+    if (s != LB_OK) return s;
+    if (params->storage != c->p.storage) return fail(LB_EINVAL, "storage cannot change on an existing context");
+    c->p = *params;
+    c->adj.valid = false;
+    return upload_disc(c);
 }
 
 lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, const float *rho_r, const float *rho_b,
@@ -840,8 +871,168 @@ int64_t lb_kernel_launches(const lb_ctx *c) { return c ? c->launches : -1; }
 
 lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_args, double *grad_out,
                      int32_t n_grad) {
-    (void)c; (void)objective; (void)T; (void)obj_args; (void)grad_out; (void)n_grad;
-    return fail(LB_ENOTIMPL, "lb_adjoint is not provided by this build");
+    if (!c || !obj_args || !grad_out) return fail(LB_EINVAL, "ctx, obj_args and grad_out must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_adjoint before lb_init/lb_load");
+    if (c->p.storage != LB_STORE_FP32) return fail(LB_EINVAL, "lb_adjoint needs FP32 population storage");
+    if (c->p.s3 != 1.0 || c->p.s4 != 1.0 || c->p.s5 != 1.0 || c->p.s6 != 1.0)
+        return fail(LB_EINVAL, "lb_adjoint needs the paper's rates s3 = s4 = s5 = s6 = 1");
+    if (T < 1) return fail(LB_EINVAL, "T must be >= 1");
+    if (n_grad < LB_ADJ_NOUT) return fail(LB_EINVAL, "grad_out must hold LB_ADJ_NOUT doubles");
+    for (int j = 0; j < LB_ADJ_NARGS; ++j)
+        if (!std::isfinite(obj_args[j])) return fail(LB_EINVAL, "obj_args must be finite");
+    if (objective == LB_OBJ_INTERFACE_AREA) {
+        if (!(obj_args[0] > 0)) return fail(LB_EINVAL, "interface area needs eps = obj_args[0] > 0");
+    } else if (objective == LB_OBJ_PENETRATION) {
+        if (!(obj_args[0] > 0)) return fail(LB_EINVAL, "penetration length needs delta = obj_args[0] > 0");
+    } else {
+        return fail(LB_EINVAL, "unknown objective");
+    }
+    if (obj_args[2] < 0) return fail(LB_EINVAL, "checkpoint interval obj_args[2] must be >= 0");
+    long long k = obj_args[2] >= 1 ? (long long)obj_args[2] : (long long)std::ceil(std::sqrt((double)T));
+    k = std::max(1ll, std::min<long long>(k, T));
+    const long long nseg = (T + k - 1) / k;
+
+    // workspace: checkpoints every k steps, one segment of k recomputed steps, adjoint state
+    const size_t NN = (size_t)c->nn, P = (size_t)c->plane;
+    const size_t pb = 27 * NN * sizeof(float2), hb = 54 * P * sizeof(float), nb2 = NN * sizeof(float2);
+    StepArgs a0 = make_args(c);
+    const long long nblk_coll = adj_collide_blocks(a0), nblk_inlet = adj_boundary_blocks(a0);
+    const size_t parts[] = {nseg * pb, nseg * hb, (k + 1) * pb, k * nb2, k * 18 * P * sizeof(float),
+                            k * 18 * P * sizeof(float), (k + 1) * hb, pb, pb, nb2, nb2, NN * sizeof(float4), nb2,
+                            hb, 9 * P * sizeof(float), hb, hb, nblk_coll * 3 * sizeof(double),
+                            nblk_inlet * 17 * sizeof(double), nblk_coll * sizeof(double), 32 * sizeof(double), nb2};
+    size_t need = 0;
+    for (size_t v : parts) need += align_up(v);
+    if (need > c->adj.bytes) {
+        if (c->adj.base) cudaFree(c->adj.base);
+        c->adj.base = nullptr;
+        c->adj.bytes = 0;
+        c->adj.valid = false;
+        if (cudaMalloc(&c->adj.base, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "cannot allocate the adjoint workspace (" + std::to_string(need >> 20) + " MiB)");
+        }
+        c->adj.bytes = need;
+    }
+    {
+        char *p = (char *)c->adj.base;
+        size_t j = 0;
+        auto take = [&](void *&dst) { dst = p; p += align_up(parts[j++]); };
+        void *v[22];
+        for (int q = 0; q < 22; ++q) take(v[q]);
+        auto &w = c->adj;
+        w.ckpt_pop = (float2 *)v[0]; w.ckpt_hist = (float *)v[1]; w.seg_pop = (float2 *)v[2];
+        w.seg_phase = (float2 *)v[3]; w.seg_zin = (float *)v[4]; w.seg_zout = (float *)v[5];
+        w.seg_hist = (float *)v[6]; w.lp[0] = (float2 *)v[7]; w.lp[1] = (float2 *)v[8]; w.lr[0] = (float2 *)v[9];
+        w.lr[1] = (float2 *)v[10]; w.lga = (float4 *)v[11]; w.lgb = (float2 *)v[12]; w.lc = (float *)v[13];
+        w.li = (float *)v[14]; w.lh[0] = (float *)v[15]; w.lh[1] = (float *)v[16]; w.acc_coll = (double *)v[17];
+        w.acc_inlet = (double *)v[18]; w.acc_obj = (double *)v[19]; w.out = (double *)v[20];
+        w.objph = (float2 *)v[21];
+        w.nblk_coll = nblk_coll;
+        w.nblk_inlet = nblk_inlet;
+    }
+    auto &w = c->adj;
+    w.valid = false;
+    const bool conv = c->g.bc_zhi == LB_BC_CONVECTIVE;
+    cudaStream_t st = c->stream;
+    LB_CUDA(cudaMemsetAsync(w.acc_coll, 0, nblk_coll * 3 * sizeof(double), st));
+    LB_CUDA(cudaMemsetAsync(w.acc_inlet, 0, nblk_inlet * 17 * sizeof(double), st));
+    LB_CUDA(cudaMemsetAsync(w.acc_obj, 0, nblk_coll * sizeof(double), st));
+    LB_CUDA(cudaMemsetAsync(w.out, 0, 32 * sizeof(double), st));
+    LB_CUDA(cudaMemsetAsync(w.lh[0], 0, hb, st));
+    LB_CUDA(cudaMemsetAsync(w.lc, 0, hb, st));
+    LB_CUDA(cudaMemsetAsync(w.li, 0, 9 * P * sizeof(float), st));
+
+    // forward pass with a checkpoint at the start of every segment
+    const int64_t step0 = c->step;
+    for (long long sg = 0; sg < nseg; ++sg) {
+        LB_CUDA(cudaMemcpyAsync(w.ckpt_pop + sg * 27 * NN, c->pop[c->cur], pb, cudaMemcpyDeviceToDevice, st));
+        if (conv)
+            LB_CUDA(cudaMemcpyAsync(w.ckpt_hist + sg * 54 * P, c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
+        const long long len = std::min<long long>(k, T - sg * k);
+        for (long long t = 0; t < len; ++t) {
+            cudaError_t e = launch_step(make_args(c), LB_STORE_FP32, st, nullptr, &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_step");
+            c->cur ^= 1;
+            if (conv) c->hcur ^= 1;
+            c->step += 1;
+        }
+    }
+
+    // objective of S(T) and its adjoint
+    AdjArgs g{};
+    g.lga = w.lga; g.lgb = w.lgb; g.lc = w.lc; g.li = w.li;
+    g.acc_coll = w.acc_coll; g.acc_inlet = w.acc_inlet;
+    int cl = 0, ch = 0;
+    {
+        AdjArgs go = g;
+        go.lp_out = w.lp[cl];
+        go.lr_out = w.lr[cl];
+        cudaError_t e = launch_objective(state_args(c), go, objective, obj_args, w.objph, w.lr[cl ^ 1], w.acc_obj,
+                                         w.out + 24, st, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_objective");
+    }
+
+    // reverse sweep: recompute each segment from its checkpoint, then step back through it
+    auto seg_args = [&](long long t, int64_t step) {
+        StepArgs a = make_args(c);
+        a.pin = w.seg_pop + t * 27 * NN;
+        a.pout = w.seg_pop + (t + 1) * 27 * NN;
+        a.phase = w.seg_phase + t * NN;
+        a.zin = w.seg_zin + t * 18 * P;
+        a.zout = w.seg_zout + t * 18 * P;
+        a.hist_in = w.seg_hist + t * 54 * P;
+        a.hist_out = w.seg_hist + (t + 1) * 54 * P;
+        a.step = step;
+        return a;
+    };
+    for (long long sg = nseg - 1; sg >= 0; --sg) {
+        const long long n0 = sg * k, len = std::min<long long>(k, T - n0);
+        LB_CUDA(cudaMemcpyAsync(w.seg_pop, w.ckpt_pop + sg * 27 * NN, pb, cudaMemcpyDeviceToDevice, st));
+        if (conv) LB_CUDA(cudaMemcpyAsync(w.seg_hist, w.ckpt_hist + sg * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
+        for (long long t = 0; t < len; ++t) {
+            cudaError_t e = launch_step(seg_args(t, step0 + n0 + t), LB_STORE_FP32, st, nullptr, &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_step (recompute)");
+        }
+        for (long long t = len - 1; t >= 0; --t) {
+            AdjArgs gs = g;
+            gs.lp_in = w.lp[cl]; gs.lr_in = w.lr[cl];
+            gs.lp_out = w.lp[cl ^ 1]; gs.lr_out = w.lr[cl ^ 1];
+            gs.lh_in = w.lh[ch]; gs.lh_out = w.lh[ch ^ 1];
+            cudaError_t e = launch_adjoint_step(seg_args(t, step0 + n0 + t), gs, st, &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_adjoint_step");
+            cl ^= 1;
+            if (conv) ch ^= 1;
+        }
+    }
+    {
+        cudaError_t e = launch_adjoint_reduce(g, nblk_coll, nblk_inlet, w.out, st, &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_adjoint_reduce");
+    }
+    double host[32];
+    LB_CUDA(cudaMemcpyAsync(host, w.out, sizeof(host), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaStreamSynchronize(st));
+    grad_out[0] = host[24];
+    for (int j = 1; j < LB_ADJ_NOUT; ++j) grad_out[j] = host[j];
+    w.cl = cl;
+    w.valid = true;
+    return LB_OK;
+}
+
+lb_status lb_adjoint_state(lb_ctx *c, float *out, int32_t on_device) {
+    if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
+    if (!c->adj.valid) return fail(LB_ESTATE, "lb_adjoint_state before a successful lb_adjoint");
+    auto &w = c->adj;
+    AdjArgs g{};
+    g.lp_in = w.lp[w.cl];
+    g.lr_in = w.lr[w.cl];
+    const size_t bytes = 54 * (size_t)c->nn * sizeof(float);
+    float *dst = on_device ? out : (float *)w.lp[w.cl ^ 1];
+    cudaError_t e = launch_adjoint_state(make_args(c), g, dst, c->stream, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_adjoint_state");
+    if (!on_device) LB_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
 }
 
 }  // extern "C"

@@ -87,7 +87,8 @@ __host__ __device__ __forceinline__ float inlet_xi(unsigned long long seed, long
 // cos m theta, sin m theta come from the angle-addition recurrence on the unit offset.
 struct InletVel {
     float ux, uy, uz;
-    float cm[9], sm[9];  // cos m theta, sin m theta for m = 0..8
+    float dux, duy, prof;  // d(ux, uy, uz)/d u_in = (dux, duy, prof)
+    float cm[9], sm[9];    // cos m theta, sin m theta for m = 0..8
 };
 
 __device__ __forceinline__ void inlet_velocity(float u_in, float noise_amp, const float *fourier, float xc, float yc,
@@ -96,9 +97,12 @@ __device__ __forceinline__ void inlet_velocity(float u_in, float noise_amp, cons
     const float rx = (float)xs - xc, ry = (float)ys - yc;
     const float r = sqrtf(rx * rx + ry * ry);
     const float c1 = r > 0.0f ? rx / r : 1.0f, s1 = r > 0.0f ? ry / r : 0.0f;
-    const float amp = noise_amp * u_in * inlet_xi(seed, step, xs, ys, nx, ny);
+    const float unit = noise_amp * inlet_xi(seed, step, xs, ys, nx, ny);
+    const float amp = unit * u_in;
     v.ux = r > 0.0f ? amp * rx / r : 0.0f;
     v.uy = r > 0.0f ? amp * ry / r : 0.0f;
+    v.dux = r > 0.0f ? unit * rx / r : 0.0f;
+    v.duy = r > 0.0f ? unit * ry / r : 0.0f;
     v.cm[0] = 1.0f;
     v.sm[0] = 0.0f;
     float prof = 1.0f;
@@ -108,6 +112,7 @@ __device__ __forceinline__ void inlet_velocity(float u_in, float noise_amp, cons
         v.sm[m] = v.sm[m - 1] * c1 + v.cm[m - 1] * s1;
         prof = fmaf(fourier[2 * (m - 1)], v.cm[m], fmaf(fourier[2 * m - 1], v.sm[m], prof));
     }
+    v.prof = prof;
     v.uz = u_in * prof;
 }
 

@@ -10,4 +10,40 @@ namespace lbcm {
 // before the collision kernel and after it.  *launches is increased by the number of
 // kernels launched.
 cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches);
+
+// Adjoint state and scratch of one reverse step (FP32 populations, paper rates).
+//   lp_in / lr_in   lambda of S(n+1): pushed part [27][NN] float2 and deferred density part [NN]
+//   lp_out / lr_out the same for S(n)
+//   lga, lgb        lambda of (grad phi, grad rho) per node: (gpx, gpy, gpz, grx), (gry, grz)
+//   lc              direct lambda of f(N) on a convective top [54][nx ny]
+//   li              direct lambda of the red inlet populations that come from the disc [9][nx ny]
+//   lh_in / lh_out  lambda of the outflow history hist(n+1) / hist(n) [54][nx ny]
+//   acc_coll        FP64 per-block sums of dJ/d(sigma, nu_r, nu_b) [blocks][3]
+//   acc_inlet       FP64 per-block sums of dJ/d(u_in, a_1, b_1, ..., a_8, b_8) [blocks][17]
+struct AdjArgs {
+    const float2 *lp_in, *lr_in;
+    float2 *lp_out, *lr_out;
+    float4 *lga;
+    float2 *lgb;
+    float *lc, *li;
+    const float *lh_in;
+    float *lh_out;
+    double *acc_coll, *acc_inlet;
+};
+
+// Blocks of the collide-adjoint and boundary-adjoint grids (sizes of acc_coll, acc_inlet).
+long long adj_collide_blocks(const StepArgs &a);
+long long adj_boundary_blocks(const StepArgs &a);
+// Reverse of the step described by a (pin = S(n), phase / zin / zout / hist_in / hist_out as
+// the forward step n wrote them).
+cudaError_t launch_adjoint_step(const StepArgs &a, const AdjArgs &g, cudaStream_t s, long long *launches);
+// Objective of the state a.pin (0 interface area, args[0] = eps; 1 penetration length,
+// args[0] = delta): scalar[0] = J; writes lambda_S(T) into g.lp_out / g.lr_out.
+cudaError_t launch_objective(const StepArgs &a, const AdjArgs &g, int objective, const double *args, float2 *ph,
+                             float2 *lr_obj, double *acc_obj, double *scalar, cudaStream_t s, long long *launches);
+// out[1] = dJ/du_in, out[2..4] = dJ/d(sigma, nu_r, nu_b), out[5..20] = dJ/d(a_1, b_1, ..., b_8).
+cudaError_t launch_adjoint_reduce(const AdjArgs &g, long long nblk_coll, long long nblk_inlet, double *out,
+                                  cudaStream_t s, long long *launches);
+// dJ/dS in the canonical layout [k][i][z][y][x] from (g.lp_in, g.lr_in).
+cudaError_t launch_adjoint_state(const StepArgs &a, const AdjArgs &g, float *out, cudaStream_t s, long long *launches);
 }  // namespace lbcm

@@ -38,6 +38,7 @@
 // for any other rates.
 #include "lbcm_device.cuh"
 #include "lbcm_internal.h"
+#include "lbcm_node.cuh"
 
 namespace lbcm {
 
@@ -117,41 +118,6 @@ __global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
     }
 }
 
-// Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
-// planes of this step substituted.  Branches are uniform across a warp (one z per warp).
-template <int S>
-__device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, float (&fr)[27], float (&fb)[27]) {
-    const size_t P = (size_t)a.plane;
-    const int N = a.nz - 1;
-    const bool periodic_z = a.bc_zlo == BC_PERIODIC;
-    const bool lo = (z == 0) && !periodic_z;
-    const bool conv = (z == N) && a.bc_zhi == BC_CONVECTIVE;
-    const bool slip_hi = (z == N) && a.bc_zhi == BC_FREESLIP;
-    if (conv) {
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            fr[i] = a.hist_out[i * P + nb.pxy];
-            fb[i] = a.hist_out[(27 + i) * P + nb.pxy];
-        }
-        return;
-    }
-    const float2 own = reader_shift<S>(a, nb.n);
-#pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        if (cz(i) == 1 && lo) {
-            fr[i] = a.zin[zrank(i) * P + nb.pxy];
-            fb[i] = a.zin[(9 + zrank(i)) * P + nb.pxy];
-        } else if (cz(i) == -1 && slip_hi) {
-            fr[i] = a.zout[zrank(i) * P + nb.pxy];
-            fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
-        } else {
-            const float2 v = load_pop<S>(a, i, nb.src(i), own);
-            fr[i] = v.x;
-            fb[i] = v.y;
-        }
-    }
-}
-
 // --------------------------------------------------------------- phase field (K_A)
 template <int S>
 __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
@@ -173,46 +139,6 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
         a.phase[nb.n] = make_float2(ph, rr + rb);
     else
         a.ph_cur[nb.n] = make_float4(ph, rr + rb, rr, rb);  // also the FP16 shift densities of S(t+1)
-}
-
-// Isotropic gradients of phi and rho (end of Section II): grad chi = 3 sum_j w_j chi(x + c_j)
-// c_j, summed over the 13 pairs of opposite directions (j, j+1) as 3 w_j c_j (chi(x + c_j) -
-// chi(x - c_j)), so that a uniform field gives exactly zero and nearby values subtract
-// exactly.  Ghosts: z = -1 is phi = 1, rho = rho_r0 inside the inlet disc and the mirror of
-// z = 0 elsewhere; z = N + 1 mirrors z = N.
-template <int S>
-__device__ __forceinline__ void stencil_gradients(const StepArgs &a, const Nbr &nb, int z, float &gpx, float &gpy,
-                                                  float &gpz, float &grx, float &gry, float &grz) {
-    const bool inlet_lo = z == 0 && a.bc_zlo == BC_INLET;
-    float ph[27], rh[27];
-#pragma unroll
-    for (int j = 1; j < 27; ++j) {
-        // ghost planes were clamped onto z = 0 / z = N (mirror)
-        if constexpr (S == STORE_FP32) {
-            const float2 v = __ldg(a.phase + nb.nbr(j));
-            ph[j] = v.x;
-            rh[j] = v.y;
-        } else {
-            const float4 v = __ldg(a.ph_cur + nb.nbr(j));
-            ph[j] = v.x;
-            rh[j] = v.y;
-        }
-        if (cz(j) == -1 && inlet_lo) {
-            if (a.disc[nb.yo[1 - cy(j)] + nb.xo[1 - cx(j)]]) {  // z = -1 inside the inlet disc
-                ph[j] = 1.0f;
-                rh[j] = a.rho_r0;
-            }
-        }
-    }
-    gpx = gpy = gpz = grx = gry = grz = 0.0f;
-#pragma unroll
-    for (int j = 1; j < 27; j += 2) {  // c_{j+1} = -c_j
-        const float w3 = 3.0f * wgt(j);
-        const float dp = ph[j] - ph[j + 1], dr = rh[j] - rh[j + 1];
-        if (cx(j) != 0) { gpx = fmaf(w3 * cx(j), dp, gpx); grx = fmaf(w3 * cx(j), dr, grx); }
-        if (cy(j) != 0) { gpy = fmaf(w3 * cy(j), dp, gpy); gry = fmaf(w3 * cy(j), dr, gry); }
-        if (cz(j) != 0) { gpz = fmaf(w3 * cz(j), dp, gpz); grz = fmaf(w3 * cz(j), dr, grz); }
-    }
 }
 
 // 1-D shifted moment sweep: values at c = -1, 0, +1 -> central moments of order 0, 1, 2
@@ -375,63 +301,6 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(0.0f, 0.0f));
 }
 
-
-// Coefficients of the inverse 1-D sweep: a value at c in {-1, 0, +1} from central moments
-// (m0, m1, m2) about u is G0[c] m0 + G1[c] m1 + G2[c] m2 with
-//   G0 = ((u^2 - u)/2, 1 - u^2, (u^2 + u)/2), G1 = (u - 1/2, -2u, u + 1/2), G2 = (1/2, -1, 1/2).
-struct InvAxis {
-    float g0[3], g1[3];
-    __device__ __forceinline__ explicit InvAxis(float u) {
-        const float u2 = u * u;
-        g0[0] = 0.5f * (u2 - u);
-        g0[1] = 1.0f - u2;
-        g0[2] = 0.5f * (u2 + u);
-        g1[0] = u - 0.5f;
-        g1[1] = -2.0f * u;
-        g1[2] = u + 0.5f;
-    }
-};
-__device__ __forceinline__ constexpr float g2c(int c) { return c == 0 ? -1.0f : 0.5f; }
-
-// Moments of the post-stream populations of one node that the paper-rate collision needs:
-// colour densities, colour-blind mass, momentum and raw second moment.
-struct Moments {
-    float rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
-};
-
-template <int S>
-__device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb, int z, Moments &m) {
-    float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
-    {
-        float fr[27], fb[27];
-        gather<S>(a, nb, z, fr, fb);
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {  // same order as the phase-field kernel
-            rho_r += fr[i];
-            rho_b += fb[i];
-        }
-        // opposite pairs (i, i+1): odd moments take the difference, even ones the sum
-        sf = fr[0] + fb[0];
-#pragma unroll
-        for (int i = 1; i < 27; i += 2) {
-            const float fp = fr[i] + fb[i], fm = fr[i + 1] + fb[i + 1];
-            const float s2 = fp + fm, d2 = fp - fm;
-            sf += s2;
-            if (cx(i) > 0) jx += d2; else if (cx(i) < 0) jx -= d2;
-            if (cy(i) > 0) jy += d2; else if (cy(i) < 0) jy -= d2;
-            if (cz(i) > 0) jz += d2; else if (cz(i) < 0) jz -= d2;
-            if (cx(i) != 0) pxx += s2;
-            if (cy(i) != 0) pyy += s2;
-            if (cz(i) != 0) pzz += s2;
-            if (cx(i) * cy(i) > 0) pxy += s2; else if (cx(i) * cy(i) < 0) pxy -= s2;
-            if (cx(i) * cz(i) > 0) pxz += s2; else if (cx(i) * cz(i) < 0) pxz -= s2;
-            if (cy(i) * cz(i) > 0) pyz += s2; else if (cy(i) * cz(i) < 0) pyz -= s2;
-        }
-    }
-
-    m = Moments{rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz};
-}
 
 // Collision, perturbation and recolouring of one node from its moments and gradients;
 // writes the 54 post-collision populations of node n.

@@ -74,7 +74,9 @@ def test_buffer_sizes_and_validation(lib):
 def test_null_handling_without_gpu(lib):
     assert lib.lb_step(None, 1) == 1
     assert lib.lb_mass(None, None) == 1
-    assert lib.lb_adjoint(None, 0, 0, None, None, 0) == 7
+    assert lib.lb_adjoint(None, 0, 0, None, None, 0) == 1          # LB_EINVAL
+    assert lib.lb_adjoint_state(None, None, 0) == 1
+    assert lib.lb_set_params(None, None) == 1
     assert lib.lb_step_count(None) == -1
     lib.lb_destroy(None)
 

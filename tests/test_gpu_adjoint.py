@@ -1,0 +1,170 @@
+"""The discrete adjoint of the CUDA step (lb_adjoint) against FP64 central finite differences
+of the oracle (same seeded inputs on both sides; the oracle never sees a GPU value).
+
+Gradient error norm: max over parameters of |g_adjoint - g_fd| / max over parameters of
+|g_fd| (the gradient's own scale), bar 1e-4; the directional derivative along a random state
+perturbation has the same bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+NAMES = ("u_in", "sigma", "nu_r", "nu_b") + tuple(f"{ab}{m}" for m in range(1, 9) for ab in "ab")
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_08923_gb300.build as b
+    b.build()
+    import paper_1804_08923_gb300 as lbm
+    return lbm
+
+
+def full_params(p):
+    base = dict(workloads.CONFIGS["droplet32"]["params"])
+    base.update(p)
+    return base
+
+
+def perturbed(params, name, h):
+    p = dict(params)
+    if name in ("u_in", "sigma", "nu_r", "nu_b"):
+        p[name] = full_params(params)[name] + h
+    else:
+        m, ab = int(name[1:]), name[0]
+        four = list(p.get("fourier", (0.0,) * 16)) + [0.0] * 16
+        four = four[:16]
+        four[2 * (m - 1) + (ab == "b")] += h
+        p["fourier"] = tuple(four)
+    return p
+
+
+def fd_step(params, name):
+    """Central-difference step: 1e-5 of the value for the scalars, 1e-4 for profile coefficients."""
+    if name in ("u_in", "sigma", "nu_r", "nu_b"):
+        return 1e-5 * abs(full_params(params)[name])
+    return 1e-4
+
+
+def oracle_J(grid, bc, params, init, T, objective, args):
+    nx, ny, nz = grid
+    ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *bc), oracle.make_params(full_params(params)))
+    init(ref)
+    ref.step(T)
+    return ref.objective(objective, args)
+
+
+def fd_gradient(grid, bc, params, init, T, objective, args, names):
+    g = np.zeros(len(names))
+    for k, nm in enumerate(names):
+        h = fd_step(params, nm)
+        jp = oracle_J(grid, bc, perturbed(params, nm, h), init, T, objective, args)
+        jm = oracle_J(grid, bc, perturbed(params, nm, -h), init, T, objective, args)
+        g[k] = (jp - jm) / (2 * h)
+    return g
+
+
+def jet_case():
+    cfg = workloads.scaled_jet("jet64", 16, 14, 18, D=8)
+    params = dict(cfg["params"])
+    params["noise_amp"] = 0.02
+    params["fourier"] = tuple(0.05 * np.random.default_rng(4).standard_normal(16))
+    return (16, 14, 18), cfg["bc"], params
+
+
+@pytest.mark.parametrize("objective,args", [("area", (1e-3,)), ("penetration", (2.0,))])
+def test_adjoint_jet_parameters_match_finite_differences(lb, objective, args):
+    """Inlet disc with noise and a profile, free slip around it, convective outflow: the
+    20 parameter gradients after 12 steps against central differences of the oracle."""
+    grid, bc, params = jet_case()
+    T = 12
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    J, g = lat.adjoint(T, objective, args)
+    J_ref = oracle_J(grid, bc, params, lambda r: r.init_jet(), T, objective, args)
+    assert abs(J / J_ref - 1) < 1e-5, (J, J_ref)
+    g_fd = fd_gradient(grid, bc, params, lambda r: r.init_jet(), T, objective, args, NAMES)
+    err = np.abs(g - g_fd).max() / np.abs(g_fd).max()
+    assert err < TOL, (err, list(zip(NAMES, g, g_fd)))
+    assert np.abs(g_fd[4:]).max() > 1e-3 * np.abs(g_fd).max()  # the profile really matters
+
+
+@pytest.mark.parametrize("bc,g", [((0, 0), (1e-5, 0.0, 2e-5)), ((1, 1), (0.0, 0.0, 3e-5))])
+def test_adjoint_state_directional_derivative(lb, bc, g):
+    """dJ/dS(0) along a random direction against the oracle's central difference of J(S(0) +
+    h dS), on a random two-phase state (periodic, and free-slip walls with gravity), 8 steps."""
+    nx, ny, nz = 12, 10, 14
+    shape = (nz, ny, nx)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.05, sigma=0.004, g=g)
+    fields = workloads.random_two_phase_fields(shape, 9, 1.0, 0.5, u_amp=0.03)
+    lat = lb.Lattice((nx, ny, nz), params, bc=bc)
+    lat.init_fields(*fields)
+    T = 8
+    J, grad = lat.adjoint(T, "area", (1e-3,), checkpoint=3)
+    lS = lat.adjoint_state().astype(np.float64)
+    dS = np.random.default_rng(2).standard_normal((2, 27) + shape) * 1e-3
+    ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *bc), oracle.make_params(full_params(params)))
+    ref.init_fields(*fields)
+    S0, H0 = ref.S.copy(), ref.hist.copy()
+    h = 1e-3
+    Js = []
+    for sgn in (1, -1):
+        ref.set_state(S0 + sgn * h * dS, H0)
+        ref.step(T)
+        Js.append(ref.objective("area", (1e-3,)))
+    fd = (Js[0] - Js[1]) / (2 * h)
+    ad = float((lS * dS).sum())
+    assert abs(ad - fd) < TOL * abs(fd), (ad, fd)
+    # sigma and the viscosities against central differences too
+    init = lambda r: r.init_fields(*fields)
+    g_fd = fd_gradient((nx, ny, nz), bc, params, init, T, "area", (1e-3,), ("sigma", "nu_r", "nu_b"))
+    err = np.abs(grad[1:4] - g_fd).max() / np.abs(g_fd).max()
+    assert err < TOL, (err, grad[1:4], g_fd)
+
+
+def test_adjoint_is_independent_of_the_checkpoint_interval(lb):
+    """Recomputed segments are bitwise the forward steps, so the gradient does not depend on
+    the checkpoint interval; the context ends at S(T), bitwise the state lb_step(T) reaches."""
+    grid, bc, params = jet_case()
+    T = 9
+    res = []
+    for k in (0, 1, 4, 9):
+        lat = lb.Lattice(grid, params, bc=bc)
+        lat.init_jet()
+        res.append(lat.adjoint(T, "area", (1e-3,), checkpoint=k))
+        if k == 0:
+            S_adj = lat.populations(device=False)
+            ref = lb.Lattice(grid, params, bc=bc)
+            ref.init_jet()
+            ref.step(T)
+            assert np.array_equal(S_adj, ref.populations(device=False))
+            assert lat.step_count == T
+    for J, g in res[1:]:
+        assert J == res[0][0]
+        assert np.array_equal(g, res[0][1])
+
+
+def test_adjoint_rejects_what_it_does_not_cover(lb):
+    grid, bc, params = jet_case()
+    lat = lb.Lattice(grid, dict(params, s3=0.9), bc=bc)
+    lat.init_jet()
+    with pytest.raises(lb.LBError):
+        lat.adjoint(3)
+    lat16 = lb.Lattice(grid, dict(params, storage=1), bc=bc)
+    lat16.init_jet()
+    with pytest.raises(lb.LBError):
+        lat16.adjoint(3)
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    with pytest.raises(lb.LBError):
+        lat.adjoint_state()
+    with pytest.raises(lb.LBError):
+        lat.adjoint(3, "area", (0.0,))

@@ -270,8 +270,13 @@ def test_host_errors(lb):
     assert ei.value.status == 6  # LB_ESTATE before init
     with pytest.raises(lb.LBError):
         g.init_droplet(-1.0, 4.0)
-    import ctypes as C
-    assert lb.library().lb_adjoint(g._ctx, 0, 10, None, None, 0) == 7
+    assert lb.library().lb_adjoint(g._ctx, 0, 10, None, None, 0) == 1  # LB_EINVAL: NULL arguments
+    with pytest.raises(lb.LBError) as ei:
+        g.adjoint(3)
+    assert ei.value.status == 6  # LB_ESTATE before init
+    with pytest.raises(lb.LBError) as ei:
+        g.set_params(nu_r=-1.0)
+    assert ei.value.status == 1 and g.params.get("nu_r") != -1.0
 
 
 # ------------------------------------------------------------------ FP16 storage

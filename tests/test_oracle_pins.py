@@ -442,3 +442,43 @@ def test_laplace_law_static_droplet():
     assert abs(dp / (2 * sigma / R) - 1) < 0.10
     umax = np.sqrt((F["u"] ** 2).sum(0)).max()
     assert umax < 1e-3  # spurious currents of the order of Table 1 (1.22e-4 at R = 25)
+
+
+# ---------------------------------------------------------- adjoint objectives (R12)
+def _phi_fields(phi, rho_r0=1.0, rho_b0=0.5, s=1.0):
+    """Colour densities with order parameter phi (Eq. order): rho_k / rho_k0 = s (1 +- phi) / 2."""
+    return rho_r0 * s * (1 + phi) / 2, rho_b0 * s * (1 - phi) / 2
+
+
+def test_objective_area_closed_forms():
+    """Uniform phi: every interior node contributes eps.  phi linear in z: the isotropic stencil
+    is exact for linear fields, so each interior node contributes sqrt(a^2 + eps^2)."""
+    nz, ny, nx = 9, 5, 6
+    lat = make_lattice((nz, ny, nx), rho_b0=0.5)
+    rr, rb = _phi_fields(np.full((nz, ny, nx), 0.3))
+    lat.init_fields(rr, rb, np.zeros((3, nz, ny, nx)))
+    eps = 1e-2
+    assert abs(lat.objective("area", (eps,)) - (nz - 2) * ny * nx * eps) < 1e-12
+    a = 0.07
+    z = np.arange(nz, dtype=float)[:, None, None] * np.ones((nz, ny, nx))
+    rr, rb = _phi_fields(a * (z - 4))
+    lat.init_fields(rr, rb, np.zeros((3, nz, ny, nx)))
+    assert abs(lat.objective("area", (eps,)) / ((nz - 2) * ny * nx * np.hypot(a, eps)) - 1) < 1e-12
+
+
+def test_objective_penetration_of_a_red_slab():
+    """Red for z <= z0, blue above: H is 1 and 0 there, so L = delta log(nx ny sum_{z<=z0}
+    e^{z/delta}), the geometric sum in closed form; one half-red plane adds H = 1/4 weights."""
+    nz, ny, nx, z0, delta = 12, 4, 5, 6, 1.5
+    lat = make_lattice((nz, ny, nx), rho_b0=0.5)
+    phi = np.where(np.arange(nz)[:, None, None] <= z0, 1.0, -1.0) * np.ones((nz, ny, nx))
+    rr, rb = _phi_fields(phi)
+    lat.init_fields(rr, rb, np.zeros((3, nz, ny, nx)))
+    q = np.exp(-1 / delta)
+    expect = z0 + delta * np.log(nx * ny * (1 - q ** (z0 + 1)) / (1 - q))
+    assert abs(lat.objective("penetration", (delta,)) - expect) < 1e-12
+    phi[z0 + 1] = 0.0  # phi = 0: H = 1/4
+    rr, rb = _phi_fields(phi)
+    lat.init_fields(rr, rb, np.zeros((3, nz, ny, nx)))
+    expect = delta * np.log(nx * ny * (q ** -(z0 + 1) * 0.25 + (q ** -(z0 + 1) - 1) / (q ** -1 - 1)))
+    assert abs(lat.objective("penetration", (delta,)) - expect) < 1e-12
