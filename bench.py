@@ -42,6 +42,41 @@ BYTES_STEP_FP16 = 112 + 112 + 16 + 16
 BYTES_KERNEL_FP16 = {"collide_kernel": 256, "phase_field_kernel": 144}
 
 
+def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,)):
+    """Cost of lb_adjoint (T steps forward with ceil(sqrt T) checkpoints, objective, reverse
+    sweep) against lb_step(T) from the same state, both timed with CUDA events."""
+    cfg = workloads.CONFIGS[name]
+    nx, ny, nz = cfg["grid"]
+    lat = lb.Lattice((nx, ny, nz), cfg["params"], bc=cfg["bc"])
+    lat.init_jet()
+    lat.step(20)
+    state = lat.save()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    lat.adjoint(T, objective, args)  # workspace allocation and warm-up
+    lat.load(state)
+    torch.cuda.synchronize()
+    ev[0].record(lat.stream)
+    lat.step(T)
+    ev[1].record(lat.stream)
+    torch.cuda.synchronize()
+    lat.load(state)
+    torch.cuda.synchronize()
+    ev[2].record(lat.stream)
+    J, g = lat.adjoint(T, objective, args)
+    ev[3].record(lat.stream)
+    torch.cuda.synchronize()
+    fwd, adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    k = int(np.ceil(np.sqrt(T)))
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return {"workload": cfg["text"], "T": T, "checkpoint_interval": k, "objective": objective,
+            "objective_args": list(args), "J": J, "grad_norm": float(np.linalg.norm(g)),
+            "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
+            "work": "T forward steps with checkpoints + T recomputed forward steps + T reverse steps",
+            "precision": "FP32 kernels, FP64 parameter-gradient accumulation"}
+
+
 def fp16_error(lb, cfg, steps):
     """FP16 against FP32 storage on the same workload after `steps` steps: relative L2 error
     of the velocity and largest change of the order parameter."""
@@ -236,6 +271,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--error-steps", type=int, default=500)
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     cfg = workloads.CONFIGS[args.config]
@@ -358,6 +394,9 @@ def main():
 
     if rank == 0:
         base = None
+        adjoint = None
+        if world == 1 and not args.no_adjoint:
+            adjoint = adjoint_leg(lb, torch)
         if world == 1 and not args.no_cpu_baseline:
             base = cpu_baseline(cfg)
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -367,7 +406,8 @@ def main():
                 "bytes_per_node_algorithmic": BYTES_STEP,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
-                "fp16_storage": fp16, "adjoint_forward_ratio": None}
+                "fp16_storage": fp16, "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None,
+                "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

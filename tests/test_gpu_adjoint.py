@@ -168,3 +168,29 @@ def test_adjoint_rejects_what_it_does_not_cover(lb):
         lat.adjoint_state()
     with pytest.raises(lb.LBError):
         lat.adjoint(3, "area", (0.0,))
+
+
+def test_autograd_function_gives_the_adjoint_gradient(lb):
+    """torch.autograd through LatticeObjective: backward returns lb_adjoint's gradient, the
+    lattice is restored to the saved state on every call, and a step against the gradient
+    lowers the objective as the first-order prediction says."""
+    import torch
+    from paper_1804_08923_gb300 import autograd as ag
+    grid, bc, params = jet_case()
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    state = lat.save()
+    theta = ag.theta_of(params).requires_grad_(True)
+    J = ag.objective(lat, theta, 6, state, "area", (1e-3,))
+    J.backward()
+    ref = lb.Lattice(grid, params, bc=bc)
+    ref.init_jet()
+    J_ref, g_ref = ref.adjoint(6, "area", (1e-3,))
+    assert float(J) == J_ref
+    assert np.array_equal(theta.grad.numpy(), g_ref)
+    g = theta.grad.detach().clone()
+    step = -1e-3 * g / g.norm() * theta.detach().norm()
+    J2 = ag.objective(lat, theta.detach() + step, 6, state, "area", (1e-3,))
+    predicted = float(J) + float(g @ step)
+    assert abs(float(J2) - predicted) < 0.05 * abs(float(g @ step))
+    assert float(J2) < float(J)
