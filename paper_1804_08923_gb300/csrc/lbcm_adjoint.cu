@@ -28,17 +28,19 @@
 
 namespace lbcm {
 
-// Adds the block sums of v[0..NV) (FP64) to acc[blk * NV + k].  Every thread of the block
-// must call it (no early return before).
+// Adds the block sums of v[0..NV) to acc[blk * NV + k] (FP64).  The sum over the block's
+// threads is FP32 (shuffles, then one warp over the warp sums); only the block total is
+// converted and accumulated in FP64, since FP64 throughput is a small fraction of FP32 here.
+// Every thread of the block must call it (no early return before).
 template <int NV>
 __device__ __forceinline__ void block_accumulate(const float (&v)[NV], double *acc, long long blk) {
-    __shared__ double sh[NV][32];
+    __shared__ float sh[NV][32];
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double d = (double)v[k];
+        float d = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
         if (lane == 0) sh[k][warp] = d;
@@ -47,10 +49,10 @@ __device__ __forceinline__ void block_accumulate(const float (&v)[NV], double *a
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double d = lane < nwarp ? sh[k][lane] : 0.0;
+            float d = lane < nwarp ? sh[k][lane] : 0.0f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-            if (lane == 0) acc[blk * NV + k] += d;
+            if (lane == 0) acc[blk * NV + k] += (double)d;
         }
     }
 }
@@ -87,21 +89,81 @@ __device__ __forceinline__ void sweep_inv_T(float &a0, float &a1, float &a2, con
     a2 = fmaf(0.5f, v0 + v2, -v1);
 }
 
+// Weighted raw moments m_pqr = sum_i v_i w_i cx^p cy^q cz^r (p, q, r <= 2) of 27 values in the
+// tensor layout [cx+1][cy+1][cz+1], by 1-D sweeps: D3Q27's w_i is the product of the 1-D weights
+// (1/6, 2/3, 1/6).  Only the moments of total order <= 3 are kept (c^3 = c on the lattice).
+struct RawMom {
+    float m000, m100, m010, m001, m200, m020, m002, m110, m101, m011, m210, m201, m120, m021, m102, m012, m111;
+};
+__device__ __forceinline__ void wsweep(float &v0, float &v1, float &v2) {
+    const float s = (v2 + v0) * (1.0f / 6.0f), d = (v2 - v0) * (1.0f / 6.0f);
+    v0 = fmaf(2.0f / 3.0f, v1, s);
+    v1 = d;
+    v2 = s;
+}
+__device__ __forceinline__ void raw_moments(float (&t)[27], RawMom &M) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wsweep(t[q], t[9 + q], t[18 + q]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wsweep(t[p * 9 + c], t[p * 9 + 3 + c], t[p * 9 + 6 + c]);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) wsweep(t[p * 3], t[p * 3 + 1], t[p * 3 + 2]);
+#define T_(p, q, r) t[(p) * 9 + (q) * 3 + (r)]
+    M = RawMom{T_(0, 0, 0), T_(1, 0, 0), T_(0, 1, 0), T_(0, 0, 1), T_(2, 0, 0), T_(0, 2, 0), T_(0, 0, 2), T_(1, 1, 0),
+               T_(1, 0, 1), T_(0, 1, 1), T_(2, 1, 0), T_(2, 0, 1), T_(1, 2, 0), T_(0, 2, 1), T_(1, 0, 2), T_(0, 1, 2),
+               T_(1, 1, 1)};
+#undef T_
+}
+// M2 v (the second-moment tensor applied to a vector) and v.M2.w
+__device__ __forceinline__ void m2v(const RawMom &M, float vx, float vy, float vz, float &ox, float &oy, float &oz) {
+    ox = M.m200 * vx + M.m110 * vy + M.m101 * vz;
+    oy = M.m110 * vx + M.m020 * vy + M.m011 * vz;
+    oz = M.m101 * vx + M.m011 * vy + M.m002 * vz;
+}
+// A3(., u, u)_a = sum_i v_i w_i c_a (c.u)^2
+__device__ __forceinline__ void m3uu(const RawMom &M, float ux, float uy, float uz, float &ox, float &oy, float &oz) {
+    const float xx = ux * ux, yy = uy * uy, zz = uz * uz, xy = 2.0f * ux * uy, xz = 2.0f * ux * uz, yz = 2.0f * uy * uz;
+    ox = M.m100 * xx + M.m120 * yy + M.m102 * zz + M.m210 * xy + M.m201 * xz + M.m111 * yz;
+    oy = M.m210 * xx + M.m010 * yy + M.m012 * zz + M.m120 * xy + M.m111 * xz + M.m021 * yz;
+    oz = M.m201 * xx + M.m021 * yy + M.m001 * zz + M.m111 * xy + M.m102 * xz + M.m012 * yz;
+}
+
 // ---------------------------------------------------------------- reverse collision
+// Every per-direction sum of the reverse pass is linear in a_i = (rho_r lS^r_i + rho_b lS^b_i)/rho
+// or b_i = lS^r_i - lS^b_i with coefficients that are polynomials in c_i times shell constants
+// proportional to w_i (varphi_i(alpha) = 27/19 (1 - alpha) w_i, the Phi coefficient 9 w_i and
+// B_i = w_i for i >= 1), so it is a combination of the weighted raw moments of a and b up to
+// third order.  Only the recolouring's 1/|c_i| is not separable and is summed directly.
 template <bool kForce>
 __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArgs &g, int x, int y, int z,
-                                                 float (&part)[3]) {
+                                                 float (&part)[3], float2 *L_s) {
     const Nbr nb(a, x, y, z);
     const int N = a.nz - 1;
     const bool pz = a.bc_zlo == BC_PERIODIC;
     const bool conv_top = !pz && z == N && a.bc_zhi == BC_CONVECTIVE;
     const bool own_in_disc = !pz && z == 0 && a.bc_zlo == BC_INLET && a.disc[nb.pxy];
 
-    // ---- forward recomputation (as collide_from_moments, moments of order <= 2)
+    // lambda of S(n+1) for the 27 directions, loaded as one batch (all requests in flight
+    // together) into this thread's column of shared memory, tensor layout
+    {
+        float2 L[27];
+#pragma unroll
+        for (int i = 0; i < 27; ++i) L[i] = adj_slot(a, g, nb, i, z, own_in_disc);
+#pragma unroll
+        for (int i = 0; i < 27; ++i) L_s[cell(i) * 128] = L[i];
+    }
+
+    // ---- the forward step's collision inputs of this node (recorded in the recompute)
+    const size_t NN = (size_t)a.NN;
+    const float4 r0 = __ldg(g.rec + nb.n), r1 = __ldg(g.rec + NN + nb.n), r2 = __ldg(g.rec + 2 * NN + nb.n),
+                 r3 = __ldg(g.rec + 3 * NN + nb.n);
     Moments mo;
-    gather_moments<STORE_FP32>(a, nb, z, mo);
-    float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients<STORE_FP32>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    mo.rho_r = r0.x; mo.rho_b = r0.y; mo.jx = r0.z; mo.jy = r0.w;
+    mo.jz = r1.x; mo.pxx = r1.y; mo.pyy = r1.z; mo.pzz = r1.w;
+    mo.pxy = r2.x; mo.pxz = r2.y; mo.pyz = r2.z;
+    const float gpx = r2.w, gpy = r3.x, gpz = r3.y, grx = r3.z, gry = r3.w, grz = __ldg(g.rec4 + nb.n);
     const float rr = mo.rho_r, rb = mo.rho_b;
     const float rho = rr + rb, inv_rho = 1.0f / rho;
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
@@ -121,7 +183,7 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     const float ugr = ux * grx + uy * gry + uz * grz;
     const float uF = ux * Fx + uy * Fy + uz * Fz;
     const float cs2 = oma * (9.0f / 19.0f);
-    // Q = Pi(f) - Pi(f^e) + Pi(F')/2 - rho u u terms: the second central moment of f - f^e + F'/2
+    // Q: second central moment of f - f^e + F'/2 (Pi(f^e), Pi(F') in closed form)
     float Qxx = mo.pxx - (rho * cs2 + rho * ux * ux + nu * (2.0f * ux * grx + ugr));
     float Qyy = mo.pyy - (rho * cs2 + rho * uy * uy + nu * (2.0f * uy * gry + ugr));
     float Qzz = mo.pzz - (rho * cs2 + rho * uz * uz + nu * (2.0f * uz * grz + ugr));
@@ -139,160 +201,159 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     const float k002 = o2 * (Qzz - trQ * third) + o2b * trQ * third;
     const float k110 = o2 * Qxy, k101 = o2 * Qxz, k011 = o2 * Qyz;
     const InvAxis Ax(ux), Ay(uy), Az(uz);
-    float V00[3], V10[3], V01[3], V20[3], V02[3], V11[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        V00[c] = g2c(c - 1) * k002;
-        V10[c] = Az.g1[c] * k101;
-        V01[c] = Az.g1[c] * k011;
-        V20[c] = Az.g0[c] * k200;
-        V02[c] = Az.g0[c] * k020;
-        V11[c] = Az.g0[c] * k110;
-    }
-    float W0[3][3], W1[3][3], W2[3][3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            W0[b][c] = fmaf(Ay.g0[b], V00[c], fmaf(Ay.g1[b], V01[c], g2c(b - 1) * V02[c]));
-            W1[b][c] = fmaf(Ay.g0[b], V10[c], Ay.g1[b] * V11[c]);
-            W2[b][c] = Ay.g0[b] * V20[c];
-        }
     const float g2 = gpx * gpx + gpy * gpy + gpz * gpz;
     const float inv_gm = 1.0f / sqrtf(g2 + a.eps2);
     const float pert = Acoef * inv_gm;
     const float R = a.beta * rr * rb * inv_rho;
 
-    // ---- pass over the directions: lambda of S(n+1) -> lambda of f** and of the recolouring
-    float lh[27];  // lambda of f* (= of f^e, h and the perturbation; F'/2 takes half)
-    float l_xr = 0.0f, l_xb = 0.0f;                       // lambda of rho_r/rho, rho_b/rho
-    float s_fe = 0.0f, s_dvp = 0.0f, s_u = 0.0f, s_nu = 0.0f, s_pert = 0.0f, s_B = 0.0f, s_w = 0.0f;
-    float v_dp[3] = {0, 0, 0}, v_nug[3] = {0, 0, 0}, v_nuu[3] = {0, 0, 0}, v_pgp[3] = {0, 0, 0};
-    float v_wcF[3] = {0, 0, 0}, v_wcu[3] = {0, 0, 0}, v_wc[3] = {0, 0, 0};
-    float s_bcv = 0.0f, s_bcd = 0.0f, v_seg[3] = {0, 0, 0};
+    // ---- a_i and b_i, in place
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        const float c0 = (float)cx(i), c1 = (float)cy(i), c2 = (float)cz(i);
-        const float cu = c0 * ux + c1 * uy + c2 * uz;
-        const float cgr = c0 * grx + c1 * gry + c2 * grz;
-        const float cgp = c0 * gpx + c1 * gpy + c2 * gpz;
-        const float vp = varphi(i, alpha, oma);
-        const float dvp = csq(i) == 0 ? 1.0f : -varphi_k(i);
-        const float pl = eq_poly(cu, usq);
-        const float Phi = csq(i) == 0 ? -3.0f * nu * ugr : phi_corr(i) * nu * cu * cgr;
-        const float fe = rho * fmaf(wgt(i), pl, vp) + Phi;
-        float fs = fe;
-        float cF = 0.0f;
-        if (kForce) {
-            cF = c0 * Fx + c1 * Fy + c2 * Fz;
-            fs += 0.5f * wgt(i) * (3.0f * (cF - uF) + 9.0f * cu * cF);
-        }
-        const int X = cx(i) + 1, Y = cy(i) + 1, Z = cz(i) + 1;
-        fs += fmaf(Ax.g0[X], W0[Y][Z], fmaf(Ax.g1[X], W1[Y][Z], g2c(cx(i)) * W2[Y][Z]));
-        const float pq = wgt(i) * cgp * cgp - bcoef(i) * g2;
-        const float fss = fmaf(pert, pq, fs);
-        const float2 L = adj_slot(a, g, nb, i, z, own_in_disc);
-        l_xr = fmaf(fss, L.x, l_xr);
-        l_xb = fmaf(fss, L.y, l_xb);
-        const float ai = (rr * L.x + rb * L.y) * inv_rho;
-        lh[cell(i)] = ai;
-        // recolouring flux seg_i = R cos_i varphi_i, cos_i = cgp / (|c_i| |g|)
-        if (csq(i) != 0) {
-            const float bi = L.x - L.y;
-            const float t = bi * inv_cnorm(i);
-            s_bcv = fmaf(t * cgp, vp, s_bcv);
-            s_bcd = fmaf(t * cgp, dvp, s_bcd);
-            v_seg[0] += c0 * t * vp; v_seg[1] += c1 * t * vp; v_seg[2] += c2 * t * vp;
-        }
-        // perturbation
-        s_pert = fmaf(ai, pq, s_pert);
-        s_B = fmaf(ai, bcoef(i), s_B);
-        const float awg = ai * wgt(i) * cgp;
-        v_pgp[0] += c0 * awg; v_pgp[1] += c1 * awg; v_pgp[2] += c2 * awg;
-        // equilibrium
-        s_fe = fmaf(ai, fmaf(wgt(i), pl, vp), s_fe);
-        s_dvp = fmaf(ai, dvp, s_dvp);
-        const float aw = ai * wgt(i);
-        const float dpl = fmaf(13.5f * cu, cu, fmaf(9.0f, cu, 3.0f)) - 4.5f * usq;
-        v_dp[0] += c0 * aw * dpl; v_dp[1] += c1 * aw * dpl; v_dp[2] += c2 * aw * dpl;
-        s_u = fmaf(aw, fmaf(-9.0f, cu, -3.0f), s_u);
-        if (csq(i) != 0) {
-            const float ap = ai * phi_corr(i);
-            s_nu = fmaf(ap * cu, cgr, s_nu);
-            v_nug[0] += c0 * ap * cgr; v_nug[1] += c1 * ap * cgr; v_nug[2] += c2 * ap * cgr;
-            v_nuu[0] += c0 * ap * cu; v_nuu[1] += c1 * ap * cu; v_nuu[2] += c2 * ap * cu;
-        }
-        if (kForce) {
-            s_w += aw;
-            v_wcF[0] += c0 * aw * cF; v_wcF[1] += c1 * aw * cF; v_wcF[2] += c2 * aw * cF;
-            v_wcu[0] += c0 * aw * cu; v_wcu[1] += c1 * aw * cu; v_wcu[2] += c2 * aw * cu;
-            v_wc[0] += c0 * aw; v_wc[1] += c1 * aw; v_wc[2] += c2 * aw;
-        }
+    for (int c = 0; c < 27; ++c) {
+        const float2 L = L_s[c * 128];
+        L_s[c * 128] = make_float2((rr * L.x + rb * L.y) * inv_rho, L.x - L.y);
     }
-    const float a0 = lh[cell(0)];
+    const float a0 = L_s[13 * 128].x, b0 = L_s[13 * 128].y;  // rest direction: cell 13
+    const float w0 = 8.0f / 27.0f, k27 = 27.0f / 19.0f;
+
+    // ---- moments of b: the recolouring weight D = sum_i f**_i b_i and the flux direction Q1
+    float Dsum, Q1x = 0.0f, Q1y = 0.0f, Q1z = 0.0f;
+    {
+        float t[27];
+#pragma unroll
+        for (int c = 0; c < 27; ++c) t[c] = L_s[c * 128].y;
+        // Q1 = 27/19 sum_{i>=1} b_i w_i c_i / |c_i|
+#pragma unroll
+        for (int i = 1; i < 27; ++i) {
+            const float v = t[cell(i)] * (k27 * wgt(i) * inv_cnorm(i));
+            Q1x += (float)cx(i) * v; Q1y += (float)cy(i) * v; Q1z += (float)cz(i) * v;
+        }
+        // sum_i b_i h_i = sum_t C_t (psi moments of b)
+        float tb[27];
+#pragma unroll
+        for (int c = 0; c < 27; ++c) tb[c] = t[c];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) sweep_inv_T(tb[q], tb[9 + q], tb[18 + q], Ax);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sweep_inv_T(tb[p * 9 + c], tb[p * 9 + 3 + c], tb[p * 9 + 6 + c], Ay);
+#pragma unroll
+        for (int p = 0; p < 9; ++p) sweep_inv_T(tb[p * 3], tb[p * 3 + 1], tb[p * 3 + 2], Az);
+        const float bh = k200 * tb[18] + k020 * tb[6] + k002 * tb[2] + k110 * tb[12] + k101 * tb[10] + k011 * tb[4];
+        RawMom B;
+        raw_moments(t, B);
+        const float B1u = B.m100 * ux + B.m010 * uy + B.m001 * uz;
+        float Bux, Buy, Buz;
+        m2v(B, ux, uy, uz, Bux, Buy, Buz);
+        float B3x, B3y, B3z;
+        m3uu(B, ux, uy, uz, B3x, B3y, B3z);
+        const float uBu = ux * Bux + uy * Buy + uz * Buz;
+        const float B3uuu = ux * B3x + uy * B3y + uz * B3z;
+        float Bgx, Bgy, Bgz;
+        m2v(B, gpx, gpy, gpz, Bgx, Bgy, Bgz);
+        Dsum = rho * fmaf(alpha, b0, k27 * oma * (B.m000 - w0 * b0));
+        Dsum = fmaf(rho, 3.0f * B1u + 4.5f * uBu - 1.5f * usq * B.m000 + 4.5f * B3uuu - 4.5f * usq * B1u, Dsum);
+        Dsum += -3.0f * nu * ugr * b0 + 9.0f * nu * (grx * Bux + gry * Buy + grz * Buz);
+        if (kForce)
+            Dsum += 0.5f * (3.0f * (B.m100 * Fx + B.m010 * Fy + B.m001 * Fz) - 3.0f * uF * B.m000 +
+                            9.0f * (Fx * Bux + Fy * Buy + Fz * Buz));
+        Dsum += bh;
+        Dsum = fmaf(pert, gpx * Bgx + gpy * Bgy + gpz * Bgz - g2 * (B.m000 - (2.0f / 3.0f) * b0), Dsum);
+    }
 
     // ---- recolouring: S^r = (rho_r/rho) f** + seg, S^b = (rho_b/rho) f** - seg
-    float lrr = l_xr * inv_rho, lrb = l_xb * inv_rho;
-    float lrho = -(l_xr * rr + l_xb * rb) * inv_rho * inv_rho;
-    const float lR = s_bcv * inv_gm;
-    float lalpha = R * inv_gm * s_bcd;
+    float lrr = Dsum * rb * inv_rho * inv_rho, lrb = -Dsum * rr * inv_rho * inv_rho;
+    float lrho = 0.0f;
+    const float gQ1 = gpx * Q1x + gpy * Q1y + gpz * Q1z;
+    const float lR = oma * gQ1 * inv_gm;
+    float lalpha = -R * inv_gm * gQ1;
     lrr = fmaf(lR * a.beta, rb * inv_rho, lrr);
     lrb = fmaf(lR * a.beta, rr * inv_rho, lrb);
     lrho = fmaf(-lR, R * inv_rho, lrho);
-    float lgpx = R * inv_gm * v_seg[0], lgpy = R * inv_gm * v_seg[1], lgpz = R * inv_gm * v_seg[2];
+    const float sq = R * inv_gm * oma;
+    float lgpx = sq * Q1x, lgpy = sq * Q1y, lgpz = sq * Q1z;
     float lgm = -R * lR * inv_gm;
-    // ---- perturbation: Omega2_i = A (w_i cgp^2 - B_i |g|^2) / |g|_eps
-    const float lA = s_pert * inv_gm;
-    lgpx = fmaf(2.0f * pert, v_pgp[0], lgpx);
-    lgpy = fmaf(2.0f * pert, v_pgp[1], lgpy);
-    lgpz = fmaf(2.0f * pert, v_pgp[2], lgpz);
-    float lg2 = -pert * s_B;
-    lgm = fmaf(-lA, pert, lgm);
-    lg2 = fmaf(lgm, 0.5f * inv_gm, lg2);
-    lgpx = fmaf(2.0f * gpx, lg2, lgpx);
-    lgpy = fmaf(2.0f * gpy, lg2, lgpy);
-    lgpz = fmaf(2.0f * gpz, lg2, lgpz);
-    // ---- equilibrium f^e_i = rho (varphi_i(alpha) + w_i poly_i(u)) + Phi_i(nu, u, grad rho)
-    lrho += s_fe;
-    lalpha = fmaf(rho, s_dvp, lalpha);
-    float lux = rho * fmaf(ux, s_u, v_dp[0]);
-    float luy = rho * fmaf(uy, s_u, v_dp[1]);
-    float luz = rho * fmaf(uz, s_u, v_dp[2]);
-    float lnu = fmaf(-3.0f * a0, ugr, s_nu);
-    lux = fmaf(nu, fmaf(-3.0f * a0, grx, v_nug[0]), lux);
-    luy = fmaf(nu, fmaf(-3.0f * a0, gry, v_nug[1]), luy);
-    luz = fmaf(nu, fmaf(-3.0f * a0, grz, v_nug[2]), luz);
-    float lgrx = nu * fmaf(-3.0f * a0, ux, v_nuu[0]);
-    float lgry = nu * fmaf(-3.0f * a0, uy, v_nuu[1]);
-    float lgrz = nu * fmaf(-3.0f * a0, uz, v_nuu[2]);
-    // ---- forcing F'_i = w_i (3 (c_i - u).F + 9 (c_i.u)(c_i.F)), weight 1/2 in f*
-    float lFx = 0.0f, lFy = 0.0f, lFz = 0.0f;
-    if (kForce) {
-        lux += 0.5f * (-3.0f * Fx * s_w + 9.0f * v_wcF[0]);
-        luy += 0.5f * (-3.0f * Fy * s_w + 9.0f * v_wcF[1]);
-        luz += 0.5f * (-3.0f * Fz * s_w + 9.0f * v_wcF[2]);
-        lFx = 0.5f * (3.0f * v_wc[0] - 3.0f * ux * s_w + 9.0f * v_wcu[0]);
-        lFy = 0.5f * (3.0f * v_wc[1] - 3.0f * uy * s_w + 9.0f * v_wcu[1]);
-        lFz = 0.5f * (3.0f * v_wc[2] - 3.0f * uz * s_w + 9.0f * v_wcu[2]);
+
+    // ---- moments of a: perturbation, equilibrium, forcing
+    float lux, luy, luz, lnu, lgrx, lgry, lgrz, lFx = 0.0f, lFy = 0.0f, lFz = 0.0f, lA;
+    {
+        float t[27];
+#pragma unroll
+        for (int c = 0; c < 27; ++c) t[c] = L_s[c * 128].x;
+        RawMom A;
+        raw_moments(t, A);
+        const float sB = A.m000 - (2.0f / 3.0f) * a0;  // sum_i a_i B_i
+        float Agx, Agy, Agz, Aux, Auy, Auz, Arx, Ary, Arz;
+        m2v(A, gpx, gpy, gpz, Agx, Agy, Agz);
+        m2v(A, ux, uy, uz, Aux, Auy, Auz);
+        m2v(A, grx, gry, grz, Arx, Ary, Arz);
+        // perturbation Omega2_i = A (w_i cgp^2 - B_i |g|^2) / |g|_eps
+        lA = (gpx * Agx + gpy * Agy + gpz * Agz - g2 * sB) * inv_gm;
+        lgpx = fmaf(2.0f * pert, Agx, lgpx);
+        lgpy = fmaf(2.0f * pert, Agy, lgpy);
+        lgpz = fmaf(2.0f * pert, Agz, lgpz);
+        float lg2 = -pert * sB;
+        lgm = fmaf(-lA, pert, lgm);
+        lg2 = fmaf(lgm, 0.5f * inv_gm, lg2);
+        lgpx = fmaf(2.0f * gpx, lg2, lgpx);
+        lgpy = fmaf(2.0f * gpy, lg2, lgpy);
+        lgpz = fmaf(2.0f * gpz, lg2, lgpz);
+        part[0] += lA * 2.25f / tau;
+        // equilibrium f^e_i = rho (varphi_i(alpha) + w_i poly_i(u)) + Phi_i(nu, u, grad rho)
+        const float A1u = A.m100 * ux + A.m010 * uy + A.m001 * uz;
+        float A3x, A3y, A3z;
+        m3uu(A, ux, uy, uz, A3x, A3y, A3z);
+        const float uAu = ux * Aux + uy * Auy + uz * Auz;
+        const float A3uuu = ux * A3x + uy * A3y + uz * A3z;
+        lrho += fmaf(alpha, a0, k27 * oma * (A.m000 - w0 * a0)) + 3.0f * A1u + 4.5f * uAu - 1.5f * usq * A.m000 +
+                4.5f * A3uuu - 4.5f * usq * A1u;
+        lalpha = fmaf(rho, a0 - k27 * (A.m000 - w0 * a0), lalpha);
+        const float c3 = 3.0f - 4.5f * usq, s_u = -3.0f * A.m000 - 9.0f * A1u;
+        lux = rho * (c3 * A.m100 + 9.0f * Aux + 13.5f * A3x + ux * s_u);
+        luy = rho * (c3 * A.m010 + 9.0f * Auy + 13.5f * A3y + uy * s_u);
+        luz = rho * (c3 * A.m001 + 9.0f * Auz + 13.5f * A3z + uz * s_u);
+        lnu = -3.0f * a0 * ugr + 9.0f * (ux * Arx + uy * Ary + uz * Arz);
+        lux = fmaf(nu, fmaf(-3.0f * a0, grx, 9.0f * Arx), lux);
+        luy = fmaf(nu, fmaf(-3.0f * a0, gry, 9.0f * Ary), luy);
+        luz = fmaf(nu, fmaf(-3.0f * a0, grz, 9.0f * Arz), luz);
+        lgrx = nu * fmaf(-3.0f * a0, ux, 9.0f * Aux);
+        lgry = nu * fmaf(-3.0f * a0, uy, 9.0f * Auy);
+        lgrz = nu * fmaf(-3.0f * a0, uz, 9.0f * Auz);
+        // forcing F'_i = w_i (3 (c_i - u).F + 9 (c_i.u)(c_i.F)), weight 1/2 in f*
+        if (kForce) {
+            float AFx, AFy, AFz;
+            m2v(A, Fx, Fy, Fz, AFx, AFy, AFz);
+            lux += 0.5f * (-3.0f * Fx * A.m000 + 9.0f * AFx);
+            luy += 0.5f * (-3.0f * Fy * A.m000 + 9.0f * AFy);
+            luz += 0.5f * (-3.0f * Fz * A.m000 + 9.0f * AFz);
+            lFx = 0.5f * (3.0f * A.m100 - 3.0f * ux * A.m000 + 9.0f * Aux);
+            lFy = 0.5f * (3.0f * A.m010 - 3.0f * uy * A.m000 + 9.0f * Auy);
+            lFz = 0.5f * (3.0f * A.m001 - 3.0f * uz * A.m000 + 9.0f * Auz);
+        }
     }
     // ---- h_i = sum_t C_t psi_t,i(u): lambda_C_t and d/du via the transposed 1-D sweeps
-    // M[a][b][c] = sum_i lh_i G_a[cx](ux) G_b[cy](uy) G_c[cz](uz)
+    float l200, l020, l002, l110, l101, l011;
+    {
+        float lh[27];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) sweep_inv_T(lh[q], lh[9 + q], lh[18 + q], Ax);
+        for (int c = 0; c < 27; ++c) lh[c] = L_s[c * 128].x;
 #pragma unroll
-    for (int a0_ = 0; a0_ < 3; ++a0_)
+        for (int q = 0; q < 9; ++q) sweep_inv_T(lh[q], lh[9 + q], lh[18 + q], Ax);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sweep_inv_T(lh[a0_ * 9 + 0 + c], lh[a0_ * 9 + 3 + c], lh[a0_ * 9 + 6 + c], Ay);
+        for (int a0_ = 0; a0_ < 3; ++a0_)
 #pragma unroll
-    for (int p = 0; p < 9; ++p) sweep_inv_T(lh[p * 3 + 0], lh[p * 3 + 1], lh[p * 3 + 2], Az);
+            for (int c = 0; c < 3; ++c) sweep_inv_T(lh[a0_ * 9 + 0 + c], lh[a0_ * 9 + 3 + c], lh[a0_ * 9 + 6 + c], Ay);
+#pragma unroll
+        for (int p = 0; p < 9; ++p) sweep_inv_T(lh[p * 3 + 0], lh[p * 3 + 1], lh[p * 3 + 2], Az);
 #define MM(p, q, r) lh[(p) * 9 + (q) * 3 + (r)]
-    const float l200 = MM(2, 0, 0), l020 = MM(0, 2, 0), l002 = MM(0, 0, 2);
-    const float l110 = MM(1, 1, 0), l101 = MM(1, 0, 1), l011 = MM(0, 1, 1);
-    // dG0/du = G1, dG1/du = 2 G2, dG2/du = 0
-    lux += k020 * MM(1, 2, 0) + k002 * MM(1, 0, 2) + 2.0f * k110 * MM(2, 1, 0) + 2.0f * k101 * MM(2, 0, 1) + k011 * MM(1, 1, 1);
-    luy += k200 * MM(2, 1, 0) + k002 * MM(0, 1, 2) + 2.0f * k110 * MM(1, 2, 0) + k101 * MM(1, 1, 1) + 2.0f * k011 * MM(0, 2, 1);
-    luz += k200 * MM(2, 0, 1) + k020 * MM(0, 2, 1) + k110 * MM(1, 1, 1) + 2.0f * k101 * MM(1, 0, 2) + 2.0f * k011 * MM(0, 1, 2);
+        l200 = MM(2, 0, 0); l020 = MM(0, 2, 0); l002 = MM(0, 0, 2);
+        l110 = MM(1, 1, 0); l101 = MM(1, 0, 1); l011 = MM(0, 1, 1);
+        // dG0/du = G1, dG1/du = 2 G2, dG2/du = 0
+        lux += k020 * MM(1, 2, 0) + k002 * MM(1, 0, 2) + 2.0f * k110 * MM(2, 1, 0) + 2.0f * k101 * MM(2, 0, 1) + k011 * MM(1, 1, 1);
+        luy += k200 * MM(2, 1, 0) + k002 * MM(0, 1, 2) + 2.0f * k110 * MM(1, 2, 0) + k101 * MM(1, 1, 1) + 2.0f * k011 * MM(0, 2, 1);
+        luz += k200 * MM(2, 0, 1) + k020 * MM(0, 2, 1) + k110 * MM(1, 1, 1) + 2.0f * k101 * MM(1, 0, 2) + 2.0f * k011 * MM(0, 1, 2);
 #undef MM
+    }
     // ---- relaxation C = (1 - s2nu) dev Q + (1 - s2b) (tr Q / 3) I
     const float trl = l200 + l020 + l002;
     const float lQxx = o2 * (l200 - trl * third) + o2b * trl * third;
@@ -326,7 +387,6 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     lgry -= nu * fmaf(2.0f, Luy, Ltr * uy);
     lgrz -= nu * fmaf(2.0f, Luz, Ltr * uz);
     // ---- sigma, tau, nu (harmonic mean), alpha-bar
-    part[0] += lA * 2.25f / tau;
     const float ltau = -lA * Acoef / tau - ls2nu * s2nu * s2nu;
     lnu = fmaf(3.0f, ltau, lnu);
     const float lH = -lnu * nu * nu;
@@ -388,13 +448,18 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     }
 }
 
+#ifndef LBCM_ADJ_MIN_BLOCKS
+#define LBCM_ADJ_MIN_BLOCKS 4
+#endif
 template <bool kForce>
-__global__ void __launch_bounds__(128) adj_collide_kernel(StepArgs a, AdjArgs g) {
+__global__ void __launch_bounds__(128, LBCM_ADJ_MIN_BLOCKS) adj_collide_kernel(StepArgs a, AdjArgs g) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
+    __shared__ float2 L_s[27 * 128];
+    const int t = threadIdx.y * 32 + threadIdx.x;
     float part[3] = {0.0f, 0.0f, 0.0f};
-    if (x < a.nx && y < a.ny) adj_collide_node<kForce>(a, g, x, y, z, part);
+    if (x < a.nx && y < a.ny) adj_collide_node<kForce>(a, g, x, y, z, part, L_s + t);
     block_accumulate<3>(part, g.acc_coll, block_id());
 }
 
@@ -426,93 +491,103 @@ __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g)
         lphi = fmaf(w3, (float)cx(j) * A.x + (float)cy(j) * A.y + czj * A.z, lphi);
         lrho = fmaf(w3, (float)cx(j) * A.w + (float)cy(j) * B.x + czj * B.y, lrho);
     }
-    const float2 ph = __ldg(a.phase + nb.n);  // (phi, rho) of this node
-    const float S_ = ph.y / (a.rho_r0 * 0.5f * (1.0f + ph.x) + a.rho_b0 * 0.5f * (1.0f - ph.x));
+    float phv, S_;  // phi and rho_r/rho_r0 + rho_b/rho_b0 of this node
+    if (g.rec) {
+        const float4 r0 = __ldg(g.rec + nb.n);
+        phv = order_parameter(r0.x, r0.y, a.inv_rho_r0, a.inv_rho_b0);
+        S_ = r0.x * a.inv_rho_r0 + r0.y * a.inv_rho_b0;
+    } else {
+        const float2 ph = __ldg(a.phase + nb.n);  // (phi, rho)
+        phv = ph.x;
+        S_ = ph.y / (a.rho_r0 * 0.5f * (1.0f + ph.x) + a.rho_b0 * 0.5f * (1.0f - ph.x));
+    }
     const float t = lphi / S_;
-    g.lr_out[nb.n] = make_float2(fmaf(t * (1.0f - ph.x), a.inv_rho_r0, lrho), fmaf(-t * (1.0f + ph.x), a.inv_rho_b0, lrho));
+    g.lr_out[nb.n] = make_float2(fmaf(t * (1.0f - phv), a.inv_rho_r0, lrho), fmaf(-t * (1.0f + phv), a.inv_rho_b0, lrho));
 }
 
 // ----------------------------------------------- inlet gradients and outflow transpose
-__global__ void __launch_bounds__(256) adj_boundary_kernel(StepArgs a, AdjArgs g) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+// One warp per (x, y) column, lane i < 27 handling direction i (both colours).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g) {
+    const int lane = threadIdx.x & 31;
+    const long long col = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
     float part[17];
 #pragma unroll
     for (int k = 0; k < 17; ++k) part[k] = 0.0f;
-    if (x < a.nx && y < a.ny) {
-        const size_t P = (size_t)a.plane, pxy = (size_t)y * a.nx + x;
-        if (a.bc_zlo == BC_INLET) {
-            const float lrr0 = g.lr_out[pxy].x;  // deferred red density adjoint of (x, y, 0)
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                if (cz(i) != 1) continue;
-                const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
-                if (!a.disc[(size_t)ys * a.nx + xs]) continue;
-                const float lam = g.li[(size_t)zrank(i) * P + pxy] + lrr0;
+    if (col < a.plane) {  // warp-uniform
+        const int x = (int)(col % a.nx), y = (int)(col / a.nx);
+        const size_t P = (size_t)a.plane, pxy = (size_t)col;
+        const int i = lane < 27 ? lane : 0;
+        const int cxi = (int)((kPackX >> (2 * i)) & 3ull) - 1, cyi = (int)((kPackY >> (2 * i)) & 3ull) - 1,
+                  czi = (int)((kPackZ >> (2 * i)) & 3ull) - 1;
+        const int q = cxi * cxi + cyi * cyi + czi * czi;
+        const float w_i = q == 0 ? 8.0f / 27.0f : q == 1 ? 2.0f / 27.0f : q == 2 ? 1.0f / 54.0f : 1.0f / 216.0f;
+        if (a.bc_zlo == BC_INLET && lane < 27 && czi == 1) {
+            const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny);
+            if (a.disc[(size_t)ys * a.nx + xs]) {
+                // rank of i among the c_z = +1 directions
+                int zr = 0;
+                for (int j = 0; j < i; ++j) zr += ((int)((kPackZ >> (2 * j)) & 3ull) - 1) == 1;
+                const float lam = g.li[(size_t)zr * P + pxy] + g.lr_out[pxy].x;
                 InletVel iv;
                 inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
-                const float c0 = (float)cx(i), c1 = (float)cy(i), c2 = (float)cz(i);
+                const float c0 = (float)cxi, c1 = (float)cyi, c2 = (float)czi;
                 const float cu = c0 * iv.ux + c1 * iv.uy + c2 * iv.uz;
                 const float usq = iv.ux * iv.ux + iv.uy * iv.uy + iv.uz * iv.uz;
                 // d f^e_i / d u = rho_r0 w_i [(3 + 9 cu + 27/2 cu^2 - 9/2 u^2) c_i - (3 + 9 cu) u]
-                const float sc = lam * a.rho_r0 * wgt(i);
+                const float sc = lam * a.rho_r0 * w_i;
                 const float dp = fmaf(13.5f * cu, cu, fmaf(9.0f, cu, 3.0f)) - 4.5f * usq;
                 const float du = fmaf(-9.0f, cu, -3.0f);
                 const float gx_ = sc * fmaf(c0, dp, du * iv.ux);
                 const float gy_ = sc * fmaf(c1, dp, du * iv.uy);
                 const float gz_ = sc * fmaf(c2, dp, du * iv.uz);
-                part[0] += gx_ * iv.dux + gy_ * iv.duy + gz_ * iv.prof;
+                part[0] = gx_ * iv.dux + gy_ * iv.duy + gz_ * iv.prof;
 #pragma unroll
                 for (int m = 1; m <= 8; ++m) {
-                    part[2 * m - 1] = fmaf(gz_ * a.u_in, iv.cm[m], part[2 * m - 1]);
-                    part[2 * m] = fmaf(gz_ * a.u_in, iv.sm[m], part[2 * m]);
+                    part[2 * m - 1] = gz_ * a.u_in * iv.cm[m];
+                    part[2 * m] = gz_ * a.u_in * iv.sm[m];
                 }
             }
         }
         if (a.bc_zhi == BC_CONVECTIVE) {
             const int N = a.nz - 1, zm = N - 1;
             const Nbr nbm(a, x, y, zm);
-            float fr[27], fb[27];
-            float rho = 0.0f, jz = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const float2 v = load_pop<STORE_FP32>(a, i, nbm.src(i), make_float2(0.0f, 0.0f));
-                fr[i] = v.x;
-                fb[i] = v.y;
+            // the source of f_i(x, y, N-1) (plain pull: 1 <= N-1)
+            const int src = nbm.zo[czi + 1] + nbm.yo[cyi + 1] + nbm.xo[cxi + 1];
+            float fr = 0.0f, fb = 0.0f;
+            if (lane < 27) {  // f(N-1) as the forward step pulled it
+                fr = __ldg(g.fm + (size_t)i * P + pxy);
+                fb = __ldg(g.fm + (size_t)(27 + i) * P + pxy);
             }
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const float s = fr[i] + fb[i];
-                rho += s;
-                if (cz(i) != 0) jz += (float)cz(i) * s;
-            }
+            const float s_ = fr + fb;
+            const float rho = warp_sum(s_), jz = warp_sum((float)czi * s_);
             const float Fz = (rho - a.rho_b0) * a.gz;
             const float lam_raw = (jz + 0.5f * Fz) / rho;
             const float lam = fminf(fmaxf(lam_raw, 0.0f), 1.0f);
             const float inv = 1.0f / (1.0f + lam);
             const float2 lrN = g.lr_out[(size_t)N * P + pxy];
-            float lvr[27], lvb[27];
-            float llam = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const size_t hr = (size_t)i * P + pxy, hb = (size_t)(27 + i) * P + pxy;
-                lvr[i] = g.lc[hr] + lrN.x + g.lh_in[hr];
-                lvb[i] = g.lc[hb] + lrN.y + g.lh_in[hb];
-                g.lh_out[hr] = lvr[i] * inv;
-                g.lh_out[hb] = lvb[i] * inv;
-                llam = fmaf(lvr[i], fr[i] - a.hist_out[hr], llam);
-                llam = fmaf(lvb[i], fb[i] - a.hist_out[hb], llam);
+            float lvr = 0.0f, lvb = 0.0f, part_l = 0.0f;
+            const size_t hr = (size_t)i * P + pxy, hb = (size_t)(27 + i) * P + pxy;
+            if (lane < 27) {
+                lvr = g.lc[hr] + lrN.x + g.lh_in[hr];
+                lvb = g.lc[hb] + lrN.y + g.lh_in[hb];
+                g.lh_out[hr] = lvr * inv;
+                g.lh_out[hb] = lvb * inv;
+                part_l = fmaf(lvr, fr - a.hist_out[hr], lvb * (fb - a.hist_out[hb]));
             }
-            llam *= inv;
-            const bool active = lam_raw > 0.0f && lam_raw < 1.0f;
-            const float inv_rho = 1.0f / rho;
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const float dl = active ? llam * ((float)cz(i) + 0.5f * a.gz - lam_raw) * inv_rho : 0.0f;
-                float2 *slot = g.lp_out + (size_t)i * a.NN + nbm.src(i);
+            const float llam = warp_sum(part_l) * inv;
+            if (lane < 27) {
+                const bool active = lam_raw > 0.0f && lam_raw < 1.0f;
+                const float dl = active ? llam * ((float)czi + 0.5f * a.gz - lam_raw) / rho : 0.0f;
+                float2 *slot = g.lp_out + (size_t)i * a.NN + src;
                 float2 v = *slot;
-                v.x += fmaf(lvr[i], lam * inv, dl);
-                v.y += fmaf(lvb[i], lam * inv, dl);
+                v.x += fmaf(lvr, lam * inv, dl);
+                v.y += fmaf(lvb, lam * inv, dl);
                 *slot = v;
             }
         }
@@ -647,8 +722,8 @@ __global__ void __launch_bounds__(256) adj_state_kernel(StepArgs a, AdjArgs g, f
 // ------------------------------------------------------------------------ launchers
 static dim3 node_block() { return dim3(32, 4, 1); }
 static dim3 node_grid(const StepArgs &a) { return dim3((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz); }
-static dim3 col_block() { return dim3(32, 8, 1); }
-static dim3 col_grid(const StepArgs &a) { return dim3((a.nx + 31) / 32, (a.ny + 7) / 8, 1); }
+static dim3 col_block() { return dim3(128, 1, 1); }  // four columns, one warp each
+static dim3 col_grid(const StepArgs &a) { return dim3((unsigned)((a.plane + 3) / 4), 1, 1); }
 
 long long adj_collide_blocks(const StepArgs &a) {
     const dim3 gr = node_grid(a);

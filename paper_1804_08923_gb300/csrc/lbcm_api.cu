@@ -129,11 +129,10 @@ struct lb_ctx {
     struct {
         void *base = nullptr;
         size_t bytes = 0;
-        float2 *ckpt_pop = nullptr, *seg_pop = nullptr, *seg_phase = nullptr, *lp[2] = {}, *lr[2] = {}, *lgb = nullptr,
-               *objph = nullptr;
-        float *ckpt_hist = nullptr, *seg_zin = nullptr, *seg_zout = nullptr, *seg_hist = nullptr, *lc = nullptr,
+        float2 *ckpt_pop = nullptr, *seg_pop = nullptr, *lp[2] = {}, *lr[2] = {}, *lgb = nullptr, *objph = nullptr;
+        float *ckpt_hist = nullptr, *seg_rec4 = nullptr, *seg_fm = nullptr, *seg_hist = nullptr, *lc = nullptr,
               *li = nullptr, *lh[2] = {};
-        float4 *lga = nullptr;
+        float4 *lga = nullptr, *seg_rec = nullptr;
         double *acc_coll = nullptr, *acc_inlet = nullptr, *acc_obj = nullptr, *out = nullptr;
         long long nblk_coll = 0, nblk_inlet = 0;
         int cl = 0;
@@ -897,8 +896,10 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     const size_t pb = 27 * NN * sizeof(float2), hb = 54 * P * sizeof(float), nb2 = NN * sizeof(float2);
     StepArgs a0 = make_args(c);
     const long long nblk_coll = adj_collide_blocks(a0), nblk_inlet = adj_boundary_blocks(a0);
-    const size_t parts[] = {nseg * pb, nseg * hb, (k + 1) * pb, k * nb2, k * 18 * P * sizeof(float),
-                            k * 18 * P * sizeof(float), (k + 1) * hb, pb, pb, nb2, nb2, NN * sizeof(float4), nb2,
+    // per recomputed step: the collision inputs (68 B a node), f(N-1) and hist(n+1) of the
+    // outflow plane; the populations themselves only in two alternating buffers
+    const size_t parts[] = {nseg * pb, nseg * hb, 2 * pb, k * 4 * NN * sizeof(float4), k * NN * sizeof(float),
+                            k * hb, (k + 1) * hb, pb, pb, nb2, nb2, NN * sizeof(float4), nb2,
                             hb, 9 * P * sizeof(float), hb, hb, nblk_coll * 3 * sizeof(double),
                             nblk_inlet * 17 * sizeof(double), nblk_coll * sizeof(double), 32 * sizeof(double), nb2};
     size_t need = 0;
@@ -922,7 +923,7 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
         for (int q = 0; q < 22; ++q) take(v[q]);
         auto &w = c->adj;
         w.ckpt_pop = (float2 *)v[0]; w.ckpt_hist = (float *)v[1]; w.seg_pop = (float2 *)v[2];
-        w.seg_phase = (float2 *)v[3]; w.seg_zin = (float *)v[4]; w.seg_zout = (float *)v[5];
+        w.seg_rec = (float4 *)v[3]; w.seg_rec4 = (float *)v[4]; w.seg_fm = (float *)v[5];
         w.seg_hist = (float *)v[6]; w.lp[0] = (float2 *)v[7]; w.lp[1] = (float2 *)v[8]; w.lr[0] = (float2 *)v[9];
         w.lr[1] = (float2 *)v[10]; w.lga = (float4 *)v[11]; w.lgb = (float2 *)v[12]; w.lc = (float *)v[13];
         w.li = (float *)v[14]; w.lh[0] = (float *)v[15]; w.lh[1] = (float *)v[16]; w.acc_coll = (double *)v[17];
@@ -974,15 +975,17 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     }
 
     // reverse sweep: recompute each segment from its checkpoint, then step back through it
+    // step t of a segment: populations alternate between two buffers; the phase field and the
+    // boundary planes are the context's scratch; what the reverse needs is kept per step
     auto seg_args = [&](long long t, int64_t step) {
         StepArgs a = make_args(c);
-        a.pin = w.seg_pop + t * 27 * NN;
-        a.pout = w.seg_pop + (t + 1) * 27 * NN;
-        a.phase = w.seg_phase + t * NN;
-        a.zin = w.seg_zin + t * 18 * P;
-        a.zout = w.seg_zout + t * 18 * P;
+        a.pin = w.seg_pop + (t & 1) * 27 * NN;
+        a.pout = w.seg_pop + ((t + 1) & 1) * 27 * NN;
         a.hist_in = w.seg_hist + t * 54 * P;
         a.hist_out = w.seg_hist + (t + 1) * 54 * P;
+        a.rec = w.seg_rec + t * 4 * NN;
+        a.rec4 = w.seg_rec4 + t * NN;
+        a.fm_out = conv ? w.seg_fm + t * 54 * P : nullptr;
         a.step = step;
         return a;
     };
@@ -996,6 +999,9 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
         }
         for (long long t = len - 1; t >= 0; --t) {
             AdjArgs gs = g;
+            gs.rec = w.seg_rec + t * 4 * NN;
+            gs.rec4 = w.seg_rec4 + t * NN;
+            gs.fm = w.seg_fm + t * 54 * P;
             gs.lp_in = w.lp[cl]; gs.lr_in = w.lr[cl];
             gs.lp_out = w.lp[cl ^ 1]; gs.lr_out = w.lr[cl ^ 1];
             gs.lh_in = w.lh[ch]; gs.lh_out = w.lh[ch ^ 1];

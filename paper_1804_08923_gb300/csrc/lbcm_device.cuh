@@ -154,6 +154,13 @@ struct StepArgs {
     float u_in, noise_amp, xc, yc;
     float shift_r[4], shift_b[4];       // varphi_i(alpha_k) by speed class |c|^2 = 1..3 (FP16 shift)
     float fourier[16];                  // inlet profile coefficients a_1, b_1, ..., a_8, b_8
+    // optional outputs for the adjoint's recompute (NULL otherwise): the collision inputs of
+    // every node, rec[0..3][NN] = (rho_r, rho_b, jx, jy), (jz, Pxx, Pyy, Pzz), (Pxy, Pxz, Pyz,
+    // gpx), (gpy, gpz, grx, gry) and rec4[NN] = grz; fm_out[2][27][nx ny] = f(N-1, t+1) of the
+    // outflow columns
+    float4 *__restrict__ rec;
+    float *__restrict__ rec4;
+    float *__restrict__ fm_out;
     unsigned long long seed;
     long long step;  // index of the step being taken (state t -> t+1 uses t)
 };

@@ -8,8 +8,10 @@ namespace lbcm {
 // storage STORE_FP32 or STORE_FP16.  When ev is not
 // NULL, ev[0..3] are recorded before the boundary kernel, before the phase-field kernel,
 // before the collision kernel and after it.  *launches is increased by the number of
-// kernels launched.
-cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches);
+// kernels launched.  collide = false stops after the phase-field kernel (boundary planes and
+// phase field of the step, no new populations; ev[3] is then not recorded).
+cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches,
+                        bool collide = true);
 
 // Adjoint state and scratch of one reverse step (FP32 populations, paper rates).
 //   lp_in / lr_in   lambda of S(n+1): pushed part [27][NN] float2 and deferred density part [NN]
@@ -20,7 +22,11 @@ cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEven
 //   lh_in / lh_out  lambda of the outflow history hist(n+1) / hist(n) [54][nx ny]
 //   acc_coll        FP64 per-block sums of dJ/d(sigma, nu_r, nu_b) [blocks][3]
 //   acc_inlet       FP64 per-block sums of dJ/d(u_in, a_1, b_1, ..., a_8, b_8) [blocks][17]
+//   rec, rec4       the forward step's collision inputs per node (as StepArgs::rec, rec4)
+//   fm              the forward step's f(N-1) of the outflow columns [54][nx ny]
 struct AdjArgs {
+    const float4 *rec;
+    const float *rec4, *fm;
     const float2 *lp_in, *lr_in;
     float2 *lp_out, *lr_out;
     float4 *lga;
@@ -34,8 +40,8 @@ struct AdjArgs {
 // Blocks of the collide-adjoint and boundary-adjoint grids (sizes of acc_coll, acc_inlet).
 long long adj_collide_blocks(const StepArgs &a);
 long long adj_boundary_blocks(const StepArgs &a);
-// Reverse of the step described by a (pin = S(n), phase / zin / zout / hist_in / hist_out as
-// the forward step n wrote them).
+// Reverse of the step described by a (hist_in / hist_out as the forward step n wrote them;
+// its populations are not read: g.rec and g.fm hold what the reverse needs of step n).
 cudaError_t launch_adjoint_step(const StepArgs &a, const AdjArgs &g, cudaStream_t s, long long *launches);
 // Objective of the state a.pin (0 interface area, args[0] = eps; 1 penetration length,
 // args[0] = delta): scalar[0] = J; writes lambda_S(T) into g.lp_out / g.lr_out.

@@ -43,77 +43,75 @@
 namespace lbcm {
 
 // ------------------------------------------------------------------ boundary planes
-template <int S>
-__global__ void __launch_bounds__(256) boundary_plane_kernel(StepArgs a) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    const long long P = a.plane, pxy = (long long)y * a.nx + x;
-    const int N = a.nz - 1;
+// One warp per (x, y) column; lane i < 27 handles direction i.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
-    if (a.bc_zlo == BC_INLET || a.bc_zlo == BC_FREESLIP) {
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            if (cz(i) != 1) continue;
-            const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
-            float vr, vb;
-            if (a.bc_zlo == BC_INLET && a.disc[(long long)ys * a.nx + xs]) {
-                // red equilibrium f^e(rho_r0, u_in) with alpha_r and Phi = 0, no blue
-                InletVel iv;
-                inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
-                const float ux = iv.ux, uy = iv.uy, uz = iv.uz;
-                const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
-                const float usq = ux * ux + uy * uy + uz * uz;
-                vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
-                vb = 0.0f;
-            } else {  // half-way specular reflection at z = -1/2
-                const float2 v = load_pop<S>(a, mirror_z(i), ys * a.nx + xs, reader_shift<S>(a, (int)pxy));
-                vr = v.x;
-                vb = v.y;
-            }
-            a.zin[(long long)zrank(i) * P + pxy] = vr;
-            a.zin[(long long)(9 + zrank(i)) * P + pxy] = vb;
+template <int S>
+__global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long col = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (col >= a.plane) return;  // whole warps leave together
+    const int x = (int)(col % a.nx), y = (int)(col / a.nx);
+    const long long P = a.plane, pxy = col;
+    const int N = a.nz - 1;
+    const int i = lane < 27 ? lane : 0;
+    const int cxi = cx(i), cyi = cy(i), czi = cz(i);
+    const bool mine = lane < 27;
+
+    if ((a.bc_zlo == BC_INLET || a.bc_zlo == BC_FREESLIP) && mine && czi == 1) {
+        const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny);
+        float vr, vb;
+        if (a.bc_zlo == BC_INLET && a.disc[(long long)ys * a.nx + xs]) {
+            // red equilibrium f^e(rho_r0, u_in) with alpha_r and Phi = 0, no blue
+            InletVel iv;
+            inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
+            const float cu = (float)cxi * iv.ux + (float)cyi * iv.uy + (float)czi * iv.uz;
+            const float usq = iv.ux * iv.ux + iv.uy * iv.uy + iv.uz * iv.uz;
+            vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
+            vb = 0.0f;
+        } else {  // half-way specular reflection at z = -1/2
+            const float2 v = load_pop<S>(a, mirror_z(i), ys * a.nx + xs, reader_shift<S>(a, (int)pxy));
+            vr = v.x;
+            vb = v.y;
         }
+        a.zin[(long long)zrank(i) * P + pxy] = vr;
+        a.zin[(long long)(9 + zrank(i)) * P + pxy] = vb;
     }
-    if (a.bc_zhi == BC_FREESLIP) {
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            if (cz(i) != -1) continue;
-            const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny);
-            const float2 v = load_pop<S>(a, mirror_z(i), (N * a.ny + ys) * a.nx + xs,
-                                         reader_shift<S>(a, N * (int)P + (int)pxy));
-            a.zout[(long long)zrank(i) * P + pxy] = v.x;
-            a.zout[(long long)(9 + zrank(i)) * P + pxy] = v.y;
-        }
+    if (a.bc_zhi == BC_FREESLIP && mine && czi == -1) {
+        const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny);
+        const float2 v = load_pop<S>(a, mirror_z(i), (N * a.ny + ys) * a.nx + xs,
+                                     reader_shift<S>(a, N * (int)P + (int)pxy));
+        a.zout[(long long)zrank(i) * P + pxy] = v.x;
+        a.zout[(long long)(9 + zrank(i)) * P + pxy] = v.y;
     }
     if (a.bc_zhi == BC_CONVECTIVE) {
         // post-stream populations of node (x, y, N-1) at t+1 (N-1 >= 1: plain pulls)
         const int z = N - 1;
-        const float2 own = reader_shift<S>(a, z * (int)P + (int)pxy);
-        float fr[27], fb[27];
-        float rho = 0.0f, jz = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            const int xs = wrapi(x - cx(i), a.nx), ys = wrapi(y - cy(i), a.ny), zs = z - cz(i);
-            const float2 v = load_pop<S>(a, i, (zs * a.ny + ys) * a.nx + xs, own);
-            fr[i] = v.x;
-            fb[i] = v.y;
+        float fr = 0.0f, fb = 0.0f;
+        if (mine) {
+            const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny), zs = z - czi;
+            const float2 v = load_pop<S>(a, i, (zs * a.ny + ys) * a.nx + xs, reader_shift<S>(a, z * (int)P + (int)pxy));
+            fr = v.x;
+            fb = v.y;
         }
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            const float s = fr[i] + fb[i];
-            rho += s;
-            if (cz(i) != 0) jz += (float)cz(i) * s;
-        }
+        const float s_ = fr + fb;
+        const float rho = warp_sum_f(s_), jz = warp_sum_f((float)czi * s_);
         const float Fz = (rho - a.rho_b0) * a.gz;
         float lam = (jz + 0.5f * Fz) / rho;  // u_z(x, y, N-1, t+1), Eq. (Momentum)
         lam = fminf(fmaxf(lam, 0.0f), 1.0f);
         const float inv = 1.0f / (1.0f + lam);
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
+        if (mine) {
             const long long hr = (long long)i * P + pxy, hb = (long long)(27 + i) * P + pxy;
-            a.hist_out[hr] = (__ldg(a.hist_in + hr) + lam * fr[i]) * inv;
-            a.hist_out[hb] = (__ldg(a.hist_in + hb) + lam * fb[i]) * inv;
+            a.hist_out[hr] = (__ldg(a.hist_in + hr) + lam * fr) * inv;
+            a.hist_out[hb] = (__ldg(a.hist_in + hb) + lam * fb) * inv;
+            if (a.fm_out) {
+                a.fm_out[hr] = fr;
+                a.fm_out[hb] = fb;
+            }
         }
     }
 }
@@ -440,7 +438,8 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
 }
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
-template <bool kForce, int S>
+// kRec (FP32, adjoint recompute): also writes the node's collision inputs to a.rec / a.rec4.
+template <bool kForce, int S, bool kRec>
 __global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -451,17 +450,24 @@ __global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel
     gather_moments<S>(a, nb, z, mo);
     float gpx, gpy, gpz, grx, gry, grz;
     stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    if constexpr (kRec) {
+        const size_t NN = (size_t)a.NN;
+        a.rec[nb.n] = make_float4(mo.rho_r, mo.rho_b, mo.jx, mo.jy);
+        a.rec[NN + nb.n] = make_float4(mo.jz, mo.pxx, mo.pyy, mo.pzz);
+        a.rec[2 * NN + nb.n] = make_float4(mo.pxy, mo.pxz, mo.pyz, gpx);
+        a.rec[3 * NN + nb.n] = make_float4(gpy, gpz, grx, gry);
+        a.rec4[nb.n] = grz;
+    }
     collide_from_moments<kForce, S>(a, nb, mo, gpx, gpy, gpz, grx, gry, grz);
 }
 
 
 // ------------------------------------------------------------------------ launchers
 template <int S>
-static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
+static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, bool collide) {
     if (ev) cudaEventRecord(ev[0], s);
     if (a.bc_zlo != BC_PERIODIC || a.bc_zhi != BC_PERIODIC) {
-        dim3 b(32, 8), g((a.nx + 31) / 32, (a.ny + 7) / 8);
-        boundary_plane_kernel<S><<<g, b, 0, s>>>(a);
+        boundary_plane_kernel<S><<<(unsigned)((a.plane + 3) / 4), 128, 0, s>>>(a);
         *launches += 1;
     }
     const bool paper_rates = a.s3 == 1.0f && a.s4 == 1.0f && a.s5 == 1.0f && a.s6 == 1.0f;
@@ -470,21 +476,29 @@ static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, lo
     if (ev) cudaEventRecord(ev[1], s);
     phase_field_kernel<S><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
+    *launches += 1;
+    if (!collide) return;
+    const bool rec = S == STORE_FP32 && a.rec != nullptr;  // paper rates only (adjoint)
     if (!paper_rates)
         collide_general_kernel<S><<<grd, blk, 0, s>>>(a);
+    else if (rec && force)
+        collide_kernel<true, S, S == STORE_FP32><<<grd, blk, 0, s>>>(a);
+    else if (rec)
+        collide_kernel<false, S, S == STORE_FP32><<<grd, blk, 0, s>>>(a);
     else if (force)
-        collide_kernel<true, S><<<grd, blk, 0, s>>>(a);
+        collide_kernel<true, S, false><<<grd, blk, 0, s>>>(a);
     else
-        collide_kernel<false, S><<<grd, blk, 0, s>>>(a);
+        collide_kernel<false, S, false><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
-    *launches += 2;
+    *launches += 1;
 }
 
-cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches) {
+cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches,
+                        bool collide) {
     if (storage == STORE_FP16)
-        launch_step_s<STORE_FP16>(a, s, ev, launches);
+        launch_step_s<STORE_FP16>(a, s, ev, launches, collide);
     else
-        launch_step_s<STORE_FP32>(a, s, ev, launches);
+        launch_step_s<STORE_FP32>(a, s, ev, launches, collide);
     return cudaGetLastError();
 }
 
