@@ -47,14 +47,27 @@ class Params(C.Structure):
                 ("fourier", C.c_double * 16)]
 
 
+_Z = C.c_double * 2  # double _Complex: (real, imaginary)
+
+
+class CSParams(C.Structure):
+    """orc_params of the complex-step build: every real field complex."""
+    _fields_ = [(name, (_Z * ct._length_) if hasattr(ct, "_length_") else _Z) if ct is not C.c_uint64 else (name, ct)
+                for name, ct in Params._fields_]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP over nodes)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                   "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
-            subprocess.run(cmd, check=True)
+            flags = ["-O2", "-std=c11", "-fPIC", "-fopenmp", "-ffp-contract=off", "-fno-fast-math"]
+            objs = [tmp + ".real.o", tmp + ".cs.o"]  # FP64, and the complex-step tangent build
+            subprocess.run(["gcc", "-c", _SRC, "-o", objs[0]] + flags, check=True)
+            subprocess.run(["gcc", "-c", _SRC, "-o", objs[1], "-DORC_COMPLEX_STEP"] + flags, check=True)
+            subprocess.run(["gcc", "-shared", "-fopenmp", "-o", tmp] + objs + ["-lm"], check=True)
+            for o in objs:
+                os.remove(o)
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -89,6 +102,11 @@ def lib():
         L.orc_mass.argtypes = [gp, dp, dp]
         L.orc_objective.argtypes = [gp, pp, dp, C.c_int, dp]
         L.orc_objective.restype = C.c_double
+        cpp = C.POINTER(CSParams)
+        L.orc_cs_step.argtypes = [gp, cpp, dp, dp, C.c_int64, dp, dp, C.POINTER(C.c_uint8)]
+        L.orc_cs_step.restype = C.c_int
+        L.orc_cs_objective_parts.argtypes = [gp, cpp, dp, C.c_int, dp, dp]
+        L.orc_cs_objective_parts.restype = None
         L.orc_velocity_set.argtypes = [C.POINTER(C.c_int32)]
         L.orc_weights.argtypes = [dp]
         L.orc_num_threads.restype = C.c_int
@@ -277,3 +295,52 @@ class Lattice:
         a[: len(args)] = args
         k = {"area": 0, "penetration": 1}[kind]
         return float(lib().orc_objective(C.byref(self.g), C.byref(self.p), _p(self.S), k, _p(a)))
+
+
+def _cs_params(p: dict, dp: dict, h: float) -> CSParams:
+    """Complex parameters p + i h dp (dp: field -> direction, "fourier" a sequence of 16)."""
+    base = make_params(p)
+    out = CSParams()
+    for name, ct in Params._fields_:
+        v = getattr(base, name)
+        if ct is C.c_uint64:
+            setattr(out, name, v)
+            continue
+        d = dp.get(name, 0.0)
+        if hasattr(ct, "_length_"):
+            dd = (list(d) if not np.isscalar(d) else [d] * ct._length_) + [0.0] * ct._length_
+            arr = getattr(out, name)
+            for k in range(ct._length_):
+                arr[k][0], arr[k][1] = v[k], h * dd[k]
+        else:
+            z = getattr(out, name)
+            z[0], z[1] = v, h * d
+    return out
+
+
+def tangent_objective(grid: Grid, params: dict, S0, hist0, T: int, kind: str, args, dparams=None, dS=None,
+                      h: float = 1e-30, step0: int = 0):
+    """Forward-mode tangent of the oracle by complex step: runs T steps from (S0, hist0) with
+    parameters params + i h dparams and state S0 + i h dS and returns (J, dJ), dJ the
+    directional derivative of the objective (reading R12) along (dparams, dS)."""
+    shape = (grid.nz, grid.ny, grid.nx)
+    S = np.zeros((2, 27) + shape + (2,))
+    S[..., 0] = np.asarray(S0, dtype=np.float64).reshape((2, 27) + shape)
+    if dS is not None:
+        S[..., 1] = h * np.asarray(dS, dtype=np.float64).reshape((2, 27) + shape)
+    H = np.zeros((2, 27, grid.ny, grid.nx, 2))
+    H[..., 0] = np.asarray(hist0, dtype=np.float64).reshape(H.shape[:-1])
+    cp = _cs_params(params, dparams or {}, h)
+    L = lib()
+    for t in range(T):
+        out = np.empty_like(S)
+        Ho = H.copy()
+        rc = L.orc_cs_step(C.byref(grid), C.byref(cp), _p(S), _p(H), step0 + t, _p(out), _p(Ho), None)
+        if rc != 0:
+            raise RuntimeError(f"oracle tangent step failed ({rc})")
+        S, H = out, Ho
+    a = np.zeros(4)
+    a[: len(args)] = args
+    z = np.zeros(2)
+    L.orc_cs_objective_parts(C.byref(grid), C.byref(cp), _p(S), {"area": 0, "penetration": 1}[kind], _p(a), _p(z))
+    return z[0], z[1] / h

@@ -53,6 +53,12 @@
  *   R11 Inlet profile (not in the paper, whose inlet is uniform; the parameters the
  *       adjoint differentiates): u_z = u_j0 [1 + sum_{m=1..8} (a_m cos m theta + b_m sin m theta)]
  *       with theta the polar angle of the source column about the disc centre (0 at the centre).
+ * Forward-mode tangent (complex step): compiled with ORC_COMPLEX_STEP the same source has
+ * real = double _Complex and exports orc_cs_step and orc_cs_objective.  A parameter or state
+ * perturbed by i h (h ~ 1e-30) gives dJ = Im J / h to rounding (Squire and Trapp, SIAM Rev.
+ * 40, 1998): every operation of the step is complex-analytic except the comparisons (pivot
+ * choice, the outflow clamp, the disc test), which act on real parts.
+ *
  *   R12 Objectives of the adjoint (not in the paper), on the order parameter phi of a state's
  *       colour densities rho_k = sum_i S_i^k: the interface area sum of sqrt(|grad phi|^2 + eps^2)
  *       over 1 <= z <= nz-2 (isotropic stencil, x and y periodic), and the penetration length
@@ -68,6 +74,31 @@
 #include <omp.h>
 #endif
 
+#ifdef ORC_COMPLEX_STEP
+#include <complex.h>
+typedef double _Complex real;
+#define RE(x) creal(x)
+#define SQRT(x) csqrt(x)
+#define LOG(x) clog(x)
+/* the complex build exports its own names */
+#define orc_build_T orc_cs_build_T
+#define orc_equilibrium orc_cs_equilibrium
+#define orc_forcing_prime orc_cs_forcing_prime
+#define orc_collide orc_cs_collide
+#define orc_perturbation orc_cs_perturbation
+#define orc_recolor orc_cs_recolor
+#define orc_stream orc_cs_stream
+#define orc_step orc_cs_step
+#define orc_objective orc_cs_objective
+double orc_inlet_xi(uint64_t seed, int64_t step, int32_t x, int32_t y, int32_t nx, int32_t ny);
+#else
+typedef double real;
+#define RE(x) (x)
+#define SQRT(x) sqrt(x)
+#define LOG(x) log(x)
+#endif
+#define RABS(x) fabs(RE(x))
+
 /* ---------------------------------------------------------------- lattice (Eq. velVec) */
 static const int CX[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1, -1, 1};
 static const int CY[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1};
@@ -81,17 +112,17 @@ typedef struct {
 } orc_grid;
 
 typedef struct {
-    double rho_r0, rho_b0;       /* initial densities rho_k^0 (Eq. order) */
-    double nu_r, nu_b;           /* kinematic viscosities */
-    double sigma;                /* interfacial tension */
-    double beta;                 /* recolouring parameter */
-    double g[3];                 /* gravity in F = (rho - rho_b^0) g */
-    double s0, s1, s2b, s3, s4, s5, s6; /* relaxation rates of K (s_2nu follows from nu) */
-    double u_in, d_in, noise_amp;/* inlet plug velocity, disc diameter, radial noise amplitude */
+    real rho_r0, rho_b0;       /* initial densities rho_k^0 (Eq. order) */
+    real nu_r, nu_b;           /* kinematic viscosities */
+    real sigma;                /* interfacial tension */
+    real beta;                 /* recolouring parameter */
+    real g[3];                 /* gravity in F = (rho - rho_b^0) g */
+    real s0, s1, s2b, s3, s4, s5, s6; /* relaxation rates of K (s_2nu follows from nu) */
+    real u_in, d_in, noise_amp;/* inlet plug velocity, disc diameter, radial noise amplitude */
     uint64_t seed;               /* inlet noise seed */
-    double eps_grad;             /* |grad phi| regulariser (R3) */
-    double alpha_b;              /* 8/27 in the paper */
-    double fourier[16];          /* inlet profile: a_1, b_1, ..., a_8, b_8 (R11) */
+    real eps_grad;             /* |grad phi| regulariser (R3) */
+    real alpha_b;              /* 8/27 in the paper */
+    real fourier[16];          /* inlet profile: a_1, b_1, ..., a_8, b_8 (R11) */
 } orc_params;
 
 static double weight(int i) {
@@ -103,7 +134,7 @@ static double weight(int i) {
 }
 
 /* Eq. (varphi_ik) */
-static double varphi(int i, double alpha) {
+static real varphi(int i, real alpha) {
     int q = CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i];
     if (q == 0) return alpha;
     if (q == 1) return 2.0 * (1.0 - alpha) / 19.0;
@@ -126,6 +157,7 @@ static int mirror_z(int i) {
     return -1;
 }
 
+#ifndef ORC_COMPLEX_STEP
 void orc_velocity_set(int32_t *c) {
     for (int i = 0; i < 27; ++i) {
         c[3 * i] = CX[i];
@@ -146,14 +178,16 @@ int orc_num_threads(void) {
 #endif
 }
 
+#endif
+
 /* ---------------------------------------------------------- moment set (Eq. momentSet) */
 /* T[a][i]: row a is the a-th nonorthogonal central moment evaluated at direction i,
  * with cbar = c_i - u. */
-void orc_build_T(const double *u, double *T) {
+void orc_build_T(const real *u, real *T) {
     for (int i = 0; i < 27; ++i) {
-        double X = CX[i] - u[0], Y = CY[i] - u[1], Z = CZ[i] - u[2];
-        double X2 = X * X, Y2 = Y * Y, Z2 = Z * Z;
-        double r[27];
+        real X = CX[i] - u[0], Y = CY[i] - u[1], Z = CZ[i] - u[2];
+        real X2 = X * X, Y2 = Y * Y, Z2 = Z * Z;
+        real r[27];
         r[0] = 1.0;
         r[1] = X;
         r[2] = Y;
@@ -186,16 +220,16 @@ void orc_build_T(const double *u, double *T) {
 }
 
 /* Dense LU factorisation with partial pivoting (textbook Doolittle form), in place. */
-static int lu_factor(double *A, int *piv) {
+static int lu_factor(real *A, int *piv) {
     for (int k = 0; k < 27; ++k) {
         int p = k;
-        double best = fabs(A[k * 27 + k]);
+        double best = RABS(A[k * 27 + k]);
         for (int r = k + 1; r < 27; ++r)
-            if (fabs(A[r * 27 + k]) > best) { best = fabs(A[r * 27 + k]); p = r; }
+            if (RABS(A[r * 27 + k]) > best) { best = RABS(A[r * 27 + k]); p = r; }
         if (best == 0.0) return -1;
         piv[k] = p;
         if (p != k)
-            for (int c = 0; c < 27; ++c) { double t = A[k * 27 + c]; A[k * 27 + c] = A[p * 27 + c]; A[p * 27 + c] = t; }
+            for (int c = 0; c < 27; ++c) { real t = A[k * 27 + c]; A[k * 27 + c] = A[p * 27 + c]; A[p * 27 + c] = t; }
         for (int r = k + 1; r < 27; ++r) {
             A[r * 27 + k] /= A[k * 27 + k];
             for (int c = k + 1; c < 27; ++c) A[r * 27 + c] -= A[r * 27 + k] * A[k * 27 + c];
@@ -204,9 +238,9 @@ static int lu_factor(double *A, int *piv) {
     return 0;
 }
 
-static void lu_solve(const double *LU, const int *piv, double *b) {
+static void lu_solve(const real *LU, const int *piv, real *b) {
     for (int k = 0; k < 27; ++k)
-        if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
+        if (piv[k] != k) { real t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
     for (int r = 0; r < 27; ++r)
         for (int c = 0; c < r; ++c) b[r] -= LU[r * 27 + c] * b[c];
     for (int r = 26; r >= 0; --r) {
@@ -215,14 +249,15 @@ static void lu_solve(const double *LU, const int *piv, double *b) {
     }
 }
 
+#ifndef ORC_COMPLEX_STEP
 /* T(u)^-1 column by column (used by the tests against M^-1 N^-1 of Appendix A). */
-int orc_T_inverse(const double *u, double *Tinv) {
-    double T[729];
+int orc_T_inverse(const real *u, real *Tinv) {
+    real T[729];
     int piv[27];
     orc_build_T(u, T);
     if (lu_factor(T, piv)) return -1;
     for (int j = 0; j < 27; ++j) {
-        double e[27] = {0};
+        real e[27] = {0};
         e[j] = 1.0;
         lu_solve(T, piv, e);
         for (int r = 0; r < 27; ++r) Tinv[r * 27 + j] = e[r];
@@ -230,8 +265,10 @@ int orc_T_inverse(const double *u, double *Tinv) {
     return 0;
 }
 
+#endif
+
 /* K = diag(s0, s1 x3, s2nu x5, s2b, s3 x7, s4 x6, s5 x3, s6) */
-static void relaxation_diag(const orc_params *p, double s2nu, double *K) {
+static void relaxation_diag(const orc_params *p, real s2nu, real *K) {
     K[0] = p->s0;
     for (int a = 1; a <= 3; ++a) K[a] = p->s1;
     for (int a = 4; a <= 8; ++a) K[a] = s2nu;
@@ -243,21 +280,21 @@ static void relaxation_diag(const orc_params *p, double s2nu, double *K) {
 }
 
 /* ------------------------------------------------------------ equilibrium (Eq. EES) */
-void orc_equilibrium(double rho, const double *u, double alpha, double nu, const double *grho, double *fe) {
-    double G[3][3];
+void orc_equilibrium(real rho, const real *u, real alpha, real nu, const real *grho, real *fe) {
+    real G[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) G[a][b] = (u[a] * grho[b] + u[b] * grho[a]) / 48.0;
-    double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    double ugr = u[0] * grho[0] + u[1] * grho[1] + u[2] * grho[2];
+    real usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    real ugr = u[0] * grho[0] + u[1] * grho[1] + u[2] * grho[2];
     for (int i = 0; i < 27; ++i) {
-        double c[3] = {CX[i], CY[i], CZ[i]};
-        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        real c[3] = {CX[i], CY[i], CZ[i]};
+        real cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
         int q = CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i];
-        double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq + 4.5 * cu * cu * cu - 4.5 * cu * usq;
-        double Gcc = 0.0;
+        real poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq + 4.5 * cu * cu * cu - 4.5 * cu * usq;
+        real Gcc = 0.0;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) Gcc += G[a][b] * c[a] * c[b];
-        double Phi;
+        real Phi;
         if (q == 0) Phi = -3.0 * nu * ugr;
         else if (q == 1) Phi = 16.0 * nu * Gcc;
         else if (q == 2) Phi = 4.0 * nu * Gcc;
@@ -267,11 +304,11 @@ void orc_equilibrium(double rho, const double *u, double alpha, double nu, const
 }
 
 /* ------------------------------------------------------------ forcing (Eq. ketFd) */
-void orc_forcing_prime(const double *u, const double *F, double *Fp) {
+void orc_forcing_prime(const real *u, const real *F, real *Fp) {
     for (int i = 0; i < 27; ++i) {
-        double c[3] = {CX[i], CY[i], CZ[i]};
-        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
-        double s = 0.0;
+        real c[3] = {CX[i], CY[i], CZ[i]};
+        real cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        real s = 0.0;
         for (int a = 0; a < 3; ++a) s += (3.0 * (c[a] - u[a]) + 9.0 * cu * c[a]) * F[a];
         Fp[i] = weight(i) * s;
     }
@@ -279,15 +316,15 @@ void orc_forcing_prime(const double *u, const double *F, double *Fp) {
 
 /* ----------------------------------------- GMRT collision (Eqs. scoll, ketF), literal */
 /* Omega1 = -T^-1 K T (f - fe) + T^-1 (I - K/2) T F' with T = N M built from Eq. momentSet. */
-int orc_collide(const double *f, const double *fe, const double *Fp, const double *u, const double *K, double *Omega1) {
-    double T[729], LU[729];
+int orc_collide(const real *f, const real *fe, const real *Fp, const real *u, const real *K, real *Omega1) {
+    real T[729], LU[729];
     int piv[27];
     orc_build_T(u, T);
     memcpy(LU, T, sizeof(T));
     if (lu_factor(LU, piv)) return -1;
-    double m[27], mf[27];
+    real m[27], mf[27];
     for (int a = 0; a < 27; ++a) {
-        double s = 0.0, sf = 0.0;
+        real s = 0.0, sf = 0.0;
         for (int i = 0; i < 27; ++i) {
             s += T[a * 27 + i] * (f[i] - fe[i]);
             sf += T[a * 27 + i] * Fp[i];
@@ -302,38 +339,39 @@ int orc_collide(const double *f, const double *fe, const double *Fp, const doubl
 }
 
 /* --------------------------------- perturbation (Eqs. perturb, B_i), readings R1-R3 */
-void orc_perturbation(double A, const double *gphi, double eps, double *Omega2) {
-    double g2 = gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2];
-    double gmag = sqrt(g2 + eps * eps);
+void orc_perturbation(real A, const real *gphi, real eps, real *Omega2) {
+    real g2 = gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2];
+    real gmag = SQRT(g2 + eps * eps);
     for (int i = 0; i < 27; ++i) {
-        double cg = CX[i] * gphi[0] + CY[i] * gphi[1] + CZ[i] * gphi[2];
+        real cg = CX[i] * gphi[0] + CY[i] * gphi[1] + CZ[i] * gphi[2];
         /* (A/2)|g| [w_i (c.g)^2/|g|^2 - B_i], written with one regularised |g| divisor */
-        double one_colour = 0.5 * A * (weight(i) * cg * cg - Bcoef(i) * g2) / gmag;
+        real one_colour = 0.5 * A * (weight(i) * cg * cg - Bcoef(i) * g2) / gmag;
         Omega2[i] = 0.0;
         for (int k = 0; k < 2; ++k) Omega2[i] += one_colour; /* R2: red and blue */
     }
 }
 
 /* ------------------------------------------------ recolouring (Eqs. op3r, op3b) */
-void orc_recolor(const double *fstar, double rho_r, double rho_b, double alpha_bar, double nu_bar,
-                 double beta, const double *gphi, double eps, double *fr, double *fb) {
-    double rho = rho_r + rho_b;
-    double zero[3] = {0.0, 0.0, 0.0};
-    double fe0[27];
+void orc_recolor(const real *fstar, real rho_r, real rho_b, real alpha_bar, real nu_bar,
+                 real beta, const real *gphi, real eps, real *fr, real *fb) {
+    real rho = rho_r + rho_b;
+    real zero[3] = {0.0, 0.0, 0.0};
+    real fe0[27];
     orc_equilibrium(rho, zero, alpha_bar, nu_bar, zero, fe0); /* f^(e)(rho, 0), R6 */
-    double g2 = gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2];
-    double gmag = sqrt(g2 + eps * eps);
+    real g2 = gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2];
+    real gmag = SQRT(g2 + eps * eps);
     for (int i = 0; i < 27; ++i) {
         double cnorm = sqrt((double)(CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i]));
-        double cos_t = 0.0;
+        real cos_t = 0.0;
         if (cnorm > 0.0) cos_t = (CX[i] * gphi[0] + CY[i] * gphi[1] + CZ[i] * gphi[2]) / (cnorm * gmag);
-        double seg = beta * rho_r * rho_b / (rho * rho) * cos_t * fe0[i];
+        real seg = beta * rho_r * rho_b / (rho * rho) * cos_t * fe0[i];
         fr[i] = rho_r / rho * fstar[i] + seg;
         fb[i] = rho_b / rho * fstar[i] - seg;
     }
 }
 
 /* ------------------------------------------------------------------ inlet noise (R7) */
+#ifndef ORC_COMPLEX_STEP
 /* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): state increment 0x9E3779B97F4A7C15
  * followed by the published 64-bit finaliser. */
 uint64_t orc_splitmix64(uint64_t state) {
@@ -350,27 +388,30 @@ double orc_inlet_xi(uint64_t seed, int64_t step, int32_t x, int32_t y, int32_t n
     return (double)(h >> 40) * (1.0 / 8388608.0) - 1.0;
 }
 
+#endif
+
 static int in_disc(const orc_grid *g, const orc_params *p, int x, int y) {
     double dx = 2.0 * x - (g->nx - 1), dy = 2.0 * y - (g->ny - 1);
-    return dx * dx + dy * dy < p->d_in * p->d_in;
+    return dx * dx + dy * dy < RE(p->d_in) * RE(p->d_in);
 }
 
-static void inlet_velocity(const orc_grid *g, const orc_params *p, int64_t step, int x, int y, double *u) {
+static void inlet_velocity(const orc_grid *g, const orc_params *p, int64_t step, int x, int y, real *u) {
     double rx = x - 0.5 * (g->nx - 1), ry = y - 0.5 * (g->ny - 1);
     double r = sqrt(rx * rx + ry * ry);
     double xi = orc_inlet_xi(p->seed, step, x, y, g->nx, g->ny);
-    double a = p->noise_amp * p->u_in * xi;
+    real a = p->noise_amp * p->u_in * xi;
     u[0] = r > 0.0 ? a * rx / r : 0.0;
     u[1] = r > 0.0 ? a * ry / r : 0.0;
-    double theta = atan2(ry, rx), prof = 1.0;
+    double theta = atan2(ry, rx);
+    real prof = 1.0;
     for (int m = 1; m <= 8; ++m)
         prof += p->fourier[2 * (m - 1)] * cos(m * theta) + p->fourier[2 * m - 1] * sin(m * theta);
     u[2] = p->u_in * prof;
 }
 
-static double alpha_red(const orc_params *p) {
+static real alpha_red(const orc_params *p) {
     /* gamma = rho_r0/rho_b0 = (1 - alpha_b)/(1 - alpha_r) */
-    double gamma = p->rho_r0 / p->rho_b0;
+    real gamma = p->rho_r0 / p->rho_b0;
     return 1.0 - (1.0 - p->alpha_b) / gamma;
 }
 
@@ -388,10 +429,10 @@ static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
 /* f[k][i](x) = S[k][i](x - c_i) with the boundary rules R7, R8.  `hist` holds the
  * post-stream populations of the outflow plane at the previous step; on return
  * `hist_out` holds those of this step. */
-void orc_stream(const orc_grid *g, const orc_params *p, const double *S, const double *hist,
-                int64_t step, double *f, double *hist_out) {
+void orc_stream(const orc_grid *g, const orc_params *p, const real *S, const real *hist,
+                int64_t step, real *f, real *hist_out) {
     const int nx = g->nx, ny = g->ny, nz = g->nz, N = nz - 1;
-    double alpha_r = alpha_red(p);
+    real alpha_r = alpha_red(p);
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -400,13 +441,13 @@ void orc_stream(const orc_grid *g, const orc_params *p, const double *S, const d
                     int xs = wrap(x - CX[i], nx), ys = wrap(y - CY[i], ny), zs = z - CZ[i];
                     size_t n = nidx(g, x, y, z);
                     for (int k = 0; k < 2; ++k) {
-                        double v;
+                        real v;
                         if (g->bc_zlo == ORC_BC_PERIODIC) {
                             v = S[pidx(g, k, i, nidx(g, xs, ys, wrap(zs, nz)))];
                         } else if (zs < 0) {
                             if (g->bc_zlo == ORC_BC_INLET && in_disc(g, p, xs, ys)) {
                                 if (k == 0) {
-                                    double uin[3], fe[27], zero[3] = {0, 0, 0};
+                                    real uin[3], fe[27], zero[3] = {0, 0, 0};
                                     inlet_velocity(g, p, step, xs, ys, uin);
                                     orc_equilibrium(p->rho_r0, uin, alpha_r, p->nu_r, zero, fe);
                                     v = fe[i];
@@ -431,20 +472,20 @@ void orc_stream(const orc_grid *g, const orc_params *p, const double *S, const d
             for (int x = 0; x < nx; ++x) {
                 size_t m = nidx(g, x, y, N - 1), n = nidx(g, x, y, N);
                 /* u_z at N-1 after streaming (Eq. Momentum with F = (rho - rho_b0) g) */
-                double rho = 0.0, jz = 0.0;
+                real rho = 0.0, jz = 0.0;
                 for (int k = 0; k < 2; ++k)
                     for (int i = 0; i < 27; ++i) {
                         rho += f[pidx(g, k, i, m)];
                         jz += f[pidx(g, k, i, m)] * CZ[i];
                     }
-                double Fz = (rho - p->rho_b0) * p->g[2];
-                double lam = (jz + 0.5 * Fz) / rho;
-                if (lam < 0.0) lam = 0.0;
-                if (lam > 1.0) lam = 1.0;
+                real Fz = (rho - p->rho_b0) * p->g[2];
+                real lam = (jz + 0.5 * Fz) / rho;
+                if (RE(lam) < 0.0) lam = 0.0;
+                if (RE(lam) > 1.0) lam = 1.0;
                 for (int k = 0; k < 2; ++k)
                     for (int i = 0; i < 27; ++i) {
                         size_t h = ((size_t)(k * 27 + i) * ny + y) * nx + x;
-                        double v = (hist[h] + lam * f[pidx(g, k, i, m)]) / (1.0 + lam);
+                        real v = (hist[h] + lam * f[pidx(g, k, i, m)]) / (1.0 + lam);
                         f[pidx(g, k, i, n)] = v;
                         hist_out[h] = v;
                     }
@@ -456,24 +497,24 @@ void orc_stream(const orc_grid *g, const orc_params *p, const double *S, const d
 /* S_in: post-collision state at step `step`; S_out: post-collision state at step+1.
  * mask (optional, nx*ny*nz bytes): nodes whose collision is evaluated; others get 0.
  * hist / hist_out: [2][27][ny][nx] outflow history (only read with a convective z_hi). */
-int orc_step(const orc_grid *g, const orc_params *p, const double *S_in, const double *hist,
-             int64_t step, double *S_out, double *hist_out, const uint8_t *mask) {
+int orc_step(const orc_grid *g, const orc_params *p, const real *S_in, const real *hist,
+             int64_t step, real *S_out, real *hist_out, const uint8_t *mask) {
     const int nx = g->nx, ny = g->ny, nz = g->nz, N = nz - 1;
     const size_t nn = (size_t)nx * ny * nz;
-    double *f = (double *)malloc(sizeof(double) * 54 * nn);
-    double *rr = (double *)malloc(sizeof(double) * nn);
-    double *rb = (double *)malloc(sizeof(double) * nn);
+    real *f = (real *)malloc(sizeof(real) * 54 * nn);
+    real *rr = (real *)malloc(sizeof(real) * nn);
+    real *rb = (real *)malloc(sizeof(real) * nn);
     if (!f || !rr || !rb) { free(f); free(rr); free(rb); return -2; }
     orc_stream(g, p, S_in, hist, step, f, hist_out);
     /* densities rho_k = sum_i f_i^k */
 #pragma omp parallel for schedule(static)
     for (size_t n = 0; n < nn; ++n) {
-        double a = 0.0, b = 0.0;
+        real a = 0.0, b = 0.0;
         for (int i = 0; i < 27; ++i) { a += f[pidx(g, 0, i, n)]; b += f[pidx(g, 1, i, n)]; }
         rr[n] = a;
         rb[n] = b;
     }
-    const double alpha_b = p->alpha_b, alpha_r = alpha_red(p);
+    const real alpha_b = p->alpha_b, alpha_r = alpha_red(p);
     int fail = 0;
 #pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(| : fail)
     for (int z = 0; z < nz; ++z)
@@ -486,10 +527,10 @@ int orc_step(const orc_grid *g, const orc_params *p, const double *S_in, const d
                     continue;
                 }
                 /* isotropic gradients of phi and rho with the ghost rules R9 */
-                double gphi[3] = {0, 0, 0}, grho[3] = {0, 0, 0};
+                real gphi[3] = {0, 0, 0}, grho[3] = {0, 0, 0};
                 for (int j = 0; j < 27; ++j) {
                     int xn = wrap(x + CX[j], nx), yn = wrap(y + CY[j], ny), zn = z + CZ[j];
-                    double a, b;
+                    real a, b;
                     if (g->bc_zlo == ORC_BC_PERIODIC) {
                         size_t m = nidx(g, xn, yn, wrap(zn, nz));
                         a = rr[m]; b = rb[m];
@@ -507,42 +548,42 @@ int orc_step(const orc_grid *g, const orc_params *p, const double *S_in, const d
                         size_t m = nidx(g, xn, yn, zn);
                         a = rr[m]; b = rb[m];
                     }
-                    double phi_j = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
-                    double rho_j = a + b;
-                    double w = weight(j);
-                    double c[3] = {CX[j], CY[j], CZ[j]};
+                    real phi_j = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
+                    real rho_j = a + b;
+                    real w = weight(j);
+                    real c[3] = {CX[j], CY[j], CZ[j]};
                     for (int d = 0; d < 3; ++d) {
                         gphi[d] += 3.0 * w * phi_j * c[d];
                         grho[d] += 3.0 * w * rho_j * c[d];
                     }
                 }
                 /* colour-blind populations, densities, order parameter */
-                double fb_[27];
+                real fb_[27];
                 for (int i = 0; i < 27; ++i) fb_[i] = f[pidx(g, 0, i, n)] + f[pidx(g, 1, i, n)];
-                double rho_r = rr[n], rho_b = rb[n], rho = rho_r + rho_b;
-                double phi = (rho_r / p->rho_r0 - rho_b / p->rho_b0) / (rho_r / p->rho_r0 + rho_b / p->rho_b0);
+                real rho_r = rr[n], rho_b = rb[n], rho = rho_r + rho_b;
+                real phi = (rho_r / p->rho_r0 - rho_b / p->rho_b0) / (rho_r / p->rho_r0 + rho_b / p->rho_b0);
                 /* body force (Eq. bodyForceJet) and Guo velocity (Eq. Momentum) */
-                double F[3], u[3];
+                real F[3], u[3];
                 for (int d = 0; d < 3; ++d) F[d] = (rho - p->rho_b0) * p->g[d];
                 for (int d = 0; d < 3; ++d) {
-                    double s = 0.0;
+                    real s = 0.0;
                     for (int i = 0; i < 27; ++i) s += fb_[i] * (d == 0 ? CX[i] : d == 1 ? CY[i] : CZ[i]);
                     u[d] = (s + 0.5 * F[d]) / rho;
                 }
                 /* mixture parameters */
-                double alpha_bar = 0.5 * (1.0 + phi) * alpha_r + 0.5 * (1.0 - phi) * alpha_b;
-                double nu_bar = 1.0 / (0.5 * (1.0 + phi) / p->nu_r + 0.5 * (1.0 - phi) / p->nu_b);
-                double s2nu = 1.0 / (3.0 * nu_bar + 0.5); /* Eq. (shear) with c = dt = 1 */
-                double tau = 1.0 / s2nu;
-                double A = 9.0 * p->sigma / (4.0 * tau); /* Eq. (sigma), R4 */
-                double K[27], fe[27], Fp[27], Om1[27], Om2[27], fs[27];
+                real alpha_bar = 0.5 * (1.0 + phi) * alpha_r + 0.5 * (1.0 - phi) * alpha_b;
+                real nu_bar = 1.0 / (0.5 * (1.0 + phi) / p->nu_r + 0.5 * (1.0 - phi) / p->nu_b);
+                real s2nu = 1.0 / (3.0 * nu_bar + 0.5); /* Eq. (shear) with c = dt = 1 */
+                real tau = 1.0 / s2nu;
+                real A = 9.0 * p->sigma / (4.0 * tau); /* Eq. (sigma), R4 */
+                real K[27], fe[27], Fp[27], Om1[27], Om2[27], fs[27];
                 relaxation_diag(p, s2nu, K);
                 orc_equilibrium(rho, u, alpha_bar, nu_bar, grho, fe);
                 orc_forcing_prime(u, F, Fp);
                 if (orc_collide(fb_, fe, Fp, u, K, Om1)) { fail |= 1; continue; }
                 orc_perturbation(A, gphi, p->eps_grad, Om2);
                 for (int i = 0; i < 27; ++i) fs[i] = fb_[i] + Om1[i] + Om2[i];
-                double fr[27], fbl[27];
+                real fr[27], fbl[27];
                 orc_recolor(fs, rho_r, rho_b, alpha_bar, nu_bar, p->beta, gphi, p->eps_grad, fr, fbl);
                 for (int i = 0; i < 27; ++i) {
                     S_out[pidx(g, 0, i, n)] = fr[i];
@@ -553,18 +594,19 @@ int orc_step(const orc_grid *g, const orc_params *p, const double *S_in, const d
     return fail ? -1 : 0;
 }
 
+#ifndef ORC_COMPLEX_STEP
 /* --------------------------------------------------------- initial states (R10, Sec. III) */
 /* Populations from fields rho_r, rho_b (nn each) and u (3*nn, component-major). */
-void orc_init_fields(const orc_grid *g, const orc_params *p, const double *rho_r, const double *rho_b,
-                     const double *u, double *S, double *hist) {
+void orc_init_fields(const orc_grid *g, const orc_params *p, const real *rho_r, const real *rho_b,
+                     const real *u, real *S, real *hist) {
     const size_t nn = (size_t)g->nx * g->ny * g->nz;
-    double alpha_r = alpha_red(p);
+    real alpha_r = alpha_red(p);
     for (size_t n = 0; n < nn; ++n) {
-        double uu[3] = {u[n], u[nn + n], u[2 * nn + n]};
-        double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+        real uu[3] = {u[n], u[nn + n], u[2 * nn + n]};
+        real usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
         for (int i = 0; i < 27; ++i) {
-            double cu = CX[i] * uu[0] + CY[i] * uu[1] + CZ[i] * uu[2];
-            double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq + 4.5 * cu * cu * cu - 4.5 * cu * usq;
+            real cu = CX[i] * uu[0] + CY[i] * uu[1] + CZ[i] * uu[2];
+            real poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq + 4.5 * cu * cu * cu - 4.5 * cu * usq;
             S[pidx(g, 0, i, n)] = rho_r[n] * (varphi(i, alpha_r) + weight(i) * poly);
             S[pidx(g, 1, i, n)] = rho_b[n] * (varphi(i, p->alpha_b) + weight(i) * poly);
         }
@@ -580,13 +622,13 @@ void orc_init_fields(const orc_grid *g, const orc_params *p, const double *rho_r
 
 /* Static droplet of Section III: tanh profiles of width W around radius R, centre at
  * the domain centre ((n - 1)/2 in each direction), at rest. */
-void orc_droplet_fields(const orc_grid *g, const orc_params *p, double R, double W, double *rho_r, double *rho_b) {
-    double xc = 0.5 * (g->nx - 1), yc = 0.5 * (g->ny - 1), zc = 0.5 * (g->nz - 1);
+void orc_droplet_fields(const orc_grid *g, const orc_params *p, real R, real W, real *rho_r, real *rho_b) {
+    real xc = 0.5 * (g->nx - 1), yc = 0.5 * (g->ny - 1), zc = 0.5 * (g->nz - 1);
     for (int z = 0; z < g->nz; ++z)
         for (int y = 0; y < g->ny; ++y)
             for (int x = 0; x < g->nx; ++x) {
-                double r = sqrt((x - xc) * (x - xc) + (y - yc) * (y - yc) + (z - zc) * (z - zc));
-                double t = tanh(2.0 * (r - R) / W);
+                real r = sqrt((x - xc) * (x - xc) + (y - yc) * (y - yc) + (z - zc) * (z - zc));
+                real t = tanh(2.0 * (r - R) / W);
                 size_t n = nidx(g, x, y, z);
                 rho_r[n] = 0.5 * p->rho_r0 * (1.0 - t);
                 rho_b[n] = 0.5 * p->rho_b0 * (1.0 + t);
@@ -597,25 +639,25 @@ void orc_droplet_fields(const orc_grid *g, const orc_params *p, double R, double
 /* Fields of a post-collision state: rho_k = sum_i S_i^k; rho u = sum_i S_i c_i - F/2
  * (the collision adds F to the momentum, Eqs. scoll and ketF); p from Eq. (press)
  * with rho and alpha-bar. */
-void orc_fields(const orc_grid *g, const orc_params *p, const double *S, double *rho_r, double *rho_b,
-                double *u, double *phi, double *pres) {
+void orc_fields(const orc_grid *g, const orc_params *p, const real *S, real *rho_r, real *rho_b,
+                real *u, real *phi, real *pres) {
     const size_t nn = (size_t)g->nx * g->ny * g->nz;
-    double alpha_r = alpha_red(p);
+    real alpha_r = alpha_red(p);
 #pragma omp parallel for schedule(static)
     for (size_t n = 0; n < nn; ++n) {
-        double a = 0.0, b = 0.0, j[3] = {0, 0, 0};
+        real a = 0.0, b = 0.0, j[3] = {0, 0, 0};
         for (int i = 0; i < 27; ++i) {
-            double fr = S[pidx(g, 0, i, n)], fb = S[pidx(g, 1, i, n)];
+            real fr = S[pidx(g, 0, i, n)], fb = S[pidx(g, 1, i, n)];
             a += fr;
             b += fb;
             j[0] += (fr + fb) * CX[i];
             j[1] += (fr + fb) * CY[i];
             j[2] += (fr + fb) * CZ[i];
         }
-        double rho = a + b;
-        double ph = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
+        real rho = a + b;
+        real ph = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
         for (int d = 0; d < 3; ++d) u[d * nn + n] = (j[d] - 0.5 * (rho - p->rho_b0) * p->g[d]) / rho;
-        double alpha_bar = 0.5 * (1.0 + ph) * alpha_r + 0.5 * (1.0 - ph) * p->alpha_b;
+        real alpha_bar = 0.5 * (1.0 + ph) * alpha_r + 0.5 * (1.0 - ph) * p->alpha_b;
         rho_r[n] = a;
         rho_b[n] = b;
         phi[n] = ph;
@@ -624,13 +666,13 @@ void orc_fields(const orc_grid *g, const orc_params *p, const double *S, double 
 }
 
 /* Per-colour total mass of a state (Neumaier-compensated sum in index order). */
-void orc_mass(const orc_grid *g, const double *S, double *out) {
+void orc_mass(const orc_grid *g, const real *S, real *out) {
     const size_t nn = (size_t)g->nx * g->ny * g->nz;
     for (int k = 0; k < 2; ++k) {
-        double s = 0.0, c = 0.0;
+        real s = 0.0, c = 0.0;
         for (int i = 0; i < 27; ++i)
             for (size_t n = 0; n < nn; ++n) {
-                double v = S[pidx(g, k, i, n)], t = s + v;
+                real v = S[pidx(g, k, i, n)], t = s + v;
                 c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
                 s = t;
             }
@@ -638,42 +680,56 @@ void orc_mass(const orc_grid *g, const double *S, double *out) {
     }
 }
 
+#endif
+
 /* ------------------------------------------------------ adjoint objectives (R12) */
-double orc_objective(const orc_grid *g, const orc_params *p, const double *S, int kind, const double *args) {
+real orc_objective(const orc_grid *g, const orc_params *p, const real *S, int kind, const double *args) {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const size_t nn = (size_t)nx * ny * nz;
-    double *phi = (double *)malloc(sizeof(double) * nn);
-    if (!phi) return NAN;
+    real *phi = (real *)malloc(sizeof(real) * nn);
+    if (!phi) return (real)NAN;
     for (size_t n = 0; n < nn; ++n) {
-        double a = 0.0, b = 0.0;
+        real a = 0.0, b = 0.0;
         for (int i = 0; i < 27; ++i) { a += S[pidx(g, 0, i, n)]; b += S[pidx(g, 1, i, n)]; }
         phi[n] = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
     }
-    double J = 0.0;
+    real J = 0.0;
     if (kind == 0) {
         double eps = args[0];
         for (int z = 1; z <= nz - 2; ++z)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
-                    double gr[3] = {0, 0, 0};
+                    real gr[3] = {0, 0, 0};
                     for (int j = 0; j < 27; ++j) {
-                        double v = phi[nidx(g, wrap(x + CX[j], nx), wrap(y + CY[j], ny), z + CZ[j])];
+                        real v = phi[nidx(g, wrap(x + CX[j], nx), wrap(y + CY[j], ny), z + CZ[j])];
                         gr[0] += 3.0 * weight(j) * CX[j] * v;
                         gr[1] += 3.0 * weight(j) * CY[j] * v;
                         gr[2] += 3.0 * weight(j) * CZ[j] * v;
                     }
-                    J += sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+                    J += SQRT(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
                 }
     } else {
-        double delta = args[0], N = nz - 1, sum = 0.0;
+        double delta = args[0], N = nz - 1;
+        real sum = 0.0;
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
-                    double h = 0.5 * (1.0 + phi[nidx(g, x, y, z)]), H = h * h;
+                    real h = 0.5 * (1.0 + phi[nidx(g, x, y, z)]), H = h * h;
                     sum += H * exp((z - N) / delta);
                 }
-        J = N + delta * log(sum);
+        J = N + delta * LOG(sum);
     }
     free(phi);
     return J;
 }
+
+#ifdef ORC_COMPLEX_STEP
+/* The complex objective as (real part, imaginary part) through a pointer (a complex return
+ * value does not cross every foreign-function interface). */
+void orc_cs_objective_parts(const orc_grid *g, const orc_params *p, const real *S, int kind, const double *args,
+                            double *out) {
+    real J = orc_objective(g, p, S, kind, args);
+    out[0] = creal(J);
+    out[1] = cimag(J);
+}
+#endif

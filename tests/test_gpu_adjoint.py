@@ -1,5 +1,6 @@
 """The discrete adjoint of the CUDA step (lb_adjoint) against FP64 central finite differences
-of the oracle (same seeded inputs on both sides; the oracle never sees a GPU value).
+of the oracle and against the oracle's forward-mode (complex-step) tangent, same seeded inputs
+on both sides; the oracle never sees a GPU value.
 
 Gradient error norm: max over parameters of |g_adjoint - g_fd| / max over parameters of
 |g_fd| (the gradient's own scale), bar 1e-4; the directional derivative along a random state
@@ -72,6 +73,24 @@ def fd_gradient(grid, bc, params, init, T, objective, args, names):
     return g
 
 
+def tangent_gradient(grid, bc, params, init, T, objective, args, names):
+    """The oracle's complex-step tangent along each parameter direction."""
+    nx, ny, nz = grid
+    g = oracle.make_grid(nx, ny, nz, *bc)
+    ref = oracle.Lattice(g, oracle.make_params(full_params(params)))
+    init(ref)
+    out = np.zeros(len(names))
+    for k, nm in enumerate(names):
+        if nm in ("u_in", "sigma", "nu_r", "nu_b"):
+            dp = {nm: 1.0}
+        else:
+            d = [0.0] * 16
+            d[2 * (int(nm[1:]) - 1) + (nm[0] == "b")] = 1.0
+            dp = {"fourier": d}
+        out[k] = oracle.tangent_objective(g, full_params(params), ref.S, ref.hist, T, objective, args, dparams=dp)[1]
+    return out
+
+
 def jet_case():
     cfg = workloads.scaled_jet("jet64", 16, 14, 18, D=8)
     params = dict(cfg["params"])
@@ -95,6 +114,9 @@ def test_adjoint_jet_parameters_match_finite_differences(lb, objective, args):
     err = np.abs(g - g_fd).max() / np.abs(g_fd).max()
     assert err < TOL, (err, list(zip(NAMES, g, g_fd)))
     assert np.abs(g_fd[4:]).max() > 1e-3 * np.abs(g_fd).max()  # the profile really matters
+    g_tan = tangent_gradient(grid, bc, params, lambda r: r.init_jet(), T, objective, args, NAMES)
+    err_t = np.abs(g - g_tan).max() / np.abs(g_tan).max()
+    assert err_t < TOL, (err_t, list(zip(NAMES, g, g_tan)))
 
 
 @pytest.mark.parametrize("bc,g", [((0, 0), (1e-5, 0.0, 2e-5)), ((1, 1), (0.0, 0.0, 3e-5))])
@@ -123,6 +145,9 @@ def test_adjoint_state_directional_derivative(lb, bc, g):
     fd = (Js[0] - Js[1]) / (2 * h)
     ad = float((lS * dS).sum())
     assert abs(ad - fd) < TOL * abs(fd), (ad, fd)
+    _, tan = oracle.tangent_objective(oracle.make_grid(nx, ny, nz, *bc), full_params(params), S0, H0, T, "area",
+                                      (1e-3,), dS=dS)
+    assert abs(ad - tan) < TOL * abs(tan), (ad, tan)
     # sigma and the viscosities against central differences too
     init = lambda r: r.init_fields(*fields)
     g_fd = fd_gradient((nx, ny, nz), bc, params, init, T, "area", (1e-3,), ("sigma", "nu_r", "nu_b"))
