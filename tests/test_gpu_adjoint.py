@@ -219,3 +219,23 @@ def test_autograd_function_gives_the_adjoint_gradient(lb):
     predicted = float(J) + float(g @ step)
     assert abs(float(J2) - predicted) < 0.05 * abs(float(g @ step))
     assert float(J2) < float(J)
+
+
+def test_adjoint_full_size_jet_short_horizon(lb):
+    """On the full 64x64x256 jet of the adjoint benchmark (D = 12, Re = 500, We = 50) in the
+    benchmark's launch configuration: J and the gradients w.r.t. u_in and a_2 after 10 steps
+    (checkpoints every 4: segments of 4, 4 and 2) against the oracle's tangent; the oracle at
+    this size costs seconds per step, hence the short horizon."""
+    cfg = workloads.CONFIGS["jet64"]
+    grid, bc, params = cfg["grid"], cfg["bc"], dict(cfg["params"])
+    T = 10
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    J, g = lat.adjoint(T, "penetration", (4.0,), checkpoint=4)
+    names = ("u_in", "a2")
+    g_tan = tangent_gradient(grid, bc, params, lambda r: r.init_jet(), T, "penetration", (4.0,), names)
+    J_ref = oracle_J(grid, bc, params, lambda r: r.init_jet(), T, "penetration", (4.0,))
+    assert abs(J / J_ref - 1) < 1e-5, (J, J_ref)
+    got = np.array([g[NAMES.index(n)] for n in names])
+    err = np.abs(got - g_tan).max() / np.abs(g_tan).max()
+    assert err < TOL, (err, got, g_tan)
