@@ -61,25 +61,34 @@ __device__ __forceinline__ long long block_id() {
     return blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
 }
 
+// Whether a pull of step n+1 reads slot (node at height z, direction i): the inlet disc and the
+// convective plane read nothing.
+__device__ __forceinline__ bool slot_read(const StepArgs &a, int i, int z, bool own_in_disc) {
+    if (a.bc_zlo == BC_PERIODIC) return true;
+    const int zr = z + cz(i);
+    if (a.bc_zhi == BC_CONVECTIVE && zr >= a.nz - 1) return false;
+    return !(zr < 0 && own_in_disc);
+}
+
 // lambda_S(n+1) of slot (node nb.n, direction i): the pushed part plus the deferred density
-// adjoint of the node that reads the slot in step n+1, if a pull reads it (the inlet disc and
-// the convective plane read nothing).
+// adjoint of the node that reads the slot in step n+1, if a pull reads it.
 __device__ __forceinline__ float2 adj_slot(const StepArgs &a, const AdjArgs &g, const Nbr &nb, int i, int z,
                                            bool own_in_disc) {
     float2 v = __ldg(g.lp_in + (size_t)i * a.NN + nb.n);
-    bool read = true;
-    if (a.bc_zlo != BC_PERIODIC) {
-        const int zr = z + cz(i);
-        if (a.bc_zhi == BC_CONVECTIVE && zr >= a.nz - 1) read = false;
-        if (zr < 0 && own_in_disc) read = false;
-    }
-    if (read) {
+    if (slot_read(a, i, z, own_in_disc)) {
         const float2 r = __ldg(g.lr_in + nb.nbr(i));
         v.x += r.x;
         v.y += r.y;
     }
     return v;
 }
+
+// 8-byte asynchronous global -> shared copy (no register holds the value in flight).
+__device__ __forceinline__ void cp_async8(unsigned smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // 1-D transpose of the inverse sweep: M_a = sum_c v_c G_a[c](u) for a = 0, 1, 2.
 __device__ __forceinline__ void sweep_inv_T(float &a0, float &a1, float &a2, const InvAxis &A) {
@@ -138,21 +147,27 @@ __device__ __forceinline__ void m3uu(const RawMom &M, float ux, float uy, float 
 // third order.  Only the recolouring's 1/|c_i| is not separable and is summed directly.
 template <bool kForce>
 __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArgs &g, int x, int y, int z,
-                                                 float (&part)[3], float2 *L_s) {
+                                                 float (&part)[3], float2 *L_s, float2 *R_s) {
     const Nbr nb(a, x, y, z);
     const int N = a.nz - 1;
     const bool pz = a.bc_zlo == BC_PERIODIC;
     const bool conv_top = !pz && z == N && a.bc_zhi == BC_CONVECTIVE;
     const bool own_in_disc = !pz && z == 0 && a.bc_zlo == BC_INLET && a.disc[nb.pxy];
 
-    // lambda of S(n+1) for the 27 directions, loaded as one batch (all requests in flight
-    // together) into this thread's column of shared memory, tensor layout
+    // lambda of S(n+1) for the 27 directions: the pushed and the deferred parts are copied
+    // asynchronously into this thread's two columns of shared memory (tensor layout), and the
+    // node's recorded forward quantities are loaded and used while they are in flight
     {
-        float2 L[27];
+        const unsigned sL = (unsigned)__cvta_generic_to_shared(L_s), sR = (unsigned)__cvta_generic_to_shared(R_s);
 #pragma unroll
-        for (int i = 0; i < 27; ++i) L[i] = adj_slot(a, g, nb, i, z, own_in_disc);
-#pragma unroll
-        for (int i = 0; i < 27; ++i) L_s[cell(i) * 128] = L[i];
+        for (int i = 0; i < 27; ++i) {
+            cp_async8(sL + cell(i) * 128 * 8, g.lp_in + (size_t)i * a.NN + nb.n);
+            if (slot_read(a, i, z, own_in_disc))
+                cp_async8(sR + cell(i) * 128 * 8, g.lr_in + nb.nbr(i));
+            else
+                R_s[cell(i) * 128] = make_float2(0.0f, 0.0f);
+        }
+        cp_async_commit();
     }
 
     // ---- the forward step's collision inputs of this node (recorded in the recompute)
@@ -206,11 +221,13 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     const float pert = Acoef * inv_gm;
     const float R = a.beta * rr * rb * inv_rho;
 
-    // ---- a_i and b_i, in place
+    // ---- a_i and b_i, in place, from lambda S = pushed + deferred
+    cp_async_wait_all();
 #pragma unroll
     for (int c = 0; c < 27; ++c) {
-        const float2 L = L_s[c * 128];
-        L_s[c * 128] = make_float2((rr * L.x + rb * L.y) * inv_rho, L.x - L.y);
+        const float2 P_ = L_s[c * 128], D_ = R_s[c * 128];
+        const float lx = P_.x + D_.x, ly = P_.y + D_.y;
+        L_s[c * 128] = make_float2((rr * lx + rb * ly) * inv_rho, lx - ly);
     }
     const float a0 = L_s[13 * 128].x, b0 = L_s[13 * 128].y;  // rest direction: cell 13
     const float w0 = 8.0f / 27.0f, k27 = 27.0f / 19.0f;
@@ -449,17 +466,17 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
 }
 
 #ifndef LBCM_ADJ_MIN_BLOCKS
-#define LBCM_ADJ_MIN_BLOCKS 4
+#define LBCM_ADJ_MIN_BLOCKS 3
 #endif
 template <bool kForce>
 __global__ void __launch_bounds__(128, LBCM_ADJ_MIN_BLOCKS) adj_collide_kernel(StepArgs a, AdjArgs g) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    __shared__ float2 L_s[27 * 128];
+    extern __shared__ float2 adj_dsm[];  // [2][27][128]: pushed and deferred lambda S(n+1)
     const int t = threadIdx.y * 32 + threadIdx.x;
     float part[3] = {0.0f, 0.0f, 0.0f};
-    if (x < a.nx && y < a.ny) adj_collide_node<kForce>(a, g, x, y, z, part, L_s + t);
+    if (x < a.nx && y < a.ny) adj_collide_node<kForce>(a, g, x, y, z, part, adj_dsm + t, adj_dsm + 27 * 128 + t);
     block_accumulate<3>(part, g.acc_coll, block_id());
 }
 
@@ -734,12 +751,20 @@ long long adj_boundary_blocks(const StepArgs &a) {
     return (long long)gr.x * gr.y * gr.z;
 }
 
+constexpr int kAdjSmem = 2 * 27 * 128 * (int)sizeof(float2);
+
 cudaError_t launch_adjoint_step(const StepArgs &a, const AdjArgs &g, cudaStream_t s, long long *launches) {
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
+    static bool attr = false;  // the dynamic shared memory exceeds the 48 KB default
+    if (!attr) {
+        cudaFuncSetAttribute(adj_collide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        cudaFuncSetAttribute(adj_collide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        attr = true;
+    }
     if (force)
-        adj_collide_kernel<true><<<node_grid(a), node_block(), 0, s>>>(a, g);
+        adj_collide_kernel<true><<<node_grid(a), node_block(), kAdjSmem, s>>>(a, g);
     else
-        adj_collide_kernel<false><<<node_grid(a), node_block(), 0, s>>>(a, g);
+        adj_collide_kernel<false><<<node_grid(a), node_block(), kAdjSmem, s>>>(a, g);
     adj_stencil_kernel<<<node_grid(a), node_block(), 0, s>>>(a, g);
     *launches += 2;
     if (a.bc_zlo == BC_INLET || a.bc_zhi == BC_CONVECTIVE) {
