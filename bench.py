@@ -42,7 +42,7 @@ BYTES_STEP_FP16 = 112 + 112 + 16 + 16
 BYTES_KERNEL_FP16 = {"collide_kernel": 256, "phase_field_kernel": 144}
 
 
-def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,)):
+def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,), checkpoint=0):
     """Cost of lb_adjoint (T steps forward with ceil(sqrt T) checkpoints, objective, reverse
     sweep) against lb_step(T) from the same state, both timed with CUDA events."""
     cfg = workloads.CONFIGS[name]
@@ -52,7 +52,7 @@ def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,)):
     lat.step(20)
     state = lat.save()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    lat.adjoint(T, objective, args)  # workspace allocation and warm-up
+    lat.adjoint(T, objective, args, checkpoint)  # workspace allocation and warm-up
     lat.load(state)
     torch.cuda.synchronize()
     ev[0].record(lat.stream)
@@ -62,11 +62,11 @@ def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,)):
     lat.load(state)
     torch.cuda.synchronize()
     ev[2].record(lat.stream)
-    J, g = lat.adjoint(T, objective, args)
+    J, g = lat.adjoint(T, objective, args, checkpoint)
     ev[3].record(lat.stream)
     torch.cuda.synchronize()
     fwd, adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
-    k = int(np.ceil(np.sqrt(T)))
+    k = checkpoint if checkpoint > 0 else int(np.ceil(np.sqrt(T)))
     lat.close()
     del lat
     torch.cuda.empty_cache()
@@ -272,6 +272,10 @@ def main():
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--error-steps", type=int, default=500)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the adjoint leg (lb_adjoint against lb_step on the 64x64x256 jet)")
+    ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--adjoint-checkpoint", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     cfg = workloads.CONFIGS[args.config]
@@ -289,6 +293,13 @@ def main():
         dist.init_process_group("nccl")
 
     import paper_1804_08923_gb300 as lb
+    if args.adjoint_only:
+        if rank == 0:
+            print(json.dumps({"adjoint": adjoint_leg(lb, torch, T=args.adjoint_steps,
+                                                     checkpoint=args.adjoint_checkpoint)}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     nx, ny, nz = cfg["grid"]
     nodes = nx * ny * nz
     lat = lb.Lattice(cfg["grid"], cfg["params"], bc=cfg["bc"])
@@ -396,7 +407,7 @@ def main():
         base = None
         adjoint = None
         if world == 1 and not args.no_adjoint:
-            adjoint = adjoint_leg(lb, torch)
+            adjoint = adjoint_leg(lb, torch, T=args.adjoint_steps, checkpoint=args.adjoint_checkpoint)
         if world == 1 and not args.no_cpu_baseline:
             base = cpu_baseline(cfg)
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
