@@ -102,6 +102,9 @@ def lib():
         L.orc_mass.argtypes = [gp, dp, dp]
         L.orc_objective.argtypes = [gp, pp, dp, C.c_int, dp]
         L.orc_objective.restype = C.c_double
+        L.orc_fragments.argtypes = [gp, pp, dp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_uint8), C.c_int64]
+        L.orc_fragments.restype = C.c_int64
         cpp = C.POINTER(CSParams)
         L.orc_cs_step.argtypes = [gp, cpp, dp, dp, C.c_int64, dp, dp, C.POINTER(C.c_uint8)]
         L.orc_cs_step.restype = C.c_int
@@ -288,6 +291,24 @@ class Lattice:
         lib().orc_mass(C.byref(self.g), _p(self.S), _p(out))
         return out
 
+    def fragments(self, connectivity: int = 6, exclude_inlet: bool = True) -> dict:
+        """Fragments of the current state (reading R13): roots (smallest node index), volumes,
+        equivalent diameters d = (6V/pi)^(1/3), the excluded column volume and the mass-median
+        diameter of the kept fragments."""
+        n = lib().orc_fragments(C.byref(self.g), C.byref(self.p), _p(self.S), connectivity, None, None, None, 0)
+        if n < 0:
+            raise MemoryError("oracle fragments")
+        roots, vols, touch = np.zeros(n, np.int64), np.zeros(n, np.int64), np.zeros(n, np.uint8)
+        if n:
+            lib().orc_fragments(C.byref(self.g), C.byref(self.p), _p(self.S), connectivity,
+                                roots.ctypes.data_as(C.POINTER(C.c_int64)), vols.ctypes.data_as(C.POINTER(C.c_int64)),
+                                touch.ctypes.data_as(C.POINTER(C.c_uint8)), n)
+        column = np.zeros(n, bool)
+        if exclude_inlet and self.g.bc_zlo == BC_INLET:
+            column = touch.astype(bool)
+        keep = ~column
+        return fragment_stats(roots[keep], vols[keep], int(vols[column].sum()))
+
     def objective(self, kind: str, args=(1e-3,)):
         """Adjoint objective of the current state (reading R12): "area" (args = eps) or
         "penetration" (args = delta)."""
@@ -344,3 +365,17 @@ def tangent_objective(grid: Grid, params: dict, S0, hist0, T: int, kind: str, ar
     z = np.zeros(2)
     L.orc_cs_objective_parts(C.byref(grid), C.byref(cp), _p(S), {"area": 0, "penetration": 1}[kind], _p(a), _p(z))
     return z[0], z[1] / h
+
+
+def fragment_stats(roots, volumes, column_volume=0) -> dict:
+    """Equivalent diameters and the mass-median diameter (reading R13) of a fragment list."""
+    roots, volumes = np.asarray(roots, np.int64), np.asarray(volumes, np.int64)
+    d = (6.0 * volumes / np.pi) ** (1.0 / 3.0)
+    d_m = 0.0
+    if volumes.size:
+        order = np.argsort(volumes, kind="stable")
+        cum = np.cumsum(volumes[order])
+        k = int(np.searchsorted(cum, 0.5 * cum[-1], side="left"))
+        d_m = float(d[order][k])
+    return {"roots": roots, "volumes": volumes, "diameters": d, "mass_median_diameter": d_m,
+            "column_volume": int(column_volume), "total_volume": int(volumes.sum())}

@@ -53,6 +53,14 @@
  *   R11 Inlet profile (not in the paper, whose inlet is uniform; the parameters the
  *       adjoint differentiates): u_z = u_j0 [1 + sum_{m=1..8} (a_m cos m theta + b_m sin m theta)]
  *       with theta the polar angle of the source column about the disc centre (0 at the centre).
+ *   R13 Fragments (Section IV.B, diameter procedure): the jet region is phi > 0 of the state's
+ *       colour densities; fragments are its connected components with face (6) or full (26)
+ *       neighbourhoods, wrapping where the lattice is periodic; V = node count, d = (6V/pi)^(1/3);
+ *       the continuous column from the nozzle is every component with a node on z = 0 (inlet
+ *       lattices); the mass-median diameter is the smallest d at which fragments with diameter
+ *       <= d hold at least half the total fragment volume.  A component is named by its smallest
+ *       linear node index.
+ *
  * Forward-mode tangent (complex step): compiled with ORC_COMPLEX_STEP the same source has
  * real = double _Complex and exports orc_cs_step and orc_cs_objective.  A parameter or state
  * perturbed by i h (h ~ 1e-30) gives dJ = Im J / h to rounding (Squire and Trapp, SIAM Rev.
@@ -722,6 +730,63 @@ real orc_objective(const orc_grid *g, const orc_params *p, const real *S, int ki
     free(phi);
     return J;
 }
+
+#ifndef ORC_COMPLEX_STEP
+/* ------------------------------------------------------------- fragments (R13) */
+/* Breadth-first flood fill from every unvisited jet node in index order: the first node of a
+ * component met in that scan is its smallest index, which names it.  Writes up to cap
+ * (root, volume, touches z = 0) triples; returns the number of components or -2 on memory
+ * exhaustion. */
+int64_t orc_fragments(const orc_grid *g, const orc_params *p, const double *S, int connectivity, int64_t *roots,
+                      int64_t *volumes, uint8_t *touch_z0, int64_t cap) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const size_t nn = (size_t)nx * ny * nz;
+    const int pz = g->bc_zlo == ORC_BC_PERIODIC;
+    uint8_t *jet = (uint8_t *)malloc(nn), *seen = (uint8_t *)calloc(nn, 1);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * nn);
+    if (!jet || !seen || !queue) { free(jet); free(seen); free(queue); return -2; }
+    for (size_t n = 0; n < nn; ++n) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 27; ++i) { a += S[pidx(g, 0, i, n)]; b += S[pidx(g, 1, i, n)]; }
+        double phi = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
+        jet[n] = phi > 0.0;
+    }
+    int64_t count = 0;
+    for (size_t s0 = 0; s0 < nn; ++s0) {
+        if (!jet[s0] || seen[s0]) continue;
+        size_t head = 0, tail = 0;
+        queue[tail++] = (int64_t)s0;
+        seen[s0] = 1;
+        int64_t vol = 0;
+        int touch = 0;
+        while (head < tail) {
+            int64_t n = queue[head++];
+            ++vol;
+            int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((int64_t)nx * ny));
+            if (z == 0) touch = 1;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int m = abs(dx) + abs(dy) + abs(dz);
+                        if (m == 0 || (connectivity == 6 && m != 1)) continue;
+                        int zz = z + dz;
+                        if (pz) zz = wrap(zz, nz);
+                        else if (zz < 0 || zz >= nz) continue;
+                        size_t q = nidx(g, wrap(x + dx, nx), wrap(y + dy, ny), zz);
+                        if (jet[q] && !seen[q]) { seen[q] = 1; queue[tail++] = (int64_t)q; }
+                    }
+        }
+        if (count < cap) {
+            if (roots) roots[count] = (int64_t)s0;
+            if (volumes) volumes[count] = vol;
+            if (touch_z0) touch_z0[count] = (uint8_t)touch;
+        }
+        ++count;
+    }
+    free(jet); free(seen); free(queue);
+    return count;
+}
+#endif
 
 #ifdef ORC_COMPLEX_STEP
 /* The complex objective as (real part, imaginary part) through a pointer (a complex return
