@@ -349,6 +349,14 @@ def main():
                 "algorithmic_bytes_per_node": BYTES_KERNEL["collide_kernel"],
                 "traffic": traffic * 1.0 if traffic is not None else None}
 
+    # ---- fragment analysis of the state the timed steps reached (lb_fragments, Section IV.B)
+    fr_t0 = time.perf_counter()
+    frag = lat.fragments(6)
+    fr_ms = (time.perf_counter() - fr_t0) * 1e3
+    fragments = {"connectivity": 6, "n_fragments": int(len(frag["roots"])),
+                 "column_volume": frag["column_volume"], "mass_median_diameter": frag["mass_median_diameter"],
+                 "wall_ms": fr_ms, "state": f"after {args.warmup + 2 * args.steps} steps of the workload"}
+
     # ---- end to end through the public API with host buffers
     rr = torch.zeros(cfg["grid"][::-1], dtype=torch.float32).pin_memory()
     rb = torch.full(cfg["grid"][::-1], cfg["params"]["rho_b0"], dtype=torch.float32).pin_memory()
@@ -418,7 +426,7 @@ def main():
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
                 "fp16_storage": fp16, "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None,
-                "adjoint": adjoint}
+                "adjoint": adjoint, "fragments": fragments}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

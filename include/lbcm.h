@@ -238,6 +238,29 @@ LB_API lb_status lb_adjoint(lb_ctx *ctx, int32_t objective, int64_t T, const dou
  * memory if on_device, else host memory.  LB_ESTATE without a preceding lb_adjoint. */
 LB_API lb_status lb_adjoint_state(lb_ctx *ctx, float *out, int32_t on_device);
 
+/* ----------------------------------------------------------------- fragment analysis
+ * Fragments of the current state (Section IV.B, diameter procedure): the jet region is
+ * phi > 0 (Eq. order) of the state's colour densities; fragments are its connected components
+ * with face (connectivity 6) or full (26) neighbourhoods, wrapping across periodic boundaries;
+ * each has a volume V (nodes) and equivalent spherical diameter d = (6V/pi)^(1/3) (lattice
+ * units).  With exclude_inlet on an inlet lattice, components with a node on z = 0 are the
+ * continuous column from the nozzle and are left out (their volume is column_volume).  The
+ * mass-median diameter is the smallest d at which the fragments with diameter <= d hold at
+ * least half of the kept volume (0 without fragments).
+ * roots / volumes / diameters (host, each may be NULL): the first min(n_fragments, cap) kept
+ * fragments in increasing order of their smallest linear node index (z, y, x row-major), which
+ * names them.
+ * Device scratch of ~9 B per node is allocated for the call.  LB_EINVAL for connectivity other
+ * than 6 or 26. */
+typedef struct {
+    int64_t n_fragments;          /* kept fragments */
+    int64_t column_volume;        /* nodes of the excluded inlet-connected components */
+    int64_t total_volume;         /* nodes of the kept fragments */
+    double mass_median_diameter;  /* lattice units */
+} lb_fragment_stats;
+LB_API lb_status lb_fragments(lb_ctx *ctx, int32_t connectivity, int32_t exclude_inlet, int64_t *roots,
+                              int64_t *volumes, double *diameters, int64_t cap, lb_fragment_stats *stats);
+
 /* Message for the last failing call made by this thread ("" if none). */
 LB_API const char *lb_last_error(void);
 

@@ -216,5 +216,24 @@ class Lattice:
         _abi.check(self.lib.lb_adjoint_state(self._ctx, a.ctypes.data_as(C.POINTER(C.c_float)), 0))
         return a
 
+    # ------------------------------------------------------------------ fragments
+    def fragments(self, connectivity: int = 6, exclude_inlet: bool = True) -> dict:
+        """Fragments of the current state (lb_fragments): roots (smallest node index), volumes,
+        equivalent diameters (6V/pi)^(1/3), the excluded column volume and the mass-median
+        diameter, all computed by the library."""
+        st = _abi.FragmentStats()
+        _abi.check(self.lib.lb_fragments(self._ctx, int(connectivity), int(bool(exclude_inlet)), None, None, None, 0,
+                                         C.byref(st)))
+        n = int(st.n_fragments)
+        roots, vols, diam = np.zeros(n, np.int64), np.zeros(n, np.int64), np.zeros(n, np.float64)
+        if n:
+            _abi.check(self.lib.lb_fragments(self._ctx, int(connectivity), int(bool(exclude_inlet)),
+                                             roots.ctypes.data_as(C.POINTER(C.c_int64)),
+                                             vols.ctypes.data_as(C.POINTER(C.c_int64)),
+                                             diam.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(st)))
+        return {"roots": roots, "volumes": vols, "diameters": diam,
+                "mass_median_diameter": float(st.mass_median_diameter), "column_volume": int(st.column_volume),
+                "total_volume": int(st.total_volume)}
+
     def load(self, blob: bytes):
         _abi.check(self.lib.lb_load(self._ctx, blob, C.c_size_t(len(blob))))

@@ -19,9 +19,14 @@ STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_EUNS
 EXPORTS = ("lb_params_default", "lb_buffer_sizes", "lb_create", "lb_create_with_buffers", "lb_init", "lb_step",
            "lb_step_count", "lb_fields", "lb_populations", "lb_history", "lb_mass", "lb_mass_noalloc", "lb_save", "lb_load",
            "lb_profile_enable", "lb_profile_read", "lb_kernel_launches", "lb_set_params", "lb_adjoint",
-           "lb_adjoint_state", "lb_last_error",
+           "lb_adjoint_state", "lb_fragments", "lb_last_error",
            "lb_destroy")
 ADJ_NOUT = 21  # LB_ADJ_NOUT: J and 20 parameter gradients
+
+
+class FragmentStats(C.Structure):
+    _fields_ = [("n_fragments", C.c_int64), ("column_volume", C.c_int64), ("total_volume", C.c_int64),
+                ("mass_median_diameter", C.c_double)]
 KERNEL_NAMES = ("boundary_plane_kernel", "phase_field_kernel", "collide_kernel")
 
 
@@ -85,6 +90,8 @@ def library(path: str = LIB_PATH):
         L.lb_set_params.argtypes = [vp, pp]
         L.lb_adjoint.argtypes = [vp, C.c_int32, C.c_int64, dp, dp, C.c_int32]
         L.lb_adjoint_state.argtypes = [vp, fp, C.c_int32]
+        L.lb_fragments.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp,
+                                   C.c_int64, C.POINTER(FragmentStats)]
         L.lb_last_error.argtypes = []
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblbcm.so")
-SOURCES = ["lbcm_step.cu", "lbcm_adjoint.cu", "lbcm_api.cu"]
+SOURCES = ["lbcm_step.cu", "lbcm_adjoint.cu", "lbcm_fragments.cu", "lbcm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,6 +1,7 @@
 // lbcm_api.cu -- host side of the C ABI declared in include/lbcm.h: parameter
 // validation, device buffers, initial states, macroscopic fields, FP64 colour-mass
 // reduction, checkpoints, and the step loop.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1022,6 +1023,103 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     for (int j = 1; j < LB_ADJ_NOUT; ++j) grad_out[j] = host[j];
     w.cl = cl;
     w.valid = true;
+    return LB_OK;
+}
+
+lb_status lb_fragments(lb_ctx *c, int32_t connectivity, int32_t exclude_inlet, int64_t *roots, int64_t *volumes,
+                       double *diameters, int64_t cap, lb_fragment_stats *stats) {
+    if (!c || !stats) return fail(LB_EINVAL, "ctx and stats must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_fragments before lb_init/lb_load");
+    if (connectivity != 6 && connectivity != 26) return fail(LB_EINVAL, "connectivity must be 6 or 26");
+    if (cap < 0) return fail(LB_EINVAL, "cap must be >= 0");
+    const size_t NN = (size_t)c->nn;
+    const long long nblk = ((long long)NN + 1023) / 1024;
+    // scratch: label, count (int32), touch (u8), block counts, block offsets, error flag
+    const size_t parts[] = {NN * 4, NN * 4, NN, (size_t)nblk * 4, (size_t)(nblk + 1) * 8, 16};
+    size_t need = 0;
+    for (size_t v : parts) need += align_up(v);
+    char *base = nullptr;
+    if (cudaMalloc(&base, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LB_ENOMEM, "cannot allocate fragment scratch");
+    }
+    struct Free { char *p; ~Free() { cudaFree(p); } } guard{base};
+    char *q = base;
+    int *label = (int *)q; q += align_up(parts[0]);
+    int *count = (int *)q; q += align_up(parts[1]);
+    uint8_t *touch = (uint8_t *)q; q += align_up(parts[2]);
+    int *bc = (int *)q; q += align_up(parts[3]);
+    long long *boff = (long long *)q; q += align_up(parts[4]);
+    int *err = (int *)q;
+    cudaStream_t st = c->stream;
+    LB_CUDA(cudaMemsetAsync(count, 0, NN * 4, st));
+    LB_CUDA(cudaMemsetAsync(touch, 0, NN, st));
+    LB_CUDA(cudaMemsetAsync(err, 0, 4, st));
+    const StepArgs sa = state_args(c);
+    cudaError_t e = launch_fragments_label(sa, c->p.storage, connectivity, label, count, touch, bc, boff, err, st,
+                                           &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_fragments_label");
+    long long nroots = 0;
+    int herr = 0;
+    LB_CUDA(cudaMemcpyAsync(&nroots, boff + nblk, sizeof(nroots), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(LB_ECUDA, "fragment labelling exceeded its iteration bound");
+    std::vector<long long> hroot((size_t)nroots), hvol((size_t)nroots);
+    std::vector<uint8_t> htouch((size_t)nroots);
+    if (nroots > 0) {
+        char *ob = nullptr;
+        if (cudaMalloc(&ob, (size_t)nroots * 17 + 64) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LB_ENOMEM, "cannot allocate the fragment list");
+        }
+        Free og{ob};
+        long long *o_root = (long long *)ob, *o_vol = o_root + nroots;
+        uint8_t *o_touch = (uint8_t *)(o_vol + nroots);
+        e = launch_fragments_write(sa, connectivity, label, count, touch, boff, o_root, o_vol, o_touch, st,
+                                   &c->launches);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_fragments_write");
+        LB_CUDA(cudaMemcpyAsync(hroot.data(), o_root, (size_t)nroots * 8, cudaMemcpyDeviceToHost, st));
+        LB_CUDA(cudaMemcpyAsync(hvol.data(), o_vol, (size_t)nroots * 8, cudaMemcpyDeviceToHost, st));
+        LB_CUDA(cudaMemcpyAsync(htouch.data(), o_touch, (size_t)nroots, cudaMemcpyDeviceToHost, st));
+        LB_CUDA(cudaStreamSynchronize(st));
+    }
+    // kept fragments, diameters and the mass-median diameter (sorted by volume, ties by root)
+    const bool drop_column = exclude_inlet && c->g.bc_zlo == LB_BC_INLET;
+    std::vector<long long> kr, kv;
+    long long column = 0, total = 0;
+    for (long long k = 0; k < nroots; ++k) {
+        if (drop_column && htouch[(size_t)k]) {
+            column += hvol[(size_t)k];
+            continue;
+        }
+        kr.push_back(hroot[(size_t)k]);
+        kv.push_back(hvol[(size_t)k]);
+        total += hvol[(size_t)k];
+    }
+    double dm = 0.0;
+    if (!kv.empty()) {
+        std::vector<size_t> order(kv.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](size_t i, size_t j) { return kv[i] < kv[j]; });
+        long long cum = 0;
+        for (size_t k : order) {
+            cum += kv[k];
+            if (2 * cum >= total) {
+                dm = std::cbrt(6.0 * (double)kv[k] / 3.14159265358979323846);
+                break;
+            }
+        }
+    }
+    for (long long k = 0; k < (long long)kr.size() && k < cap; ++k) {
+        if (roots) roots[k] = kr[(size_t)k];
+        if (volumes) volumes[k] = kv[(size_t)k];
+        if (diameters) diameters[k] = std::cbrt(6.0 * (double)kv[(size_t)k] / 3.14159265358979323846);
+    }
+    stats->n_fragments = (int64_t)kr.size();
+    stats->column_volume = column;
+    stats->total_volume = total;
+    stats->mass_median_diameter = dm;
     return LB_OK;
 }
 

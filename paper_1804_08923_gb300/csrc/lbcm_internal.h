@@ -52,4 +52,16 @@ cudaError_t launch_adjoint_reduce(const AdjArgs &g, long long nblk_coll, long lo
                                   cudaStream_t s, long long *launches);
 // dJ/dS in the canonical layout [k][i][z][y][x] from (g.lp_in, g.lr_in).
 cudaError_t launch_adjoint_state(const StepArgs &a, const AdjArgs &g, float *out, cudaStream_t s, long long *launches);
+
+// Fragment labelling of the state a.pin (stored as `storage`): union-find labels (smallest node
+// index of each component, -1 outside the jet), volumes and z = 0 flags at the roots, root
+// counts per block of 1024 nodes and their exclusive scan boff[0..nblk] (boff[nblk] = roots).
+// count and touch must be zero on entry; err is set if a bounded loop ran out.
+cudaError_t launch_fragments_label(const StepArgs &a, int storage, int connectivity, int *label, int *count,
+                                   uint8_t *touch, int *bc, long long *boff, int *err, cudaStream_t s,
+                                   long long *launches);
+// The roots in index order with their volumes and z = 0 flags.
+cudaError_t launch_fragments_write(const StepArgs &a, int connectivity, const int *label, const int *count,
+                                   const uint8_t *touch, const long long *boff, long long *out_root,
+                                   long long *out_vol, uint8_t *out_touch, cudaStream_t s, long long *launches);
 }  // namespace lbcm
