@@ -32,7 +32,7 @@ BC_PERIODIC, BC_FREESLIP, BC_INLET, BC_CONVECTIVE = 0, 1, 2, 3
 
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("bc_zlo", C.c_int32), ("bc_zhi", C.c_int32)]
+                ("bc_zlo", C.c_int32), ("bc_zhi", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -200,8 +200,10 @@ def num_threads() -> int:
 
 
 # ----------------------------------------------------------------------- whole lattice
-def make_grid(nx, ny, nz, bc_zlo=BC_PERIODIC, bc_zhi=BC_PERIODIC) -> Grid:
-    return Grid(nx, ny, nz, bc_zlo, bc_zhi)
+def make_grid(nx, ny, nz, bc_zlo=BC_PERIODIC, bc_zhi=BC_PERIODIC, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC) -> Grid:
+    """Lattice extents and boundaries: z ends (PERIODIC at both or neither), x and y sides
+    PERIODIC or FREESLIP walls (reading R14)."""
+    return Grid(nx, ny, nz, bc_zlo, bc_zhi, bc_x, bc_y)
 
 
 def make_params(d: dict) -> Params:

@@ -53,6 +53,12 @@
  *   R11 Inlet profile (not in the paper, whose inlet is uniform; the parameters the
  *       adjoint differentiates): u_z = u_j0 [1 + sum_{m=1..8} (a_m cos m theta + b_m sin m theta)]
  *       with theta the polar angle of the source column about the disc centre (0 at the centre).
+ *   R14 Free-slip side walls (Section IV.A: walls cover the sides, free slip): at x = -1/2 and
+ *       x = nx - 1/2 (likewise y) a pull whose source lies beyond the wall reads the node's own
+ *       layer with that velocity component reversed (half-way specular reflection); the z rules
+ *       then act on the reflected direction at the reflected source column.  Gradient ghosts
+ *       beyond a side wall mirror the wall layer; fragments and the area objective do not wrap
+ *       across it.
  *   R13 Fragments (Section IV.B, diameter procedure): the jet region is phi > 0 of the state's
  *       colour densities; fragments are its connected components with face (6) or full (26)
  *       neighbourhoods, wrapping where the lattice is periodic; V = node count, d = (6V/pi)^(1/3);
@@ -116,7 +122,8 @@ enum { ORC_BC_PERIODIC = 0, ORC_BC_FREESLIP = 1, ORC_BC_INLET = 2, ORC_BC_CONVEC
 
 typedef struct {
     int32_t nx, ny, nz;
-    int32_t bc_zlo, bc_zhi; /* x and y are periodic */
+    int32_t bc_zlo, bc_zhi;
+    int32_t bc_x, bc_y;     /* PERIODIC or FREESLIP side walls (R14) */
 } orc_grid;
 
 typedef struct {
@@ -163,6 +170,38 @@ static int mirror_z(int i) {
     for (int j = 0; j < 27; ++j)
         if (CX[j] == CX[i] && CY[j] == CY[i] && CZ[j] == -CZ[i]) return j;
     return -1;
+}
+
+/* direction with velocity (cx, cy, cz) */
+static int dir_of(int cx, int cy, int cz) {
+    for (int j = 0; j < 27; ++j)
+        if (CX[j] == cx && CY[j] == cy && CZ[j] == cz) return j;
+    return -1;
+}
+
+/* Source column of a pull along c = (cxi, cyi) from column (x, y): wrapped where periodic,
+ * reflected into the node's own layer at a free-slip side wall (R14), which reverses that
+ * component of the direction leaving the source. */
+static void side_source(const orc_grid *g, int x, int y, int *cxi, int *cyi, int *xs, int *ys) {
+    *xs = x - *cxi;
+    *ys = y - *cyi;
+    if (*xs < 0 || *xs >= g->nx) {
+        if (g->bc_x == ORC_BC_FREESLIP) { *xs = x; *cxi = -*cxi; }
+        else *xs = ((*xs % g->nx) + g->nx) % g->nx;
+    }
+    if (*ys < 0 || *ys >= g->ny) {
+        if (g->bc_y == ORC_BC_FREESLIP) { *ys = y; *cyi = -*cyi; }
+        else *ys = ((*ys % g->ny) + g->ny) % g->ny;
+    }
+}
+
+/* Neighbour column of (x, y) along (dx, dy) for gradient ghosts: wrapped where periodic,
+ * the wall layer itself beyond a side wall (mirror ghost, R14). */
+static void side_neighbour(const orc_grid *g, int x, int y, int dx, int dy, int *xn, int *yn) {
+    *xn = x + dx;
+    *yn = y + dy;
+    if (*xn < 0 || *xn >= g->nx) *xn = g->bc_x == ORC_BC_FREESLIP ? x : ((*xn % g->nx) + g->nx) % g->nx;
+    if (*yn < 0 || *yn >= g->ny) *yn = g->bc_y == ORC_BC_FREESLIP ? y : ((*yn % g->ny) + g->ny) % g->ny;
 }
 
 #ifndef ORC_COMPLEX_STEP
@@ -446,30 +485,32 @@ void orc_stream(const orc_grid *g, const orc_params *p, const real *S, const rea
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
                 for (int i = 0; i < 27; ++i) {
-                    int xs = wrap(x - CX[i], nx), ys = wrap(y - CY[i], ny), zs = z - CZ[i];
+                    int cxi = CX[i], cyi = CY[i], xs, ys, zs = z - CZ[i];
+                    side_source(g, x, y, &cxi, &cyi, &xs, &ys);
+                    const int ii = dir_of(cxi, cyi, CZ[i]); /* direction leaving the source (R14) */
                     size_t n = nidx(g, x, y, z);
                     for (int k = 0; k < 2; ++k) {
                         real v;
                         if (g->bc_zlo == ORC_BC_PERIODIC) {
-                            v = S[pidx(g, k, i, nidx(g, xs, ys, wrap(zs, nz)))];
+                            v = S[pidx(g, k, ii, nidx(g, xs, ys, wrap(zs, nz)))];
                         } else if (zs < 0) {
                             if (g->bc_zlo == ORC_BC_INLET && in_disc(g, p, xs, ys)) {
                                 if (k == 0) {
                                     real uin[3], fe[27], zero[3] = {0, 0, 0};
                                     inlet_velocity(g, p, step, xs, ys, uin);
                                     orc_equilibrium(p->rho_r0, uin, alpha_r, p->nu_r, zero, fe);
-                                    v = fe[i];
+                                    v = fe[ii];
                                 } else {
                                     v = 0.0;
                                 }
                             } else {
-                                v = S[pidx(g, k, mirror_z(i), nidx(g, xs, ys, 0))];
+                                v = S[pidx(g, k, mirror_z(ii), nidx(g, xs, ys, 0))];
                             }
                         } else if (zs > N) {
                             /* only free-slip reaches here; the convective plane is replaced below */
-                            v = S[pidx(g, k, mirror_z(i), nidx(g, xs, ys, N))];
+                            v = S[pidx(g, k, mirror_z(ii), nidx(g, xs, ys, N))];
                         } else {
-                            v = S[pidx(g, k, i, nidx(g, xs, ys, zs))];
+                            v = S[pidx(g, k, ii, nidx(g, xs, ys, zs))];
                         }
                         f[pidx(g, k, i, n)] = v;
                     }
@@ -537,7 +578,8 @@ int orc_step(const orc_grid *g, const orc_params *p, const real *S_in, const rea
                 /* isotropic gradients of phi and rho with the ghost rules R9 */
                 real gphi[3] = {0, 0, 0}, grho[3] = {0, 0, 0};
                 for (int j = 0; j < 27; ++j) {
-                    int xn = wrap(x + CX[j], nx), yn = wrap(y + CY[j], ny), zn = z + CZ[j];
+                    int xn, yn, zn = z + CZ[j];
+                    side_neighbour(g, x, y, CX[j], CY[j], &xn, &yn);
                     real a, b;
                     if (g->bc_zlo == ORC_BC_PERIODIC) {
                         size_t m = nidx(g, xn, yn, wrap(zn, nz));
@@ -709,7 +751,9 @@ real orc_objective(const orc_grid *g, const orc_params *p, const real *S, int ki
                 for (int x = 0; x < nx; ++x) {
                     real gr[3] = {0, 0, 0};
                     for (int j = 0; j < 27; ++j) {
-                        real v = phi[nidx(g, wrap(x + CX[j], nx), wrap(y + CY[j], ny), z + CZ[j])];
+                        int xn, yn;
+                        side_neighbour(g, x, y, CX[j], CY[j], &xn, &yn);
+                        real v = phi[nidx(g, xn, yn, z + CZ[j])];
                         gr[0] += 3.0 * weight(j) * CX[j] * v;
                         gr[1] += 3.0 * weight(j) * CY[j] * v;
                         gr[2] += 3.0 * weight(j) * CZ[j] * v;
@@ -769,10 +813,18 @@ int64_t orc_fragments(const orc_grid *g, const orc_params *p, const double *S, i
                     for (int dx = -1; dx <= 1; ++dx) {
                         int m = abs(dx) + abs(dy) + abs(dz);
                         if (m == 0 || (connectivity == 6 && m != 1)) continue;
-                        int zz = z + dz;
+                        int zz = z + dz, xx = x + dx, yy = y + dy;
                         if (pz) zz = wrap(zz, nz);
                         else if (zz < 0 || zz >= nz) continue;
-                        size_t q = nidx(g, wrap(x + dx, nx), wrap(y + dy, ny), zz);
+                        if (xx < 0 || xx >= nx) {
+                            if (g->bc_x == ORC_BC_FREESLIP) continue;
+                            xx = wrap(xx, nx);
+                        }
+                        if (yy < 0 || yy >= ny) {
+                            if (g->bc_y == ORC_BC_FREESLIP) continue;
+                            yy = wrap(yy, ny);
+                        }
+                        size_t q = nidx(g, xx, yy, zz);
                         if (jet[q] && !seen[q]) { seen[q] = 1; queue[tail++] = (int64_t)q; }
                     }
         }

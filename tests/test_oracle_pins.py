@@ -482,3 +482,75 @@ def test_objective_penetration_of_a_red_slab():
     lat.init_fields(rr, rb, np.zeros((3, nz, ny, nx)))
     expect = delta * np.log(nx * ny * (q ** -(z0 + 1) * 0.25 + (q ** -(z0 + 1) - 1) / (q ** -1 - 1)))
     assert abs(lat.objective("penetration", (delta,)) - expect) < 1e-12
+
+
+# ----------------------------------------------------------- free-slip side walls (R14)
+def _mirror_dir(axis):
+    """Direction index with component `axis` of c reversed."""
+    out = []
+    for i in range(27):
+        c = [C[i, 0], C[i, 1], C[i, 2]]
+        c[axis] = -c[axis]
+        out.append(int(np.where((C[:, 0] == c[0]) & (C[:, 1] == c[1]) & (C[:, 2] == c[2]))[0][0]))
+    return np.array(out)
+
+
+def _double(S, axis, hist=None):
+    """Mirror-double a state along x (axis 0) or y (axis 1): node n - 1 - x of the copy holds
+    the populations of x with that velocity component reversed."""
+    m = _mirror_dir(axis)
+    ax = 4 - axis  # array axis of x (4) or y (3) in S[k][i][z][y][x]
+    Sm = np.flip(S[:, m], axis=ax)
+    return np.concatenate([S, Sm], axis=ax)
+
+
+@pytest.mark.parametrize("walls", [("x",), ("x", "y")])
+def test_side_walls_equal_the_mirror_doubled_periodic_lattice(walls):
+    """A half-way specular wall at x = -1/2 and x = nx - 1/2 is the mirror image of a periodic
+    lattice twice as wide: the walled step must equal the periodic step of the mirror-doubled
+    state, node for node.  Streaming is bit-identical; the mirror images' densities are the
+    same 27 values summed in another order, so the step agrees to rounding (1e-15)."""
+    nx, ny, nz = 7, 6, 5
+    bx = oracle.BC_FREESLIP if "x" in walls else oracle.BC_PERIODIC
+    by = oracle.BC_FREESLIP if "y" in walls else oracle.BC_PERIODIC
+    p = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.03, nu_b=0.07, sigma=0.004, g=(0.0, 0.0, 2e-4))
+    walled = oracle.Lattice(oracle.make_grid(nx, ny, nz, 0, 0, bx, by), oracle.make_params(
+        dict(workloads.CONFIGS["droplet32"]["params"], **p)))
+    walled.init_fields(*workloads.random_two_phase_fields((nz, ny, nx), 4, 1.0, 0.5, u_amp=0.03))
+    S = walled.S.copy()
+    D = _double(S, 0) if "x" in walls else S
+    if "y" in walls:
+        D = _double(D, 1)
+    dnx, dny = D.shape[4], D.shape[3]
+    doubled = oracle.Lattice(oracle.make_grid(dnx, dny, nz), oracle.make_params(
+        dict(workloads.CONFIGS["droplet32"]["params"], **p)))
+    doubled.set_state(D, np.zeros((2, 27, dny, dnx)))
+    for t in range(3):
+        fw, _ = walled.stream()
+        fd, _ = doubled.stream()
+        assert np.abs(fw - fd[..., :ny, :nx]).max() <= (0.0 if t == 0 else 1e-15)
+        walled.step(1)
+        doubled.step(1)
+        assert np.abs(walled.S - doubled.S[..., :ny, :nx]).max() < 1e-15
+
+
+def test_closed_box_conserves_colour_mass_and_tangential_flow():
+    """x, y and z free-slip walls: per-colour mass to round-off with gravity; a uniform flow
+    along z between x and y walls (tangential to both) is a fixed point with z periodic."""
+    shape = (6, 7, 8)
+    lat = oracle.Lattice(oracle.make_grid(8, 7, 6, oracle.BC_FREESLIP, oracle.BC_FREESLIP, oracle.BC_FREESLIP,
+                                          oracle.BC_FREESLIP),
+                         oracle.make_params(dict(workloads.CONFIGS["droplet32"]["params"], rho_b0=0.5, nu_b=0.05,
+                                                 g=(1e-4, -1e-4, 3e-4))))
+    lat.init_fields(*workloads.random_two_phase_fields(shape, 6, 1.0, 0.5, u_amp=0.03))
+    m0 = lat.mass()
+    lat.step(8)
+    assert np.abs(lat.mass() / m0 - 1).max() < 1e-13
+    uni = oracle.Lattice(oracle.make_grid(8, 7, 6, 0, 0, oracle.BC_FREESLIP, oracle.BC_FREESLIP),
+                         oracle.make_params(dict(workloads.CONFIGS["droplet32"]["params"], sigma=0.0)))
+    u = np.zeros((3,) + shape)
+    u[2] = 0.04
+    uni.init_fields(np.full(shape, 0.6), np.full(shape, 0.4), u)
+    S0 = uni.S.copy()
+    uni.step(5)
+    assert np.abs(uni.S - S0).max() < 1e-15
