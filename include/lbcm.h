@@ -62,6 +62,11 @@ typedef enum {
 typedef struct {
     int32_t nx, ny, nz;    /* lattice extent; nx*ny*nz < 2^31 */
     int32_t bc_zlo, bc_zhi;
+    int32_t bc_x, bc_y;    /* LB_BC_PERIODIC (0) or LB_BC_FREESLIP side walls (Section IV.A: the
+                              jet's side walls are free-slip): a pull whose source lies beyond a
+                              wall reads the node's own layer with that velocity component
+                              reversed (half-way specular reflection); gradient ghosts mirror
+                              the wall layer */
 } lb_grid;
 
 /* Population storage.  FP32: every population in single precision.  FP16: the 26 moving

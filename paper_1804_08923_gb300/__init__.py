@@ -33,7 +33,8 @@ def _torch():
 class Lattice:
     """One D3Q27 two-colour lattice resident on a CUDA device.
 
-    grid: (nx, ny, nz); bc: (bc_zlo, bc_zhi); params: dict of lb_params fields.
+    grid: (nx, ny, nz); bc: (bc_zlo, bc_zhi) or (bc_zlo, bc_zhi, bc_x, bc_y) with x and y
+    PERIODIC or FREESLIP side walls; params: dict of lb_params fields.
     Buffers are torch uint8 tensors owned by this object (PyTorch's caching allocator);
     the library works on them through lb_create_with_buffers.
     """

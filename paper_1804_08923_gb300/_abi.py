@@ -38,7 +38,7 @@ class LBError(RuntimeError):
 
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("bc_zlo", C.c_int32), ("bc_zhi", C.c_int32)]
+                ("bc_zlo", C.c_int32), ("bc_zhi", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -110,8 +110,9 @@ def check(status: int):
         raise LBError(status, msg)
 
 
-def make_grid(nx, ny, nz, bc_zlo=BC_PERIODIC, bc_zhi=BC_PERIODIC) -> Grid:
-    return Grid(nx, ny, nz, bc_zlo, bc_zhi)
+def make_grid(nx, ny, nz, bc_zlo=BC_PERIODIC, bc_zhi=BC_PERIODIC, bc_x=BC_PERIODIC, bc_y=BC_PERIODIC) -> Grid:
+    """Extents and boundaries: z ends, x and y sides (PERIODIC or FREESLIP walls)."""
+    return Grid(nx, ny, nz, bc_zlo, bc_zhi, bc_x, bc_y)
 
 
 def make_params(d: dict) -> Params:

@@ -445,11 +445,11 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
             // slots the plain pulls would have read are read by nobody
             g.lc[(size_t)i * P + nb.pxy] = o.x;
             g.lc[(size_t)(27 + i) * P + nb.pxy] = o.y;
-            if (cz(i) >= 0) g.lp_out[(size_t)i * a.NN + nb.src(i)] = make_float2(0.0f, 0.0f);
+            if (cz(i) >= 0) g.lp_out[(size_t)nb.pulled(i) * a.NN + nb.src(i)] = make_float2(0.0f, 0.0f);
             if (cz(i) == 1) g.lp_out[(size_t)i * a.NN + nb.n] = make_float2(0.0f, 0.0f);
         } else if (!pz && z == 0 && cz(i) == 1) {
-            const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];  // source column (offsets)
-            const size_t slot = (size_t)mirror_z(i) * a.NN + ys + xs;
+            const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];  // source column (offsets, reflected)
+            const size_t slot = (size_t)mirror_z(nb.pulled(i)) * a.NN + ys + xs;
             if (a.bc_zlo == BC_INLET && a.disc[ys + xs]) {
                 g.li[(size_t)zrank(i) * P + nb.pxy] = o.x;
                 g.lp_out[slot] = make_float2(0.0f, 0.0f);
@@ -458,9 +458,9 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
             }
         } else if (!pz && z == N && cz(i) == -1 && a.bc_zhi == BC_FREESLIP) {
             const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];
-            g.lp_out[(size_t)mirror_z(i) * a.NN + (size_t)N * P + ys + xs] = o;
+            g.lp_out[(size_t)mirror_z(nb.pulled(i)) * a.NN + (size_t)N * P + ys + xs] = o;
         } else {
-            g.lp_out[(size_t)i * a.NN + nb.src(i)] = o;
+            g.lp_out[(size_t)nb.pulled(i) * a.NN + nb.src(i)] = o;
         }
     }
 }
@@ -500,13 +500,17 @@ __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g)
         const bool below = !pz && z == 0 && cz(j) == 1;   // x = y - c_j would sit on z = -1
         const bool above = !pz && z == N && cz(j) == -1;  // ... on z = N + 1
         if (below && lo_const) continue;
+        // beyond a wall the reader is on this layer and reached y through its mirror ghost
+        // with that component of c reversed
         const float czj = (below || above) ? -(float)cz(j) : (float)cz(j);
-        const int src = nb.src(j);  // clamped onto the wall plane: the mirrored reader
+        const float cxj = nb.fx(j) ? -(float)cx(j) : (float)cx(j);
+        const float cyj = nb.fy(j) ? -(float)cy(j) : (float)cy(j);
+        const int src = nb.src(j);  // clamped onto the wall layer: the mirrored reader
         const float4 A = __ldg(g.lga + src);
         const float2 B = __ldg(g.lgb + src);
         const float w3 = 3.0f * wgt(j);
-        lphi = fmaf(w3, (float)cx(j) * A.x + (float)cy(j) * A.y + czj * A.z, lphi);
-        lrho = fmaf(w3, (float)cx(j) * A.w + (float)cy(j) * B.x + czj * B.y, lrho);
+        lphi = fmaf(w3, cxj * A.x + cyj * A.y + czj * A.z, lphi);
+        lrho = fmaf(w3, cxj * A.w + cyj * B.x + czj * B.y, lrho);
     }
     float phv, S_;  // phi and rho_r/rho_r0 + rho_b/rho_b0 of this node
     if (g.rec) {
@@ -542,10 +546,19 @@ __global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g
         const int i = lane < 27 ? lane : 0;
         const int cxi = (int)((kPackX >> (2 * i)) & 3ull) - 1, cyi = (int)((kPackY >> (2 * i)) & 3ull) - 1,
                   czi = (int)((kPackZ >> (2 * i)) & 3ull) - 1;
+        // source column of the pull of direction i, reflected at free-slip side walls, and the
+        // direction that leaves it
+        int xs = x - cxi, ys = y - cyi, cxs = cxi, cys = cyi;
+        if (xs < 0 || xs >= a.nx) {
+            if (a.wall_x) { xs = x; cxs = -cxi; } else xs = wrapi(xs, a.nx);
+        }
+        if (ys < 0 || ys >= a.ny) {
+            if (a.wall_y) { ys = y; cys = -cyi; } else ys = wrapi(ys, a.ny);
+        }
+        const int ii = dir_of(cxs, cys, czi);
         const int q = cxi * cxi + cyi * cyi + czi * czi;
         const float w_i = q == 0 ? 8.0f / 27.0f : q == 1 ? 2.0f / 27.0f : q == 2 ? 1.0f / 54.0f : 1.0f / 216.0f;
         if (a.bc_zlo == BC_INLET && lane < 27 && czi == 1) {
-            const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny);
             if (a.disc[(size_t)ys * a.nx + xs]) {
                 // rank of i among the c_z = +1 directions
                 int zr = 0;
@@ -553,7 +566,7 @@ __global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g
                 const float lam = g.li[(size_t)zr * P + pxy] + g.lr_out[pxy].x;
                 InletVel iv;
                 inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
-                const float c0 = (float)cxi, c1 = (float)cyi, c2 = (float)czi;
+                const float c0 = (float)cxs, c1 = (float)cys, c2 = (float)czi;  // direction leaving the ghost
                 const float cu = c0 * iv.ux + c1 * iv.uy + c2 * iv.uz;
                 const float usq = iv.ux * iv.ux + iv.uy * iv.uy + iv.uz * iv.uz;
                 // d f^e_i / d u = rho_r0 w_i [(3 + 9 cu + 27/2 cu^2 - 9/2 u^2) c_i - (3 + 9 cu) u]
@@ -574,7 +587,7 @@ __global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g
         if (a.bc_zhi == BC_CONVECTIVE) {
             const int N = a.nz - 1, zm = N - 1;
             const Nbr nbm(a, x, y, zm);
-            // the source of f_i(x, y, N-1) (plain pull: 1 <= N-1)
+            // the source of f_i(x, y, N-1) (plain pull in z: 1 <= N-1; reflected at side walls)
             const int src = nbm.zo[czi + 1] + nbm.yo[cyi + 1] + nbm.xo[cxi + 1];
             float fr = 0.0f, fb = 0.0f;
             if (lane < 27) {  // f(N-1) as the forward step pulled it
@@ -601,7 +614,7 @@ __global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g
             if (lane < 27) {
                 const bool active = lam_raw > 0.0f && lam_raw < 1.0f;
                 const float dl = active ? llam * ((float)czi + 0.5f * a.gz - lam_raw) / rho : 0.0f;
-                float2 *slot = g.lp_out + (size_t)i * a.NN + src;
+                float2 *slot = g.lp_out + (size_t)ii * a.NN + src;
                 float2 v = *slot;
                 v.x += fmaf(lvr, lam * inv, dl);
                 v.y += fmaf(lvb, lam * inv, dl);

@@ -76,6 +76,8 @@ lb_status validate(const lb_grid *g, const lb_params *p) {
     if ((g->bc_zlo == LB_BC_PERIODIC) != (g->bc_zhi == LB_BC_PERIODIC))
         return fail(LB_EINVAL, "z must be periodic at both ends or at neither");
     if (g->bc_zlo != LB_BC_PERIODIC && g->nz < 2) return fail(LB_EINVAL, "walls need nz >= 2");
+    if ((g->bc_x != LB_BC_PERIODIC && g->bc_x != LB_BC_FREESLIP) || (g->bc_y != LB_BC_PERIODIC && g->bc_y != LB_BC_FREESLIP))
+        return fail(LB_EINVAL, "bc_x and bc_y must be PERIODIC or FREESLIP");
     if (g->bc_zhi == LB_BC_CONVECTIVE && g->nz < 3) return fail(LB_EINVAL, "convective outflow needs nz >= 3");
     if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0)) return fail(LB_EINVAL, "rho_r0 and rho_b0 must be > 0");
     if (!(p->nu_r > 0) || !(p->nu_b > 0)) return fail(LB_EINVAL, "nu_r and nu_b must be > 0");
@@ -423,6 +425,8 @@ StepArgs make_args(const lb_ctx *c) {
     a.plane = c->plane;
     a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
     a.bc_zlo = g.bc_zlo; a.bc_zhi = g.bc_zhi;
+    a.wall_x = g.bc_x == LB_BC_FREESLIP;
+    a.wall_y = g.bc_y == LB_BC_FREESLIP;
     a.rho_r0 = (float)p.rho_r0; a.rho_b0 = (float)p.rho_b0;
     a.inv_rho_r0 = (float)(1.0 / p.rho_r0); a.inv_rho_b0 = (float)(1.0 / p.rho_b0);
     const double alpha_b = 8.0 / 27.0;

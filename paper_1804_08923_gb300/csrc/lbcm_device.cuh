@@ -28,6 +28,17 @@ __host__ __device__ constexpr int mirror_z(int i) {
         if (cx(j) == cx(i) && cy(j) == cy(i) && cz(j) == -cz(i)) r = j;
     return r;
 }
+// direction with velocity (x, y, z)
+__host__ __device__ constexpr int dir_of(int x, int y, int z) {
+    int r = 0;
+    for (int j = 0; j < 27; ++j)
+        if (cx(j) == x && cy(j) == y && cz(j) == z) r = j;
+    return r;
+}
+// direction i with c_x, c_y or both reversed (specular reflection on a side wall)
+__host__ __device__ constexpr int flip_x(int i) { return dir_of(-cx(i), cy(i), cz(i)); }
+__host__ __device__ constexpr int flip_y(int i) { return dir_of(cx(i), -cy(i), cz(i)); }
+__host__ __device__ constexpr int flip_xy(int i) { return dir_of(-cx(i), -cy(i), cz(i)); }
 // rank of direction i among those with the same c_z = +1 (or -1), 0..8
 __host__ __device__ constexpr int zrank(int i) {
     int r = 0;
@@ -146,6 +157,7 @@ struct StepArgs {
     const uint8_t *__restrict__ disc;   // inlet disc membership [ny][nx]
     long long NN, plane;                // nodes, nx*ny
     int nx, ny, nz, bc_zlo, bc_zhi;
+    int wall_x, wall_y;                 // free-slip side walls (else periodic)
     float rho_r0, rho_b0, inv_rho_r0, inv_rho_b0;
     float alpha_r, alpha_b, inv_nu_r, inv_nu_b;
     float sigma, beta, eps2;
@@ -170,20 +182,26 @@ __device__ __forceinline__ float2 shift_w(const StepArgs &a, int i) {
     return make_float2(a.shift_r[csq(i)], a.shift_b[csq(i)]);
 }
 
-// Populations (red, blue) of direction i stored at node src, decoded to FP32; for FP16,
-// own = (rho_r, rho_b) of the reading node, the node the value was encoded for.
+// Populations (red, blue) of direction j stored at node src, decoded to FP32; for FP16,
+// own = (rho_r, rho_b) of the reading node, the node the value was encoded for.  i is a
+// direction with |c_i| = |c_j| (j itself, or the direction j is reflected from at a side wall):
+// it selects the shift weight, so that an unrolled caller indexes the weights at compile time.
 template <int S>
-__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, float2 own) {
+__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, float2 own, int j) {
     if constexpr (S == STORE_FP32) {
-        return __ldg(reinterpret_cast<const float2 *>(a.pin) + (size_t)i * a.NN + src);
+        return __ldg(reinterpret_cast<const float2 *>(a.pin) + (size_t)j * a.NN + src);
     } else {
         const float2 *rest = reinterpret_cast<const float2 *>(a.pin);
         if (i == 0) return __ldg(rest + src);
         const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
-        const float2 h = __half22float2(__ldg(mov + (size_t)(i - 1) * a.NN + src));
+        const float2 h = __half22float2(__ldg(mov + (size_t)(j - 1) * a.NN + src));
         const float2 w = shift_w(a, i);
         return make_float2(fmaf(own.x, w.x, h.x), fmaf(own.y, w.y, h.y));
     }
+}
+template <int S>
+__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, float2 own) {
+    return load_pop<S>(a, i, src, own, i);
 }
 
 // Colour densities a node decodes its gathered populations with (FP16; unused for FP32).
@@ -223,12 +241,14 @@ __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >
 
 // 32-bit offsets of the node and of its three neighbouring columns, rows and planes:
 // xo[d+1] = x - d, yo[d+1] = (y - d) nx, zo[d+1] = (z - d) nx ny for d = -1, 0, 1, wrapped
-// periodically in x and y (and z if periodic), clamped to [0, N] in z otherwise.  The pull
+// where periodic and clamped onto the wall layer at walls (the half-way reflection returns to
+// the node's own layer; gradient ghosts mirror it).  The pull
 // source of direction i is zo[cz+1] + yo[cy+1] + xo[cx+1]; the neighbour x + c_j is
 // zo[1-cz] + yo[1-cy] + xo[1-cx].  nx ny nz < 2^31 keeps every offset in 32 bits.
 struct Nbr {
     int xo[3], yo[3], zo[3];
     int n, pxy;
+    bool wxl, wxh, wyl, wyh;  // the node lies on a free-slip side wall (x = 0, x = nx-1, y = 0, y = ny-1)
     __device__ __forceinline__ Nbr(const StepArgs &a, int x, int y, int z) {
         const bool periodic_z = a.bc_zlo == BC_PERIODIC;
         const int N = a.nz - 1, P = (int)a.plane;
@@ -238,14 +258,31 @@ struct Nbr {
             if (periodic_z) zs = wrapi(zs, a.nz);
             zs = min(max(zs, 0), N);
             zo[d + 1] = zs * P;
-            yo[d + 1] = wrapi(y - d, a.ny) * a.nx;
-            xo[d + 1] = wrapi(x - d, a.nx);
+            const int ys = a.wall_y ? min(max(y - d, 0), a.ny - 1) : wrapi(y - d, a.ny);
+            const int xs = a.wall_x ? min(max(x - d, 0), a.nx - 1) : wrapi(x - d, a.nx);
+            yo[d + 1] = ys * a.nx;
+            xo[d + 1] = xs;
         }
         pxy = yo[1] + x;
         n = zo[1] + pxy;
+        wxl = a.wall_x && x == 0;
+        wxh = a.wall_x && x == a.nx - 1;
+        wyl = a.wall_y && y == 0;
+        wyh = a.wall_y && y == a.ny - 1;
     }
     __device__ __forceinline__ int src(int i) const { return zo[cz(i) + 1] + yo[cy(i) + 1] + xo[cx(i) + 1]; }
     __device__ __forceinline__ int nbr(int j) const { return zo[1 - cz(j)] + yo[1 - cy(j)] + xo[1 - cx(j)]; }
+    // whether the pull of direction i (source x - c_i) crosses a side wall in x / in y
+    __device__ __forceinline__ bool fx(int i) const { return cx(i) > 0 ? wxl : (cx(i) < 0 ? wxh : false); }
+    __device__ __forceinline__ bool fy(int i) const { return cy(i) > 0 ? wyl : (cy(i) < 0 ? wyh : false); }
+    // the direction that leaves the (reflected) source of the pull of direction i
+    __device__ __forceinline__ int pulled(int i) const {
+        const bool bx = fx(i), by = fy(i);
+        return bx ? (by ? flip_xy(i) : flip_x(i)) : (by ? flip_y(i) : i);
+    }
+    // whether the neighbour x + c_j lies beyond a side wall in x / in y (mirror ghost)
+    __device__ __forceinline__ bool gx(int j) const { return cx(j) < 0 ? wxl : (cx(j) > 0 ? wxh : false); }
+    __device__ __forceinline__ bool gy(int j) const { return cy(j) < 0 ? wyl : (cy(j) > 0 ? wyh : false); }
 };
 
 // Colour densities of the node that will read direction i from node nb.n (FP16 encoding).

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) frag_init_kernel(StepArgs a, int *label) 
 }
 
 struct FragGeom {
-    int nx, ny, nz, periodic_z, conn;
+    int nx, ny, nz, periodic_z, conn, wall_x, wall_y;
     long long NN, plane;
 };
 
@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(256) frag_union_kernel(FragGeom g, int *label,
                         if (!g.periodic_z) continue;
                         zz += g.nz;
                     }
+                    if ((g.wall_x && (x + dx < 0 || x + dx >= g.nx)) || (g.wall_y && (y + dy < 0 || y + dy >= g.ny)))
+                        continue;  // no neighbour across a side wall
                     const int xx = x + dx < 0 ? x + dx + g.nx : (x + dx >= g.nx ? x + dx - g.nx : x + dx);
                     const int yy = y + dy < 0 ? y + dy + g.ny : (y + dy >= g.ny ? y + dy - g.ny : y + dy);
                     const long long m = (long long)zz * g.plane + (long long)yy * g.nx + xx;
@@ -181,7 +183,7 @@ static int frag_grid(long long n) {
 cudaError_t launch_fragments_label(const StepArgs &a, int storage, int connectivity, int *label, int *count,
                                    uint8_t *touch, int *bc, long long *boff, int *err, cudaStream_t s,
                                    long long *launches) {
-    FragGeom g{a.nx, a.ny, a.nz, a.bc_zlo == BC_PERIODIC, connectivity, a.NN, a.plane};
+    FragGeom g{a.nx, a.ny, a.nz, a.bc_zlo == BC_PERIODIC, connectivity, a.wall_x, a.wall_y, a.NN, a.plane};
     if (storage == STORE_FP16)
         frag_init_kernel<STORE_FP16><<<frag_grid(a.NN), 256, 0, s>>>(a, label);
     else
@@ -199,7 +201,7 @@ cudaError_t launch_fragments_label(const StepArgs &a, int storage, int connectiv
 cudaError_t launch_fragments_write(const StepArgs &a, int connectivity, const int *label, const int *count,
                                    const uint8_t *touch, const long long *boff, long long *out_root,
                                    long long *out_vol, uint8_t *out_touch, cudaStream_t s, long long *launches) {
-    FragGeom g{a.nx, a.ny, a.nz, a.bc_zlo == BC_PERIODIC, connectivity, a.NN, a.plane};
+    FragGeom g{a.nx, a.ny, a.nz, a.bc_zlo == BC_PERIODIC, connectivity, a.wall_x, a.wall_y, a.NN, a.plane};
     const long long nblk = (a.NN + kFragBlock - 1) / kFragBlock;
     frag_write_kernel<<<(unsigned)nblk, kFragBlock, 0, s>>>(g, label, count, touch, boff, out_root, out_vol, out_touch);
     *launches += 1;

@@ -9,7 +9,7 @@ namespace lbcm {
 
 // Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
-template <int S>
+template <int S, bool W>
 __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, float (&fr)[27], float (&fb)[27]) {
     const size_t P = (size_t)a.plane;
     const int N = a.nz - 1;
@@ -35,7 +35,9 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
             fr[i] = a.zout[zrank(i) * P + nb.pxy];
             fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
         } else {
-            const float2 v = load_pop<S>(a, i, nb.src(i), own);
+            // W: the lattice has side walls, where the pull reflects (the direction leaving the
+            // source is nb.pulled(i)); without them the plane index is a compile-time constant
+            const float2 v = load_pop<S>(a, i, nb.src(i), own, W ? nb.pulled(i) : i);
             fr[i] = v.x;
             fb[i] = v.y;
         }
@@ -105,13 +107,13 @@ struct Moments {
     float rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
 };
 
-template <int S>
+template <int S, bool W>
 __device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb, int z, Moments &m) {
     float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
     {
         float fr[27], fb[27];
-        gather<S>(a, nb, z, fr, fb);
+        gather<S, W>(a, nb, z, fr, fb);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {  // same order as the phase-field kernel
             rho_r += fr[i];

@@ -61,20 +61,29 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
     const int i = lane < 27 ? lane : 0;
     const int cxi = cx(i), cyi = cy(i), czi = cz(i);
     const bool mine = lane < 27;
+    // source column of the pull of direction i, reflected at free-slip side walls, and the
+    // direction that leaves it
+    int xs = x - cxi, ys = y - cyi, cxs = cxi, cys = cyi;
+    if (xs < 0 || xs >= a.nx) {
+        if (a.wall_x) { xs = x; cxs = -cxi; } else xs = wrapi(xs, a.nx);
+    }
+    if (ys < 0 || ys >= a.ny) {
+        if (a.wall_y) { ys = y; cys = -cyi; } else ys = wrapi(ys, a.ny);
+    }
+    const int ii = dir_of(cxs, cys, czi);
 
     if ((a.bc_zlo == BC_INLET || a.bc_zlo == BC_FREESLIP) && mine && czi == 1) {
-        const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny);
         float vr, vb;
         if (a.bc_zlo == BC_INLET && a.disc[(long long)ys * a.nx + xs]) {
             // red equilibrium f^e(rho_r0, u_in) with alpha_r and Phi = 0, no blue
             InletVel iv;
             inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
-            const float cu = (float)cxi * iv.ux + (float)cyi * iv.uy + (float)czi * iv.uz;
+            const float cu = (float)cxs * iv.ux + (float)cys * iv.uy + (float)czi * iv.uz;
             const float usq = iv.ux * iv.ux + iv.uy * iv.uy + iv.uz * iv.uz;
             vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
             vb = 0.0f;
         } else {  // half-way specular reflection at z = -1/2
-            const float2 v = load_pop<S>(a, mirror_z(i), ys * a.nx + xs, reader_shift<S>(a, (int)pxy));
+            const float2 v = load_pop<S>(a, mirror_z(ii), ys * a.nx + xs, reader_shift<S>(a, (int)pxy));
             vr = v.x;
             vb = v.y;
         }
@@ -82,8 +91,7 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
         a.zin[(long long)(9 + zrank(i)) * P + pxy] = vb;
     }
     if (a.bc_zhi == BC_FREESLIP && mine && czi == -1) {
-        const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny);
-        const float2 v = load_pop<S>(a, mirror_z(i), (N * a.ny + ys) * a.nx + xs,
+        const float2 v = load_pop<S>(a, mirror_z(ii), (N * a.ny + ys) * a.nx + xs,
                                      reader_shift<S>(a, N * (int)P + (int)pxy));
         a.zout[(long long)zrank(i) * P + pxy] = v.x;
         a.zout[(long long)(9 + zrank(i)) * P + pxy] = v.y;
@@ -93,8 +101,8 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
         const int z = N - 1;
         float fr = 0.0f, fb = 0.0f;
         if (mine) {
-            const int xs = wrapi(x - cxi, a.nx), ys = wrapi(y - cyi, a.ny), zs = z - czi;
-            const float2 v = load_pop<S>(a, i, (zs * a.ny + ys) * a.nx + xs, reader_shift<S>(a, z * (int)P + (int)pxy));
+            const int zs = z - czi;
+            const float2 v = load_pop<S>(a, ii, (zs * a.ny + ys) * a.nx + xs, reader_shift<S>(a, z * (int)P + (int)pxy));
             fr = v.x;
             fb = v.y;
         }
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
 }
 
 // --------------------------------------------------------------- phase field (K_A)
-template <int S>
+template <int S, bool W>
 __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -125,7 +133,7 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     if (x >= a.nx || y >= a.ny) return;
     const Nbr nb(a, x, y, z);
     float fr[27], fb[27];
-    gather<S>(a, nb, z, fr, fb);
+    gather<S, W>(a, nb, z, fr, fb);
     float rr = 0.0f, rb = 0.0f;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
@@ -159,7 +167,7 @@ __device__ __forceinline__ void sweep_inv(float &a0, float &a1, float &a2, float
 }
 
 // ------------------------- collide, perturb, recolour (K_B), any relaxation rates
-template <int S>
+template <int S, bool W>
 __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     float rho_r = 0.0f, rho_b = 0.0f;
     {
         float fr[27], fb[27];
-        gather<S>(a, nb, z, fr, fb);
+        gather<S, W>(a, nb, z, fr, fb);
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             rho_r += fr[i];
@@ -439,7 +447,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
 // kRec (FP32, adjoint recompute): also writes the node's collision inputs to a.rec / a.rec4.
-template <bool kForce, int S, bool kRec>
+template <bool kForce, int S, bool kRec, bool W>
 __global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -447,7 +455,7 @@ __global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel
     if (x >= a.nx || y >= a.ny) return;
     const Nbr nb(a, x, y, z);
     Moments mo;
-    gather_moments<S>(a, nb, z, mo);
+    gather_moments<S, W>(a, nb, z, mo);
     float gpx, gpy, gpz, grx, gry, grz;
     stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
     if constexpr (kRec) {
@@ -463,8 +471,8 @@ __global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel
 
 
 // ------------------------------------------------------------------------ launchers
-template <int S>
-static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, bool collide) {
+template <int S, bool W>
+static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, bool collide) {
     if (ev) cudaEventRecord(ev[0], s);
     if (a.bc_zlo != BC_PERIODIC || a.bc_zhi != BC_PERIODIC) {
         boundary_plane_kernel<S><<<(unsigned)((a.plane + 3) / 4), 128, 0, s>>>(a);
@@ -474,23 +482,31 @@ static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, lo
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
     dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
     if (ev) cudaEventRecord(ev[1], s);
-    phase_field_kernel<S><<<grd, blk, 0, s>>>(a);
+    phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
     *launches += 1;
     if (!collide) return;
     const bool rec = S == STORE_FP32 && a.rec != nullptr;  // paper rates only (adjoint)
     if (!paper_rates)
-        collide_general_kernel<S><<<grd, blk, 0, s>>>(a);
+        collide_general_kernel<S, W><<<grd, blk, 0, s>>>(a);
     else if (rec && force)
-        collide_kernel<true, S, S == STORE_FP32><<<grd, blk, 0, s>>>(a);
+        collide_kernel<true, S, S == STORE_FP32, W><<<grd, blk, 0, s>>>(a);
     else if (rec)
-        collide_kernel<false, S, S == STORE_FP32><<<grd, blk, 0, s>>>(a);
+        collide_kernel<false, S, S == STORE_FP32, W><<<grd, blk, 0, s>>>(a);
     else if (force)
-        collide_kernel<true, S, false><<<grd, blk, 0, s>>>(a);
+        collide_kernel<true, S, false, W><<<grd, blk, 0, s>>>(a);
     else
-        collide_kernel<false, S, false><<<grd, blk, 0, s>>>(a);
+        collide_kernel<false, S, false, W><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     *launches += 1;
+}
+
+template <int S>
+static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, bool collide) {
+    if (a.wall_x || a.wall_y)
+        launch_step_sw<S, true>(a, s, ev, launches, collide);
+    else
+        launch_step_sw<S, false>(a, s, ev, launches, collide);
 }
 
 cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches,

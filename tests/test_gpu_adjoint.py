@@ -239,3 +239,43 @@ def test_adjoint_full_size_jet_short_horizon(lb):
     got = np.array([g[NAMES.index(n)] for n in names])
     err = np.abs(got - g_tan).max() / np.abs(g_tan).max()
     assert err < TOL, (err, got, g_tan)
+
+
+def test_adjoint_with_side_walls(lb):
+    """The paper's boundaries (side walls free-slip): gradients against the oracle's tangent and
+    central differences."""
+    grid, bc, params = jet_case()
+    bc = tuple(bc) + (1, 1)
+    T = 10
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    J, g = lat.adjoint(T, "area", (1e-3,))
+    init = lambda r: r.init_jet()
+    names = ("u_in", "sigma", "nu_r", "nu_b", "a1", "b2", "a5")
+    idx = [NAMES.index(n) for n in names]
+    g_tan = tangent_gradient(grid, bc, params, init, T, "area", (1e-3,), names)
+    err = np.abs(g[idx] - g_tan).max() / np.abs(g_tan).max()
+    assert err < TOL, (err, g[idx], g_tan)
+    g_fd = fd_gradient(grid, bc, params, init, T, "area", (1e-3,), names)
+    assert np.abs(g[idx] - g_fd).max() / np.abs(g_fd).max() < TOL
+
+
+def test_adjoint_state_with_side_walls(lb):
+    """dJ/dS(0) along a random direction, closed box (all walls free-slip), gravity."""
+    nx, ny, nz = 11, 10, 9
+    shape = (nz, ny, nx)
+    bc = (1, 1, 1, 1)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.05, sigma=0.004, g=(1e-5, -2e-5, 3e-5))
+    fields = workloads.random_two_phase_fields(shape, 21, 1.0, 0.5, u_amp=0.03)
+    lat = lb.Lattice((nx, ny, nz), params, bc=bc)
+    lat.init_fields(*fields)
+    T = 6
+    lat.adjoint(T, "area", (1e-3,), checkpoint=2)
+    lS = lat.adjoint_state().astype(np.float64)
+    dS = np.random.default_rng(6).standard_normal((2, 27) + shape) * 1e-3
+    ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *bc), oracle.make_params(full_params(params)))
+    ref.init_fields(*fields)
+    _, tan = oracle.tangent_objective(oracle.make_grid(nx, ny, nz, *bc), full_params(params), ref.S, ref.hist, T,
+                                      "area", (1e-3,), dS=dS)
+    ad = float((lS * dS).sum())
+    assert abs(ad - tan) < TOL * abs(tan), (ad, tan)

@@ -107,3 +107,13 @@ def test_full_size_field(lb):
     jet = balls(shape, spec)
     gpu, ref = both(lb, jet, bc=(1, 1))
     same(gpu.fragments(6), ref.fragments(6))
+
+
+def test_no_fragment_joins_across_a_side_wall(lb):
+    """With free-slip side walls a ball cut by the x = 0 plane is two pieces, not one wrapped
+    fragment; against the oracle."""
+    jet = balls((14, 12, 20), [((0.2, 6.0, 7.0), 3.3), ((10.0, 0.1, 6.0), 2.8)])
+    gw, rw = both(lb, jet, bc=(1, 1, 1, 1))
+    same(gw.fragments(6), rw.fragments(6))
+    gp, rp = both(lb, jet, bc=(1, 1))
+    assert len(gw.fragments(6)["roots"]) == len(gp.fragments(6)["roots"]) + 2

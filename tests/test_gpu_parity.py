@@ -345,3 +345,46 @@ def test_fp16_save_load_roundtrip_is_bitwise(lb):
     gpu.load(blob)
     gpu.step(5)
     assert np.array_equal(gpu.populations(device=False), a)
+
+
+# ------------------------------------------------------------ free-slip side walls
+def test_side_walls_jet_parity(lb):
+    """The paper's jet boundaries (Section IV.A): inlet disc at z = 0, convective outflow, and
+    free-slip walls on all four sides, 36x34x40, 50 steps."""
+    cfg = workloads.scaled_jet("jet96", 36, 34, 40, D=10)
+    params = cfg["params"]
+    shape = (40, 34, 36)
+    bc = tuple(cfg["bc"]) + (1, 1)
+    gpu, ref = pair(lb, shape, params, bc=bc)
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 50)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+@pytest.mark.parametrize("walls", [(1, 0), (0, 1), (1, 1)])
+def test_closed_and_side_walled_boxes_with_gravity(lb, walls):
+    """Random two-phase state, free-slip z walls, free-slip x and/or y walls, gravity with
+    components along every axis, ragged 33x10x9 lattice, 40 steps."""
+    shape = (9, 10, 33)
+    params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.03, nu_b=0.06, sigma=0.003, g=(2e-5, -3e-5, 4e-5))
+    gpu, ref = pair(lb, shape, params, bc=(1, 1) + walls)
+    fields = workloads.random_two_phase_fields(shape, 13, 1.0, 0.5, u_amp=0.03)
+    gpu.init_fields(*fields)
+    ref.init_fields(*fields)
+    run_both(gpu, ref, 40)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL, e.max()
+
+
+def test_side_walls_fp16_storage_parity(lb):
+    cfg = workloads.scaled_jet("jet96", 36, 34, 40, D=10)
+    params = dict(cfg["params"], storage=1)
+    shape = (40, 34, 36)
+    gpu, ref = pair(lb, shape, params, bc=tuple(cfg["bc"]) + (1, 1))
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 50)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < TOL16, e.max()
