@@ -272,6 +272,7 @@ def main():
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--error-steps", type=int, default=500)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-paper-workload", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint leg (lb_adjoint against lb_step on the 64x64x256 jet)")
     ap.add_argument("--adjoint-steps", type=int, default=500)
@@ -351,7 +352,7 @@ def main():
 
     # ---- the same workload with the paper's free-slip side walls (Section IV.A) in place of
     #      periodic x and y: throughput only
-    sw = lb.Lattice(cfg["grid"], cfg["params"], bc=tuple(cfg["bc"]) + (1, 1))
+    sw = lb.Lattice(cfg["grid"], cfg["params"], bc=tuple(cfg["bc"])[:2] + (1, 1))
     sw.init_jet() if cfg["init"]["kind"] == "jet" else sw.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
     sw.step(args.warmup)
     sw_steps = min(args.steps, 500)
@@ -366,6 +367,30 @@ def main():
                   "ms_per_step": sw_ms / sw_steps, "boundaries": "free-slip walls at x and y (Section IV.A)"}
     sw.close()
     del sw
+
+    # ---- the paper's own workload: UT Case 1 (240x240x1200 melt jet, free-slip side walls,
+    #      gravity), whose 20 000 iterations the paper reports as about 32 hours
+    paper = None
+    if world == 1 and not args.no_paper_workload:
+        ucfg = workloads.CONFIGS["ut1"]
+        un = int(np.prod(ucfg["grid"]))
+        ut = lb.Lattice(ucfg["grid"], ucfg["params"], bc=ucfg["bc"])
+        ut.init_jet()
+        ut.step(args.warmup)
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        u0.record(ut.stream)
+        ut.step(200)
+        u1.record(ut.stream)
+        torch.cuda.synchronize()
+        ums = u0.elapsed_time(u1)
+        paper = {"workload": ucfg["text"], "nodes": un, "steps": 200, "value": un * 200 / (ums * 1e-3) / 1e6,
+                 "unit": "MLUPS", "ms_per_step": ums / 200, "hours_for_20000_steps": ums / 200 * 20000 / 3.6e6,
+                 "paper": "about 32 h for 20 000 iterations on unstated hardware: 12 MLUPS for the 69.12 M nodes "
+                          "of this lattice (1.2 MLUPS for the 6.912 M nodes the text prints)"}
+        ut.close()
+        del ut
+        torch.cuda.empty_cache()
 
     # ---- fragment analysis of the state the timed steps reached (lb_fragments, Section IV.B)
     fr_t0 = time.perf_counter()
@@ -444,7 +469,8 @@ def main():
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
                 "fp16_storage": fp16, "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None,
-                "adjoint": adjoint, "fragments": fragments, "side_walls": side_walls}
+                "adjoint": adjoint, "fragments": fragments, "side_walls": side_walls,
+                "paper_workload": paper}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -7,6 +7,24 @@
 
 namespace lbcm {
 
+// Direction i of the gather: the boundary planes at z = 0 / z = N, else the pull from the
+// source node, reading the populations of direction j there.
+template <int S>
+__device__ __forceinline__ void gather_one(const StepArgs &a, const Nbr &nb, int i, bool lo, bool slip_hi, size_t P,
+                                           float2 own, int j, float (&fr)[27], float (&fb)[27]) {
+    if (cz(i) == 1 && lo) {
+        fr[i] = a.zin[zrank(i) * P + nb.pxy];
+        fb[i] = a.zin[(9 + zrank(i)) * P + nb.pxy];
+    } else if (cz(i) == -1 && slip_hi) {
+        fr[i] = a.zout[zrank(i) * P + nb.pxy];
+        fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
+    } else {
+        const float2 v = load_pop<S>(a, i, nb.src(i), own, j);
+        fr[i] = v.x;
+        fb[i] = v.y;
+    }
+}
+
 // Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
 template <int S, bool W>
@@ -26,21 +44,17 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
         return;
     }
     const float2 own = reader_shift<S>(a, nb.n);
+    // W: the lattice has side walls, where a pull reflects (the direction leaving the source is
+    // nb.pulled(i), selected at run time).  Only warps holding a wall node take that path; the
+    // others, and lattices without side walls, index every plane at compile time.
+    bool reflect = false;
+    if constexpr (W) reflect = __any_sync(__activemask(), nb.wxl || nb.wxh || nb.wyl || nb.wyh);
+    if (reflect) {
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        if (cz(i) == 1 && lo) {
-            fr[i] = a.zin[zrank(i) * P + nb.pxy];
-            fb[i] = a.zin[(9 + zrank(i)) * P + nb.pxy];
-        } else if (cz(i) == -1 && slip_hi) {
-            fr[i] = a.zout[zrank(i) * P + nb.pxy];
-            fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
-        } else {
-            // W: the lattice has side walls, where the pull reflects (the direction leaving the
-            // source is nb.pulled(i)); without them the plane index is a compile-time constant
-            const float2 v = load_pop<S>(a, i, nb.src(i), own, W ? nb.pulled(i) : i);
-            fr[i] = v.x;
-            fb[i] = v.y;
-        }
+        for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, nb.pulled(i), fr, fb);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, i, fr, fb);
     }
 }
 

@@ -64,6 +64,26 @@ CONFIGS = {
         dict(**jet_parameters(D=48, u=0.05, gamma=8.0, eta=0.1, Re=1e6, We=5000), noise_amp=0.01),
         dict(kind="jet"), 1000,
         "atomisation jet 384x384x1536 (226M nodes), D=48, u=0.05, gamma=8, eta=0.1, Re=1e6, We=5000, 1% noise"),
+    # The paper's own runs (Section IV): UT melt jets (Table of UT conditions, Cases 1-4) on the
+    # 8D x 8D x 40D lattice with D = 30, u_j0 = 0.05, rho_j = 1, rho_c = 1/gamma, free-slip side
+    # walls, gravity on the dispersed phase, no inlet disturbance.
+    **{f"ut{k}": _cfg(
+        f"ut{k}", (240, 240, 1200), (BC_INLET, BC_CONVECTIVE, BC_FREESLIP, BC_FREESLIP),
+        dict(**jet_parameters(D=30, u=0.05, gamma=8.3, eta=0.54, Re=Re, We=We, Fr=Fr)),
+        dict(kind="jet"), 20000,
+        f"UT Case {k}: melt jet 240x240x1200, D=30, u=0.05, gamma=8.3, eta=0.54, Re={Re:g}, We={We:g}, Fr={Fr:g}, "
+        "free-slip side walls, gravity +z")
+       for k, (Re, We, Fr) in enumerate([(6.1e4, 230, 64), (6.5e4, 180, 24), (1.1e5, 330, 20), (1.5e5, 450, 16)], 1)},
+    # FT T1, coarse grid: the lattice parameters printed with its figure (sigma = 1.6e-5 gives
+    # We = u^2 D / sigma = 4.7e3, not the 9.3e4 of its table of conditions; the printed lattice
+    # values are used).
+    "ft_coarse": _cfg(
+        "ft_coarse", (240, 240, 600), (BC_INLET, BC_CONVECTIVE, BC_FREESLIP, BC_FREESLIP),
+        dict(rho_r0=1.0, rho_b0=0.099, nu_r=1.4e-6, nu_b=9.9e-7, sigma=1.6e-5, g=(0.0, 0.0, 4.1e-7),
+             u_in=0.05, d_in=30.0),
+        dict(kind="jet"), 20000,
+        "FT T1 coarse: UO2 melt into sodium 240x240x600, D=30, u=0.05, gamma=10.1, eta=1.4, Re=1.1e6, "
+        "lattice sigma=1.6e-5, g=4.1e-7, free-slip side walls"),
 }
 
 
