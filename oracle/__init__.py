@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("s3", C.c_double), ("s4", C.c_double), ("s5", C.c_double), ("s6", C.c_double),
                 ("u_in", C.c_double), ("d_in", C.c_double), ("noise_amp", C.c_double),
                 ("seed", C.c_uint64), ("eps_grad", C.c_double), ("alpha_b", C.c_double),
-                ("fourier", C.c_double * 16)]
+                ("fourier", C.c_double * 16), ("alpha_mix", C.c_int32)]
 
 
 _Z = C.c_double * 2  # double _Complex: (real, imaginary)
@@ -52,8 +52,8 @@ _Z = C.c_double * 2  # double _Complex: (real, imaginary)
 
 class CSParams(C.Structure):
     """orc_params of the complex-step build: every real field complex."""
-    _fields_ = [(name, (_Z * ct._length_) if hasattr(ct, "_length_") else _Z) if ct is not C.c_uint64 else (name, ct)
-                for name, ct in Params._fields_]
+    _fields_ = [(name, (_Z * ct._length_) if hasattr(ct, "_length_") else _Z)
+                if ct not in (C.c_uint64, C.c_int32) else (name, ct) for name, ct in Params._fields_]
 
 
 def build(force: bool = False) -> str:
@@ -223,6 +223,7 @@ def make_params(d: dict) -> Params:
     fr = list(d.get("fourier", ())) + [0.0] * 16
     for m in range(16):
         p.fourier[m] = fr[m]
+    p.alpha_mix = int(d.get("alpha_mix", 0))
     return p
 
 
@@ -326,7 +327,7 @@ def _cs_params(p: dict, dp: dict, h: float) -> CSParams:
     out = CSParams()
     for name, ct in Params._fields_:
         v = getattr(base, name)
-        if ct is C.c_uint64:
+        if ct in (C.c_uint64, C.c_int32):
             setattr(out, name, v)
             continue
         d = dp.get(name, 0.0)

@@ -59,6 +59,10 @@
  *       then act on the reflected direction at the reflected source column.  Gradient ghosts
  *       beyond a side wall mirror the wall layer; fragments and the area objective do not wrap
  *       across it.
+ *   R15 Alternative to the printed alpha-bar interpolation (alpha_mix = 1): weights rho_k / rho
+ *       (mass fractions) instead of (1 +- phi)/2 (volume fractions), which makes the equation
+ *       of state additive, rho c_s^2(alpha-bar) = rho_r c_r^2 + rho_b c_b^2.  Not the paper's
+ *       formula; the reading under which its density-ratio droplets stay stable.
  *   R13 Fragments (Section IV.B, diameter procedure): the jet region is phi > 0 of the state's
  *       colour densities; fragments are its connected components with face (6) or full (26)
  *       neighbourhoods, wrapping where the lattice is periodic; V = node count, d = (6V/pi)^(1/3);
@@ -138,6 +142,7 @@ typedef struct {
     real eps_grad;             /* |grad phi| regulariser (R3) */
     real alpha_b;              /* 8/27 in the paper */
     real fourier[16];          /* inlet profile: a_1, b_1, ..., a_8, b_8 (R11) */
+    int32_t alpha_mix;           /* 0: alpha-bar by (1 +- phi)/2 as printed; 1: by mass fraction (R15) */
 } orc_params;
 
 static double weight(int i) {
@@ -621,7 +626,8 @@ int orc_step(const orc_grid *g, const orc_params *p, const real *S_in, const rea
                     u[d] = (s + 0.5 * F[d]) / rho;
                 }
                 /* mixture parameters */
-                real alpha_bar = 0.5 * (1.0 + phi) * alpha_r + 0.5 * (1.0 - phi) * alpha_b;
+                real alpha_bar = p->alpha_mix ? (rho_r * alpha_r + rho_b * alpha_b) / rho
+                                              : 0.5 * (1.0 + phi) * alpha_r + 0.5 * (1.0 - phi) * alpha_b;
                 real nu_bar = 1.0 / (0.5 * (1.0 + phi) / p->nu_r + 0.5 * (1.0 - phi) / p->nu_b);
                 real s2nu = 1.0 / (3.0 * nu_bar + 0.5); /* Eq. (shear) with c = dt = 1 */
                 real tau = 1.0 / s2nu;
@@ -707,7 +713,8 @@ void orc_fields(const orc_grid *g, const orc_params *p, const real *S, real *rho
         real rho = a + b;
         real ph = (a / p->rho_r0 - b / p->rho_b0) / (a / p->rho_r0 + b / p->rho_b0);
         for (int d = 0; d < 3; ++d) u[d * nn + n] = (j[d] - 0.5 * (rho - p->rho_b0) * p->g[d]) / rho;
-        real alpha_bar = 0.5 * (1.0 + ph) * alpha_r + 0.5 * (1.0 - ph) * p->alpha_b;
+        real alpha_bar = p->alpha_mix ? (a * alpha_r + b * p->alpha_b) / rho
+                                      : 0.5 * (1.0 + ph) * alpha_r + 0.5 * (1.0 - ph) * p->alpha_b;
         rho_r[n] = a;
         rho_b[n] = b;
         phi[n] = ph;

@@ -554,3 +554,50 @@ def test_closed_box_conserves_colour_mass_and_tangential_flow():
     S0 = uni.S.copy()
     uni.step(5)
     assert np.abs(uni.S - S0).max() < 1e-15
+
+
+# ------------------------------------------------- alpha-bar by mass fraction (R15)
+def test_mass_fraction_alpha_makes_the_pressure_additive():
+    """With alpha_mix = 1 the equation of state is rho c_s^2(alpha-bar) = rho_r c_r^2 + rho_b c_b^2,
+    c_k^2 = 9 (1 - alpha_k) / 19; the printed (1 +- phi)/2 interpolation is not additive."""
+    shape = (5, 6, 7)
+    gamma = 20.0
+    rr, rb, u = (np.asarray(v, np.float64) for v in workloads.random_two_phase_fields(shape, 2, gamma, 1.0, u_amp=0.0))
+    ar = 1 - (1 - 8 / 27) / gamma
+    add = rr * 9 * (1 - ar) / 19 + rb * 9 * (1 - 8 / 27) / 19
+    for mix, expect_equal in ((1, True), (0, False)):
+        lat = make_lattice(shape, rho_r0=gamma, rho_b0=1.0, alpha_mix=mix)
+        lat.init_fields(rr, rb, u)
+        pr = lat.fields()["p"]
+        assert (np.abs(pr - add).max() < 1e-13 * add.max()) == expect_equal
+
+
+def test_tanh_droplet_start_pressure_under_both_readings():
+    """The Section III start with rho_r0 = gamma rho_b0: uniform pressure rho_b0/3 under R15; under
+    the printed interpolation the interface midpoint (phi = 0) carries (gamma+1)^2/(4 gamma) of it."""
+    gamma, n = 100.0, 24
+    for mix in (1, 0):
+        lat = make_lattice((n, n, n), rho_r0=gamma, rho_b0=1.0, alpha_mix=mix)
+        lat.init_droplet(6.0, 4.0)
+        F = lat.fields()
+        if mix:
+            assert np.abs(F["p"] - 1 / 3).max() < 1e-13
+        else:
+            # at phi = 0 exactly: rho = (gamma + 1) rho_b0 / 2, alpha-bar = (alpha_r + alpha_b) / 2
+            ar = 1 - (1 - 8 / 27) / gamma
+            p_mid = (gamma + 1) / 2 * 9 * (1 - (ar + 8 / 27) / 2) / 19
+            assert abs(p_mid * 3 - (gamma + 1) ** 2 / (4 * gamma)) < 1e-12
+            assert F["p"].max() > 0.9 * p_mid
+
+
+def test_readings_coincide_at_equal_densities():
+    """gamma = 1: alpha_r = alpha_b, so both interpolations give the same step (to rounding)."""
+    shape = (6, 5, 7)
+    fields = workloads.random_two_phase_fields(shape, 8, 1.0, 1.0, u_amp=0.03)
+    out = []
+    for mix in (0, 1):
+        lat = make_lattice(shape, nu_b=0.05, sigma=0.003, alpha_mix=mix)
+        lat.init_fields(*fields)
+        lat.step(3)
+        out.append(lat.S)
+    assert np.abs(out[0] - out[1]).max() < 1e-15
