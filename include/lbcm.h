@@ -96,6 +96,10 @@ typedef struct {
                                theta the polar angle of the inlet column about the disc centre;
                                stored a_1, b_1, ..., a_8, b_8 (not in the paper: the parameters the
                                adjoint differentiates); all 0 = the paper's uniform inlet */
+    int32_t alpha_mix;      /* alpha-bar of Eqs. (varphi_ik, press): 0 = the printed interpolation by
+                               (1 +- phi)/2; 1 = by mass fractions rho_k/rho, which makes the
+                               equation of state additive over the colours (the reading under
+                               which the paper's high-density-ratio droplets stay stable) */
 } lb_params;
 
 /* Fills *p with the paper's defaults: rho_r0 = rho_b0 = 1, nu = 1/6, sigma = 0, beta = 0.7,

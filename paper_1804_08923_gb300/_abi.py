@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("s4", C.c_double), ("s5", C.c_double), ("s6", C.c_double),
                 ("u_in", C.c_double), ("d_in", C.c_double), ("noise_amp", C.c_double),
                 ("seed", C.c_uint64), ("eps_grad", C.c_double), ("storage", C.c_int32),
-                ("check_every", C.c_int32), ("fourier", C.c_double * 16)]
+                ("check_every", C.c_int32), ("fourier", C.c_double * 16), ("alpha_mix", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -126,7 +126,7 @@ def make_params(d: dict) -> Params:
             vals = list(v) + [0.0] * 16
             for m in range(16):
                 p.fourier[m] = float(vals[m])
-        elif k in ("seed", "storage", "check_every"):
+        elif k in ("seed", "storage", "check_every", "alpha_mix"):
             setattr(p, k, int(v))
         elif k in dict(Params._fields_):
             setattr(p, k, float(v))

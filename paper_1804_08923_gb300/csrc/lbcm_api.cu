@@ -93,6 +93,7 @@ lb_status validate(const lb_grid *g, const lb_params *p) {
     if (p->storage != LB_STORE_FP32 && p->storage != LB_STORE_FP16)
         return fail(LB_EINVAL, "storage must be LB_STORE_FP32 or LB_STORE_FP16");
     if (p->check_every < 0) return fail(LB_EINVAL, "check_every must be >= 0");
+    if (p->alpha_mix != 0 && p->alpha_mix != 1) return fail(LB_EINVAL, "alpha_mix must be 0 or 1");
     if (g->bc_zlo == LB_BC_INLET) {
         if (!(p->d_in >= 0) || !std::isfinite(p->d_in) || !std::isfinite(p->u_in) || !std::isfinite(p->noise_amp))
             return fail(LB_EINVAL, "inlet parameters must be finite, d_in >= 0");
@@ -257,7 +258,8 @@ __global__ void fields_kernel(StepArgs sa, FieldOut fo, float gx, float gy, floa
         if (fo.o[LB_FIELD_UY]) fo.o[LB_FIELD_UY][n] = (jy - 0.5f * fc * gy) / rho;
         if (fo.o[LB_FIELD_UZ]) fo.o[LB_FIELD_UZ][n] = (jz - 0.5f * fc * gz) / rho;
         if (fo.o[LB_FIELD_P]) {
-            const float alpha = 0.5f * (1.0f + phi) * sa.alpha_r + 0.5f * (1.0f - phi) * sa.alpha_b;
+            const float alpha = sa.alpha_mix ? (rr * sa.alpha_r + rb * sa.alpha_b) / rho
+                                             : 0.5f * (1.0f + phi) * sa.alpha_r + 0.5f * (1.0f - phi) * sa.alpha_b;
             fo.o[LB_FIELD_P][n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (press)
         }
     }
@@ -431,6 +433,7 @@ StepArgs make_args(const lb_ctx *c) {
     a.inv_rho_r0 = (float)(1.0 / p.rho_r0); a.inv_rho_b0 = (float)(1.0 / p.rho_b0);
     const double alpha_b = 8.0 / 27.0;
     a.alpha_b = (float)alpha_b;
+    a.alpha_mix = p.alpha_mix;
     a.alpha_r = (float)(1.0 - (1.0 - alpha_b) / (p.rho_r0 / p.rho_b0));
     a.inv_nu_r = (float)(1.0 / p.nu_r); a.inv_nu_b = (float)(1.0 / p.nu_b);
     a.sigma = (float)p.sigma; a.beta = (float)p.beta;

@@ -127,6 +127,12 @@ __device__ __forceinline__ void inlet_velocity(float u_in, float noise_amp, cons
     v.uz = u_in * prof;
 }
 
+// alpha-bar: (1 + phi)/2 alpha_r + (1 - phi)/2 alpha_b as printed, or by mass fractions.
+__device__ __forceinline__ float alpha_bar(int mix, float rho_r, float rho_b, float inv_rho, float hp, float hm,
+                                           float alpha_r, float alpha_b) {
+    return mix ? (rho_r * alpha_r + rho_b * alpha_b) * inv_rho : hp * alpha_r + hm * alpha_b;
+}
+
 // Order parameter of Eq. (order) from the colour densities (1/rho_k0 given).
 __device__ __forceinline__ float order_parameter(float rho_r, float rho_b, float inv_rho_r0, float inv_rho_b0) {
     const float A = rho_r * inv_rho_r0, B = rho_b * inv_rho_b0;
@@ -158,6 +164,7 @@ struct StepArgs {
     long long NN, plane;                // nodes, nx*ny
     int nx, ny, nz, bc_zlo, bc_zhi;
     int wall_x, wall_y;                 // free-slip side walls (else periodic)
+    int alpha_mix;                      // alpha-bar by (1 +- phi)/2 (0) or by mass fraction (1)
     float rho_r0, rho_b0, inv_rho_r0, inv_rho_b0;
     float alpha_r, alpha_b, inv_nu_r, inv_nu_b;
     float sigma, beta, eps2;

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     // order parameter (Eq. order) and mixture parameters
     const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
-    const float alpha = hp * a.alpha_r + hm * a.alpha_b;
+    const float alpha = alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
     const float one_m_alpha = 1.0f - alpha;
     const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);  // harmonic mean
     const float tau = 3.0f * nu + 0.5f;                           // Eq. (shear): 1/s_2nu
@@ -328,7 +328,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     const float ux = jFx * inv_rho, uy = jFy * inv_rho, uz = jFz * inv_rho;
     const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
-    const float alpha = hp * a.alpha_r + hm * a.alpha_b;
+    const float alpha = alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
     const float oma = 1.0f - alpha;
     const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);
     const float tau = 3.0f * nu + 0.5f;

@@ -279,3 +279,18 @@ def test_adjoint_state_with_side_walls(lb):
                                       "area", (1e-3,), dS=dS)
     ad = float((lS * dS).sum())
     assert abs(ad - tan) < TOL * abs(tan), (ad, tan)
+
+
+def test_adjoint_with_mass_fraction_alpha(lb):
+    """Reading R15 changes d alpha-bar / d rho_k: gradients at density ratio 8 against the oracle's
+    tangent."""
+    grid, bc, params = jet_case()
+    params = dict(params, rho_b0=1 / 8.0, alpha_mix=1)
+    T = 8
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    J, g = lat.adjoint(T, "area", (1e-3,))
+    names = ("u_in", "sigma", "nu_r", "nu_b", "a2")
+    g_tan = tangent_gradient(grid, bc, params, lambda r: r.init_jet(), T, "area", (1e-3,), names)
+    got = np.array([g[NAMES.index(n)] for n in names])
+    assert np.abs(got - g_tan).max() / np.abs(g_tan).max() < TOL, (got, g_tan)

@@ -388,3 +388,23 @@ def test_side_walls_fp16_storage_parity(lb):
     run_both(gpu, ref, 50)
     e = norm_err(gpu, ref, params)
     assert e.max() < TOL16, e.max()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_mass_fraction_alpha_parity(lb, storage):
+    """Reading R15 (alpha-bar by mass fraction) at density ratio 20 with gravity: random
+    two-phase state, 30 steps."""
+    shape = (10, 9, 34)
+    params = dict(rho_r0=20.0, rho_b0=1.0, nu_r=0.03, nu_b=0.06, sigma=0.003, g=(0.0, 1e-5, -2e-5), alpha_mix=1,
+                  storage=storage)
+    gpu, ref = pair(lb, shape, params)
+    fields = workloads.random_two_phase_fields(shape, 17, 20.0, 1.0, u_amp=0.02)
+    gpu.init_fields(*fields)
+    ref.init_fields(*fields)
+    run_both(gpu, ref, 30)
+    e = norm_err(gpu, ref, params)
+    assert e.max() < (TOL if storage == 0 else TOL16), e.max()
+    F = gpu.fields(device=False)
+    ar = 1 - (1 - 8 / 27) / 20.0
+    add = F["rho_r"] * 9 * (1 - ar) / 19 + F["rho_b"] / 3
+    assert np.abs(F["p"] - add).max() < 1e-5 * add.max()  # additive equation of state
