@@ -145,7 +145,7 @@ __device__ __forceinline__ void m3uu(const RawMom &M, float ux, float uy, float 
 // proportional to w_i (varphi_i(alpha) = 27/19 (1 - alpha) w_i, the Phi coefficient 9 w_i and
 // B_i = w_i for i >= 1), so it is a combination of the weighted raw moments of a and b up to
 // third order.  Only the recolouring's 1/|c_i| is not separable and is summed directly.
-template <bool kForce>
+template <bool kForce, bool W>
 __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArgs &g, int x, int y, int z,
                                                  float (&part)[3], float2 *L_s, float2 *R_s) {
     const Nbr nb(a, x, y, z);
@@ -435,7 +435,9 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     lrr += lrho;
     lrb += lrho;
 
-    // ---- outputs: lambda_f_i^k = lambda_j . c_i + c_i Lambda_P c_i + lambda_rho_k, pushed
+    // ---- outputs: lambda_f_i^k = lambda_j . c_i + c_i Lambda_P c_i + lambda_rho_k, pushed to the
+    // slot the pull read (with side walls, W: the reflected direction, selected at run time)
+#define PULLED(i) (W ? nb.pulled(i) : (i))
     g.lga[nb.n] = make_float4(lgpx, lgpy, lgpz, lgrx);
     g.lgb[nb.n] = make_float2(lgry, lgrz);
     const size_t P = (size_t)a.plane;
@@ -450,11 +452,11 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
             // slots the plain pulls would have read are read by nobody
             g.lc[(size_t)i * P + nb.pxy] = o.x;
             g.lc[(size_t)(27 + i) * P + nb.pxy] = o.y;
-            if (cz(i) >= 0) g.lp_out[(size_t)nb.pulled(i) * a.NN + nb.src(i)] = make_float2(0.0f, 0.0f);
+            if (cz(i) >= 0) g.lp_out[(size_t)PULLED(i) * a.NN + nb.src(i)] = make_float2(0.0f, 0.0f);
             if (cz(i) == 1) g.lp_out[(size_t)i * a.NN + nb.n] = make_float2(0.0f, 0.0f);
         } else if (!pz && z == 0 && cz(i) == 1) {
             const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];  // source column (offsets, reflected)
-            const size_t slot = (size_t)mirror_z(nb.pulled(i)) * a.NN + ys + xs;
+            const size_t slot = (size_t)mirror_z(PULLED(i)) * a.NN + ys + xs;
             if (a.bc_zlo == BC_INLET && a.disc[ys + xs]) {
                 g.li[(size_t)zrank(i) * P + nb.pxy] = o.x;
                 g.lp_out[slot] = make_float2(0.0f, 0.0f);
@@ -463,17 +465,18 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
             }
         } else if (!pz && z == N && cz(i) == -1 && a.bc_zhi == BC_FREESLIP) {
             const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];
-            g.lp_out[(size_t)mirror_z(nb.pulled(i)) * a.NN + (size_t)N * P + ys + xs] = o;
+            g.lp_out[(size_t)mirror_z(PULLED(i)) * a.NN + (size_t)N * P + ys + xs] = o;
         } else {
-            g.lp_out[(size_t)nb.pulled(i) * a.NN + nb.src(i)] = o;
+            g.lp_out[(size_t)PULLED(i) * a.NN + nb.src(i)] = o;
         }
     }
+#undef PULLED
 }
 
 #ifndef LBCM_ADJ_MIN_BLOCKS
 #define LBCM_ADJ_MIN_BLOCKS 3
 #endif
-template <bool kForce>
+template <bool kForce, bool W>
 __global__ void __launch_bounds__(128, LBCM_ADJ_MIN_BLOCKS) adj_collide_kernel(StepArgs a, AdjArgs g) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(128, LBCM_ADJ_MIN_BLOCKS) adj_collide_kernel(S
     extern __shared__ float2 adj_dsm[];  // [2][27][128]: pushed and deferred lambda S(n+1)
     const int t = threadIdx.y * 32 + threadIdx.x;
     float part[3] = {0.0f, 0.0f, 0.0f};
-    if (x < a.nx && y < a.ny) adj_collide_node<kForce>(a, g, x, y, z, part, adj_dsm + t, adj_dsm + 27 * 128 + t);
+    if (x < a.nx && y < a.ny) adj_collide_node<kForce, W>(a, g, x, y, z, part, adj_dsm + t, adj_dsm + 27 * 128 + t);
     block_accumulate<3>(part, g.acc_coll, block_id());
 }
 
@@ -490,6 +493,7 @@ __global__ void __launch_bounds__(128, LBCM_ADJ_MIN_BLOCKS) adj_collide_kernel(S
 // node x on z = 0 (z = N) reads y through the mirror ghost with c_j's z component flipped,
 // except inside the inlet disc, where the ghost is a constant.  Same for rho.  Then
 // lambda_rho_k(y) = lambda_phi dphi/drho_k + lambda_rho.
+template <bool W>
 __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -508,8 +512,8 @@ __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g)
         // beyond a wall the reader is on this layer and reached y through its mirror ghost
         // with that component of c reversed
         const float czj = (below || above) ? -(float)cz(j) : (float)cz(j);
-        const float cxj = nb.fx(j) ? -(float)cx(j) : (float)cx(j);
-        const float cyj = nb.fy(j) ? -(float)cy(j) : (float)cy(j);
+        const float cxj = W && nb.fx(j) ? -(float)cx(j) : (float)cx(j);
+        const float cyj = W && nb.fy(j) ? -(float)cy(j) : (float)cy(j);
         const int src = nb.src(j);  // clamped onto the wall layer: the mirrored reader
         const float4 A = __ldg(g.lga + src);
         const float2 B = __ldg(g.lgb + src);
@@ -773,17 +777,28 @@ constexpr int kAdjSmem = 2 * 27 * 128 * (int)sizeof(float2);
 
 cudaError_t launch_adjoint_step(const StepArgs &a, const AdjArgs &g, cudaStream_t s, long long *launches) {
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
+    const bool walls = a.wall_x || a.wall_y;
     static bool attr = false;  // the dynamic shared memory exceeds the 48 KB default
     if (!attr) {
-        cudaFuncSetAttribute(adj_collide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
-        cudaFuncSetAttribute(adj_collide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        cudaFuncSetAttribute(adj_collide_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        cudaFuncSetAttribute(adj_collide_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        cudaFuncSetAttribute(adj_collide_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
+        cudaFuncSetAttribute(adj_collide_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem);
         attr = true;
     }
-    if (force)
-        adj_collide_kernel<true><<<node_grid(a), node_block(), kAdjSmem, s>>>(a, g);
+    const dim3 gr = node_grid(a), bl = node_block();
+    if (force && walls)
+        adj_collide_kernel<true, true><<<gr, bl, kAdjSmem, s>>>(a, g);
+    else if (force)
+        adj_collide_kernel<true, false><<<gr, bl, kAdjSmem, s>>>(a, g);
+    else if (walls)
+        adj_collide_kernel<false, true><<<gr, bl, kAdjSmem, s>>>(a, g);
     else
-        adj_collide_kernel<false><<<node_grid(a), node_block(), kAdjSmem, s>>>(a, g);
-    adj_stencil_kernel<<<node_grid(a), node_block(), 0, s>>>(a, g);
+        adj_collide_kernel<false, false><<<gr, bl, kAdjSmem, s>>>(a, g);
+    if (walls)
+        adj_stencil_kernel<true><<<gr, bl, 0, s>>>(a, g);
+    else
+        adj_stencil_kernel<false><<<gr, bl, 0, s>>>(a, g);
     *launches += 2;
     if (a.bc_zlo == BC_INLET || a.bc_zhi == BC_CONVECTIVE) {
         adj_boundary_kernel<<<col_grid(a), col_block(), 0, s>>>(a, g);
@@ -809,7 +824,10 @@ cudaError_t launch_objective(const StepArgs &a, const AdjArgs &g, int objective,
         ao.phase = ph;
         const float eps = (float)args[0];
         obj_area_kernel<<<node_grid(a), node_block(), 0, s>>>(a, ph, g.lga, g.lgb, acc_obj, eps * eps);
-        adj_stencil_kernel<<<node_grid(a), node_block(), 0, s>>>(ao, o);
+        if (a.wall_x || a.wall_y)
+            adj_stencil_kernel<true><<<node_grid(a), node_block(), 0, s>>>(ao, o);
+        else
+            adj_stencil_kernel<false><<<node_grid(a), node_block(), 0, s>>>(ao, o);
         obj_fill_kernel<<<stride_grid(a.NN), 256, 0, s>>>(a.NN, lr_obj, g.lp_out, g.lr_out);
         adj_reduce_kernel<<<1, 1024, 0, s>>>(acc_obj, nblk, 1, 0, scalar);
         *launches += 4;
