@@ -638,13 +638,14 @@ __global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g
 // (phi, rho) of a post-collision state: rho_k = sum_i S_i^k.
 __global__ void __launch_bounds__(256) obj_fields_kernel(StepArgs a, float2 *ph) {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.NN; n += (long long)gridDim.x * blockDim.x) {
-        float rr = 0.0f, rb = 0.0f;
+        MassAcc mr, mb;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             const float2 v = load_pop<STORE_FP32>(a, i, (int)n, make_float2(0.0f, 0.0f));
-            rr += v.x;
-            rb += v.y;
+            mr.add(i, v.x);
+            mb.add(i, v.y);
         }
+        const float rr = mr.total(), rb = mb.total();
         ph[n] = make_float2(order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0), rr + rb);
     }
 }

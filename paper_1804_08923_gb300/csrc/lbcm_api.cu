@@ -202,7 +202,7 @@ __global__ void init_kernel(InitArgs ia, StepArgs sa) {
         init_fields_at(ia, n, rr, rb, ux, uy, uz);
         const Nbr nb = node_nbr(sa, n);
         const float usq = ux * ux + uy * uy + uz * uz;
-        float sr = 0.0f, sb = 0.0f;
+        MassAcc sr, sb;
         const bool top = nb.zo[1] == (ia.nz - 1) * (int)sa.plane;
         const long long h = nb.pxy, P = sa.plane;
 #pragma unroll
@@ -212,14 +212,14 @@ __global__ void init_kernel(InitArgs ia, StepArgs sa) {
             const float2 f = make_float2(rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw),
                                          rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw));
             const float2 d = store_pop<S>(sa, i, (int)n, f, dest_shift<S>(sa, nb, i));
-            sr += d.x;
-            sb += d.y;
+            sr.add(i, d.x);
+            sb.add(i, d.y);
             if (top) {
                 ia.hist[(long long)i * P + h] = d.x;
                 ia.hist[(long long)(27 + i) * P + h] = d.y;
             }
         }
-        const float2 f0 = make_float2(rr - sr, rb - sb);
+        const float2 f0 = make_float2(rr - sr.s, rb - sb.s);
         store_pop<S>(sa, 0, (int)n, f0, make_float2(0.0f, 0.0f));
         if (top) {
             ia.hist[h] = f0.x;
@@ -238,16 +238,18 @@ __global__ void fields_kernel(StepArgs sa, FieldOut fo, float gx, float gy, floa
     const long long NN = sa.NN;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
         const Nbr nb = node_nbr(sa, n);
-        float rr = 0.0f, rb = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+        MassAcc mr, mb;
+        float jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
             const float2 v = stored_pop<S>(sa, nb, i);
-            rr += v.x;
-            rb += v.y;
+            mr.add(i, v.x);
+            mb.add(i, v.y);
             if (cx(i) != 0) jx += cx(i) * (v.x + v.y);
             if (cy(i) != 0) jy += cy(i) * (v.x + v.y);
             if (cz(i) != 0) jz += cz(i) * (v.x + v.y);
         }
+        const float rr = mr.total(), rb = mb.total();
         const float rho = rr + rb;
         const float phi = order_parameter(rr, rb, sa.inv_rho_r0, sa.inv_rho_b0);
         const float fc = rho - sa.rho_b0;

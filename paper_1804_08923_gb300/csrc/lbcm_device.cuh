@@ -133,6 +133,28 @@ __device__ __forceinline__ float alpha_bar(int mix, float rho_r, float rho_b, fl
     return mix ? (rho_r * alpha_r + rho_b * alpha_b) * inv_rho : hp * alpha_r + hm * alpha_b;
 }
 
+// Sum of one colour's 27 populations of a node in one fixed association,
+//   f_0 + (((f_1 + f_2) + (f_3 + f_4)) + ... + (f_25 + f_26)),
+// the one the collision uses when it writes the rest population as the remainder rho_k - s of
+// the moving ones.  A reader that gathers the same moving values therefore gets rho_k back
+// (fl(fl(rho - s) + s) = rho up to a rounding tie), so a uniform state is an exact fixed point
+// of the FP32 step instead of drifting by an ulp of density now and then; a drift that, being
+// the same at every node, would not average out and, against the frozen convective plane,
+// would drive a spurious outflow velocity.  add(i, v) must be called in the order i = 0..26
+// (or 1..26 for the moving part s alone).
+struct MassAcc {
+    float f0 = 0.0f, odd = 0.0f, s = 0.0f;
+    __device__ __forceinline__ void add(int i, float v) {
+        if (i == 0)
+            f0 = v;
+        else if (i & 1)
+            odd = v;
+        else
+            s += odd + v;
+    }
+    __device__ __forceinline__ float total() const { return f0 + s; }
+};
+
 // Order parameter of Eq. (order) from the colour densities (1/rho_k0 given).
 __device__ __forceinline__ float order_parameter(float rho_r, float rho_b, float inv_rho_r0, float inv_rho_b0) {
     const float A = rho_r * inv_rho_r0, B = rho_b * inv_rho_b0;

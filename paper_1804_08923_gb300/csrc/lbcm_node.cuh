@@ -123,16 +123,19 @@ struct Moments {
 
 template <int S, bool W>
 __device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb, int z, Moments &m) {
-    float rho_r = 0.0f, rho_b = 0.0f, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float rho_r, rho_b, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
     {
         float fr[27], fb[27];
         gather<S, W>(a, nb, z, fr, fb);
+        MassAcc mr, mb;  // the phase-field kernel's association
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {  // same order as the phase-field kernel
-            rho_r += fr[i];
-            rho_b += fb[i];
+        for (int i = 0; i < 27; ++i) {
+            mr.add(i, fr[i]);
+            mb.add(i, fb[i]);
         }
+        rho_r = mr.total();
+        rho_b = mb.total();
         // opposite pairs (i, i+1): odd moments take the difference, even ones the sum
         sf = fr[0] + fb[0];
 #pragma unroll

@@ -134,12 +134,13 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     const Nbr nb(a, x, y, z);
     float fr[27], fb[27];
     gather<S, W>(a, nb, z, fr, fb);
-    float rr = 0.0f, rb = 0.0f;
+    MassAcc mr, mb;
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
-        rr += fr[i];
-        rb += fb[i];
+        mr.add(i, fr[i]);
+        mb.add(i, fb[i]);
     }
+    const float rr = mr.total(), rb = mb.total();
     const float ph = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
     if constexpr (S == STORE_FP32)
         a.phase[nb.n] = make_float2(ph, rr + rb);
@@ -177,16 +178,19 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
 
     // post-stream populations, colour-blind sum and densities (same order as K_A)
     float f[27];
-    float rho_r = 0.0f, rho_b = 0.0f;
+    float rho_r, rho_b;
     {
         float fr[27], fb[27];
         gather<S, W>(a, nb, z, fr, fb);
+        MassAcc mr, mb;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            rho_r += fr[i];
-            rho_b += fb[i];
+            mr.add(i, fr[i]);
+            mb.add(i, fb[i]);
             f[i] = fr[i] + fb[i];
         }
+        rho_r = mr.total();
+        rho_b = mb.total();
     }
 
     float gpx, gpy, gpz, grx, gry, grz;
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;  // beta rho_r rho_b / (rho |g|)
     const float pert = Acoef * inv_gm;
     const int n = nb.n;
-    float sum_r = 0.0f, sum_b = 0.0f;
+    MassAcc sum_r, sum_b;  // moving populations written (as read back), per colour
 #pragma unroll
     for (int i = 1; i < 27; ++i) {  // the rest direction is the per-colour remainder below
         const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
@@ -300,11 +304,11 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
         const float seg = seg0 * varphi(i, alpha, one_m_alpha) * cgp * inv_cnorm(i);
         const float2 d = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fs, seg), fmaf(frac_b, fs, -seg)),
                                       dest_shift<S>(a, nb, i));
-        sum_r += d.x;
-        sum_b += d.y;
+        sum_r.add(i, d.x);
+        sum_b.add(i, d.y);
     }
     // rest direction as the per-colour remainder (see collide_from_moments)
-    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(0.0f, 0.0f));
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r.s, rho_b - sum_b.s), make_float2(0.0f, 0.0f));
 }
 
 
@@ -403,7 +407,8 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     const float pert = Acoef * inv_gm;
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
-    float sum_r = 0.0f, sum_b = 0.0f;  // moving populations written (as read back), per colour
+    // moving populations written (as read back), per colour, summed as MassAcc sums them
+    float sum_r = 0.0f, sum_b = 0.0f;
     // opposite pairs (i, i+1), c_{i+1} = -c_i: c.u, c.grad rho and c.grad phi change sign;
     // f^e splits into an even part (rest weight, quadratic terms, Phi) and an odd part
     // (linear and cubic terms), the perturbation is even and the recolouring flux odd.
@@ -441,7 +446,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     // (sum_i f_i^k* = rho_k), so the rest population is that mass minus the moving ones as
     // they will be read back; this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32
     // rounding of the lattice constants and any storage rounding from drifting the colour
-    // masses step after step.
+    // masses step after step (the pairwise sum above is MassAcc's association).
     store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(0.0f, 0.0f));
 }
 

@@ -408,3 +408,24 @@ def test_mass_fraction_alpha_parity(lb, storage):
     ar = 1 - (1 - 8 / 27) / 20.0
     add = F["rho_r"] * 9 * (1 - ar) / 19 + F["rho_b"] / 3
     assert np.abs(F["p"] - add).max() < 1e-5 * add.max()  # additive equation of state
+
+
+@pytest.mark.parametrize("storage,bc", [(0, (1, 3)), (1, (1, 3)), (0, (1, 3, 1, 1)), (0, (0, 0))])
+def test_uniform_rest_state_is_a_fixed_point(lb, storage, bc):
+    """A uniform resting mixture (gamma = 1.5, the jet's ambient ratio) must stay exactly at rest:
+    after the first step the state repeats bit for bit, so the interior cannot drift away from
+    a frozen convective plane and set up a spurious outflow velocity."""
+    shape = (16, 12, 40)
+    params = dict(rho_r0=1.0, rho_b0=2 / 3, nu_r=4e-4, nu_b=4e-4, sigma=4e-4, storage=storage)
+    nz, ny, nx = shape
+    gpu = lb.Lattice((nx, ny, nz), params, bc=bc)
+    for rr, rb in ((0.0, 2 / 3), (0.3, 0.4), (1.0, 0.0)):
+        gpu.init_fields(np.full(shape, rr, np.float32), np.full(shape, rb, np.float32), np.zeros((3,) + shape, np.float32))
+        gpu.step(1)
+        s1 = gpu.populations(device=False).copy()
+        gpu.step(40)
+        assert np.array_equal(gpu.populations(device=False), s1)
+        F = gpu.fields(device=False)
+        for k in ("ux", "uy", "uz"):
+            assert not F[k].any()
+        assert np.unique(F["rho_r"]).size == 1 and np.unique(F["rho_b"]).size == 1
