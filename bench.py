@@ -40,6 +40,15 @@ BYTES_KERNEL = {"collide_kernel": 440, "phase_field_kernel": 224}
 # step 32, write 112; phase field: read 112 + own previous phase 16, write 16.
 BYTES_STEP_FP16 = 112 + 112 + 16 + 16
 BYTES_KERNEL_FP16 = {"collide_kernel": 256, "phase_field_kernel": 144}
+# fitted FP16 encoding: the phase entry grows by the reader's FP8 odd fit (uint2, 8 B) to 24 B
+BYTES_STEP_FIT = 112 + 112 + 24 + 24
+BYTES_KERNEL_FIT = {"collide_kernel": 272, "phase_field_kernel": 160}
+STORAGE_TEXT = {
+    1: "moving populations as half-precision deviations from the reading node's rest equilibrium, "
+       "rest population FP32",
+    2: "moving populations as half-precision deviations from a prediction of the reading node "
+       "(rho_k (1 - alpha-bar) k_q plus an FP8 least-squares odd fit of its previous gather), rest "
+       "population FP32"}
 
 
 def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,), checkpoint=0):
@@ -77,12 +86,12 @@ def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,), 
             "precision": "FP32 kernels, FP64 parameter-gradient accumulation"}
 
 
-def fp16_error(lb, cfg, steps):
-    """FP16 against FP32 storage on the same workload after `steps` steps: relative L2 error
-    of the velocity and largest change of the order parameter."""
+def fp16_error(lb, cfg, steps, storage=1):
+    """FP16 (either encoding) against FP32 storage on the same workload after `steps` steps:
+    relative L2 error of the velocity and largest change of the order parameter."""
     import torch
     out = {}
-    lats = [lb.Lattice(cfg["grid"], dict(cfg["params"], storage=s), bc=cfg["bc"]) for s in (0, 1)]
+    lats = [lb.Lattice(cfg["grid"], dict(cfg["params"], storage=s), bc=cfg["bc"]) for s in (0, storage)]
     for l in lats:
         l.init_jet() if cfg["init"]["kind"] == "jet" else l.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
         l.step(steps)
@@ -418,13 +427,9 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": f"host fields -> lb_init, {args.steps} x lb_step, lb_fields -> host (pinned)"}
 
-    # ---- FP16-shifted storage on the same workload: throughput, roofline, and error vs FP32
-    fp16 = None
-    if not args.no_fp16:
-        lat.close()
-        del lat
-        torch.cuda.empty_cache()
-        h = lb.Lattice(cfg["grid"], dict(cfg["params"], storage=1), bc=cfg["bc"])
+    # ---- FP16 storage (both encodings) on the same workload: throughput, roofline, error vs FP32
+    def fp16_leg(storage, bytes_step, bytes_kernel, tag):
+        h = lb.Lattice(cfg["grid"], dict(cfg["params"], storage=storage), bc=cfg["bc"])
         h.init_jet() if cfg["init"]["kind"] == "jet" else h.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
         h.step(args.warmup)
         barrier()
@@ -442,17 +447,23 @@ def main():
         h.close()
         del h
         torch.cuda.empty_cache()
-        fp16 = {"value": nodes * args.steps * world / (ms16 * 1e-3) / 1e6, "unit": "MLUPS",
-                "ms_per_step": ms16 / args.steps, "storage": "moving populations as half-precision deviations "
-                "from the reading node's rest equilibrium, rest population FP32",
-                "bytes_per_node_algorithmic": BYTES_STEP_FP16,
-                "roofline": {"bound": "hbm", "kernel": "collide_kernel<fp16>",
-                             "achieved": BYTES_KERNEL_FP16["collide_kernel"] * nodes / (c_ms * 1e-3) / 1e9,
-                             "peak": peak, "unit": "GB/s",
-                             "frac": BYTES_KERNEL_FP16["collide_kernel"] * nodes / (c_ms * 1e-3) / 1e9 / peak,
-                             "algorithmic_bytes_per_node": BYTES_KERNEL_FP16["collide_kernel"], "traffic": None},
+        achieved = bytes_kernel["collide_kernel"] * nodes / (c_ms * 1e-3) / 1e9
+        return {"value": nodes * args.steps * world / (ms16 * 1e-3) / 1e6, "unit": "MLUPS",
+                "ms_per_step": ms16 / args.steps, "storage": STORAGE_TEXT[storage],
+                "bytes_per_node_algorithmic": bytes_step,
+                "roofline": {"bound": "hbm", "kernel": f"collide_kernel<{tag}>", "achieved": achieved,
+                             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "algorithmic_bytes_per_node": bytes_kernel["collide_kernel"], "traffic": None},
                 "kernels": {name: {"avg_ms": t / max(n, 1), "launches": n} for name, (t, n) in p16.items() if n},
-                "error_vs_fp32": fp16_error(lb, cfg, args.error_steps)}
+                "error_vs_fp32": fp16_error(lb, cfg, args.error_steps, storage)}
+
+    fp16 = fit = None
+    if not args.no_fp16:
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        fp16 = fp16_leg(1, BYTES_STEP_FP16, BYTES_KERNEL_FP16, "fp16")
+        fit = fp16_leg(2, BYTES_STEP_FIT, BYTES_KERNEL_FIT, "fp16_fit")
 
     if rank == 0:
         base = None
@@ -468,7 +479,7 @@ def main():
                 "bytes_per_node_algorithmic": BYTES_STEP,
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
-                "fp16_storage": fp16, "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None,
+                "fp16_storage": fp16, "fp16_fit_storage": fit, "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None,
                 "adjoint": adjoint, "fragments": fragments, "side_walls": side_walls,
                 "paper_workload": paper}
         print(json.dumps(line), flush=True)

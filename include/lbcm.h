@@ -70,12 +70,17 @@ typedef struct {
 } lb_grid;
 
 /* Population storage.  FP32: every population in single precision.  FP16: the 26 moving
- * populations of each colour are stored in half precision as deviations from the storing
- * node's rest equilibrium, h_i^k = f_i^k - rho_k varphi_i(alpha_k) (Eq. varphi_ik), the rest
- * population in single precision; it takes each colour's remainder of the moving ones as
- * they are read back, so per-node colour mass is kept to FP32 rounding.  Arithmetic is FP32
- * in both. */
-typedef enum { LB_STORE_FP32 = 0, LB_STORE_FP16 = 1 } lb_storage;
+ * populations of each colour are stored in half precision as deviations from the rest
+ * equilibrium of the node that will read them (pull streaming), h_i^k = f_i^k -
+ * rho_k varphi_i(alpha_k) (Eq. varphi_ik), the rest population in single precision; it takes
+ * each colour's remainder of the moving ones as they are read back, so per-node colour mass
+ * is kept to FP32 rounding.  FP16_FIT: the same layout, with the deviation taken from a
+ * prediction of the reading node, rho_k (1 - alpha-bar) k_q plus an odd part w_i c_i . v_k
+ * fitted to the populations it gathered in the step before (v_k kept in FP8 beside its
+ * densities, 8 more bytes per node and phase buffer); about 4x smaller deviations near
+ * interfaces, at some extra arithmetic.  Arithmetic is FP32 in all three.  The adjoint needs
+ * FP32. */
+typedef enum { LB_STORE_FP32 = 0, LB_STORE_FP16 = 1, LB_STORE_FP16_FIT = 2 } lb_storage;
 
 typedef struct {
     double rho_r0, rho_b0;  /* initial densities (Eq. order); gamma = rho_r0/rho_b0 >= 19/27 */
@@ -211,7 +216,8 @@ LB_API lb_status lb_profile_read(lb_ctx *ctx, double *ms, int64_t *launches, int
 /* Total number of kernels this context has launched since creation. */
 LB_API int64_t lb_kernel_launches(const lb_ctx *ctx);
 
-/* Replaces the parameters of an existing context (same grid and storage; the state is kept).
+/* Replaces the parameters of an existing context (same grid and storage; the state is kept;
+ * with FP16 storage rho_r0 and rho_b0 stay fixed once the context holds a state).
  * Validated like lb_create; LB_EINVAL leaves the context unchanged. */
 LB_API lb_status lb_set_params(lb_ctx *ctx, const lb_params *params);
 

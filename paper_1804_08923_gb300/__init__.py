@@ -15,10 +15,12 @@ import numpy as np
 
 from . import _abi
 from ._abi import (BC_CONVECTIVE, BC_FREESLIP, BC_INLET, BC_PERIODIC, FIELD_NAMES, INIT_DROPLET, INIT_FIELDS,
-                   INIT_JET, INIT_UNIFORM, LBError, library, make_grid, make_params)
+                   INIT_JET, INIT_UNIFORM, STORE_FP16, STORE_FP16_FIT, STORE_FP32, LBError, library, make_grid,
+                   make_params)
 
 __all__ = ["Lattice", "LBError", "library", "make_grid", "make_params", "BC_PERIODIC", "BC_FREESLIP",
-           "BC_INLET", "BC_CONVECTIVE", "FIELD_NAMES", "GRAD_NAMES", "OBJECTIVES"]
+           "BC_INLET", "BC_CONVECTIVE", "STORE_FP32", "STORE_FP16", "STORE_FP16_FIT", "FIELD_NAMES", "GRAD_NAMES",
+           "OBJECTIVES"]
 
 # order of the gradient entries lb_adjoint returns after J
 GRAD_NAMES = ("u_in", "sigma", "nu_r", "nu_b") + tuple(f"{ab}{m}" for m in range(1, 9) for ab in "ab")

@@ -11,6 +11,7 @@ MAX_BUFFERS = 8
 
 BC_PERIODIC, BC_FREESLIP, BC_INLET, BC_CONVECTIVE = 0, 1, 2, 3
 INIT_UNIFORM, INIT_DROPLET, INIT_JET, INIT_FIELDS = 0, 1, 2, 3
+STORE_FP32, STORE_FP16, STORE_FP16_FIT = 0, 1, 2
 FIELD_NAMES = ("rho_r", "rho_b", "phi", "ux", "uy", "uz", "p")
 STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_EUNSTABLE", 5: "LB_ETIMEOUT",
           6: "LB_ESTATE", 7: "LB_ENOTIMPL"}

@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(256) obj_fields_kernel(StepArgs a, float2 *ph)
         MassAcc mr, mb;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            const float2 v = load_pop<STORE_FP32>(a, i, (int)n, make_float2(0.0f, 0.0f));
+            const float2 v = load_pop<STORE_FP32>(a, i, (int)n, no_shift());
             mr.add(i, v.x);
             mb.add(i, v.y);
         }

@@ -40,9 +40,17 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Bytes of one population buffer: FP32 float2[27][NN]; FP16 float2 rest[NN] + __half2[26][NN].
+// Bytes of one population buffer: FP32 float2[27][NN]; FP16 (either encoding) float2 rest[NN]
+// + __half2[26][NN].
 size_t pop_buffer_bytes(size_t nn, int storage) {
-    return storage == LB_STORE_FP16 ? 8 * nn + 4 * 26 * nn : 8 * 27 * nn;
+    return storage != LB_STORE_FP32 ? 8 * nn + 4 * 26 * nn : 8 * 27 * nn;
+}
+
+// Bytes of the phase buffer: FP32 float2[NN]; FP16 two float4[NN] (one per population buffer);
+// FP16_FIT also two uint2[NN] of FP8 odd fits.
+size_t phase_buffer_bytes(size_t nn, int storage) {
+    if (storage == LB_STORE_FP32) return align_up(8 * nn);
+    return 2 * align_up(16 * nn) + (storage == LB_STORE_FP16_FIT ? 2 * align_up(8 * nn) : 0);
 }
 
 struct AuxLayout {
@@ -90,8 +98,8 @@ lb_status validate(const lb_grid *g, const lb_params *p) {
     for (double v : s)
         if (!(v >= 0.0 && v < 2.0)) return fail(LB_EINVAL, "relaxation rates must lie in [0, 2)");
     if (!(p->eps_grad >= 0) || !std::isfinite(p->eps_grad)) return fail(LB_EINVAL, "eps_grad must be finite and >= 0");
-    if (p->storage != LB_STORE_FP32 && p->storage != LB_STORE_FP16)
-        return fail(LB_EINVAL, "storage must be LB_STORE_FP32 or LB_STORE_FP16");
+    if (p->storage != LB_STORE_FP32 && p->storage != LB_STORE_FP16 && p->storage != LB_STORE_FP16_FIT)
+        return fail(LB_EINVAL, "storage must be LB_STORE_FP32, LB_STORE_FP16 or LB_STORE_FP16_FIT");
     if (p->check_every < 0) return fail(LB_EINVAL, "check_every must be >= 0");
     if (p->alpha_mix != 0 && p->alpha_mix != 1) return fail(LB_EINVAL, "alpha_mix must be 0 or 1");
     if (g->bc_zlo == LB_BC_INLET) {
@@ -118,6 +126,7 @@ struct lb_ctx {
     void *pop[2] = {nullptr, nullptr};
     float2 *phase = nullptr;               // FP32: (phi, rho) of the current step
     float4 *ph4[2] = {nullptr, nullptr};   // FP16: (phi, rho, rho_r, rho_b) paired with pop[0], pop[1]
+    uint2 *vp[2] = {nullptr, nullptr};     // FP16_FIT: FP8 odd fits paired with pop[0], pop[1]
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -184,13 +193,31 @@ __device__ __forceinline__ void init_fields_at(const InitArgs &ia, long long n, 
 }
 
 // FP16: phase entries (phi, rho, rho_r, rho_b) of the initial state, which its populations
-// are encoded for.
-__global__ void init_phase_kernel(InitArgs ia, float4 *__restrict__ ph, float inv_rho_r0, float inv_rho_b0) {
+// are encoded for.  FP16_FIT: (phi, rho, A_r, A_b) and the odd fit of the node's own initial
+// populations (the same prediction the phase-field pass makes from gathered ones).
+template <int S>
+__global__ void init_phase_kernel(InitArgs ia, StepArgs sa) {
     const long long NN = (long long)ia.nx * ia.ny * ia.nz;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < NN; n += (long long)gridDim.x * blockDim.x) {
         float rr, rb, ux, uy, uz;
         init_fields_at(ia, n, rr, rb, ux, uy, uz);
-        ph[n] = make_float4(order_parameter(rr, rb, inv_rho_r0, inv_rho_b0), rr + rb, rr, rb);
+        const float ph = order_parameter(rr, rb, sa.inv_rho_r0, sa.inv_rho_b0);
+        if constexpr (S == STORE_FP16) {
+            sa.ph_cur[n] = make_float4(ph, rr + rb, rr, rb);
+        } else {
+            const float2 A = fit_even(sa, rr, rb);
+            sa.ph_cur[n] = make_float4(ph, rr + rb, A.x, A.y);
+            const float usq = ux * ux + uy * uy + uz * uz;
+            float fr[27], fb[27];
+#pragma unroll
+            for (int i = 0; i < 27; ++i) {
+                const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+                const float pw = wgt(i) * eq_poly(cu, usq);
+                fr[i] = rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw);
+                fb[i] = rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw);
+            }
+            sa.vp_cur[n] = fit_odd_fp8(sa, fr, fb);
+        }
     }
 }
 
@@ -220,7 +247,7 @@ __global__ void init_kernel(InitArgs ia, StepArgs sa) {
             }
         }
         const float2 f0 = make_float2(rr - sr.s, rb - sb.s);
-        store_pop<S>(sa, 0, (int)n, f0, make_float2(0.0f, 0.0f));
+        store_pop<S>(sa, 0, (int)n, f0, no_shift());
         if (top) {
             ia.hist[h] = f0.x;
             ia.hist[27 * P + h] = f0.y;
@@ -394,9 +421,14 @@ lb_status setup_ctx(lb_ctx *c) {
     const size_t hist_bytes = (size_t)54 * c->plane * sizeof(float);
     c->pop[0] = c->bufs[0];
     c->pop[1] = c->bufs[1];
-    if (c->p.storage == LB_STORE_FP16) {
+    if (c->p.storage != LB_STORE_FP32) {
+        const size_t b4 = align_up(16 * (size_t)c->nn), b2 = align_up(8 * (size_t)c->nn);
         c->ph4[0] = (float4 *)c->bufs[2];
-        c->ph4[1] = (float4 *)((char *)c->bufs[2] + align_up(16 * (size_t)c->nn));
+        c->ph4[1] = (float4 *)((char *)c->bufs[2] + b4);
+        if (c->p.storage == LB_STORE_FP16_FIT) {
+            c->vp[0] = (uint2 *)((char *)c->bufs[2] + 2 * b4);
+            c->vp[1] = (uint2 *)((char *)c->bufs[2] + 2 * b4 + b2);
+        }
     } else {
         c->phase = (float2 *)c->bufs[2];
     }
@@ -420,6 +452,8 @@ StepArgs make_args(const lb_ctx *c) {
     a.phase = c->phase;
     a.ph_prev = c->ph4[c->cur];
     a.ph_cur = c->ph4[c->cur ^ 1];
+    a.vp_prev = c->vp[c->cur];
+    a.vp_cur = c->vp[c->cur ^ 1];
     a.hist_in = c->hist[c->hcur];
     a.hist_out = c->hist[c->hcur ^ 1];
     a.zin = c->zin;
@@ -452,6 +486,18 @@ StepArgs make_args(const lb_ctx *c) {
         a.shift_r[q] = (float)(kq[q] * (1.0 - alpha_r));
         a.shift_b[q] = (float)(kq[q] * (1.0 - alpha_b));
     }
+    // FP16_FIT scales, powers of two tied to the density scale: S_h = 2^floor(log2(1024 /
+    // rho_max)) keeps |S_h h| far below the FP16 maximum for |h| up to 64 rho_max while moving
+    // the small deviations of a resting fluid out of the subnormal range; S_v = 2^round(log2(64 /
+    // rho_max)) maps odd fits up to 7 rho_max (3 rho u for u < 2) into the e4m3 range.
+    const double rho_max = std::max(p.rho_r0, p.rho_b0);
+    const int eh = std::min(60, std::max(-60, (int)std::floor(std::log2(1024.0 / rho_max))));
+    const int ev = std::min(60, std::max(-60, (int)std::lround(std::log2(64.0 / rho_max))));
+    a.dev_scale = std::ldexp(1.0f, eh);
+    a.inv_dev_scale = std::ldexp(1.0f, -eh);
+    a.v_scale = std::ldexp(1.0f, ev);
+    const double wq[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+    for (int q = 0; q < 4; ++q) a.wv[q] = (float)std::ldexp(wq[q], -ev);
     for (int m = 0; m < 16; ++m) a.fourier[m] = (float)p.fourier[m];
     a.seed = p.seed;
     a.step = c->step;
@@ -465,6 +511,8 @@ StepArgs state_args(const lb_ctx *c) {
     StepArgs a = make_args(c);
     a.ph_cur = c->ph4[c->cur];
     a.ph_prev = c->ph4[c->cur];
+    a.vp_cur = c->vp[c->cur];
+    a.vp_prev = c->vp[c->cur];
     return a;
 }
 
@@ -472,6 +520,8 @@ lb_status run_mass(lb_ctx *c, double out[2]) {
     const StepArgs sa = state_args(c);
     if (c->p.storage == LB_STORE_FP16)
         mass_partial_store_kernel<STORE_FP16><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
+    else if (c->p.storage == LB_STORE_FP16_FIT)
+        mass_partial_store_kernel<STORE_FP16_FIT><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
     else
         mass_partial_store_kernel<STORE_FP32><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
     mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->partial, kMassBlocks, c->partial + 2 * kMassBlocks);
@@ -514,7 +564,7 @@ lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *
     const size_t nn = (size_t)grid->nx * grid->ny * grid->nz, plane = (size_t)grid->nx * grid->ny;
     sizes_out[0] = align_up(pop_buffer_bytes(nn, params->storage));
     sizes_out[1] = sizes_out[0];
-    sizes_out[2] = params->storage == LB_STORE_FP16 ? 2 * align_up(16 * nn) : align_up(8 * nn);  // phase field
+    sizes_out[2] = phase_buffer_bytes(nn, params->storage);  // phase field
     sizes_out[3] = 2 * align_up(54 * plane * sizeof(float));
     sizes_out[4] = aux_layout(*grid).total;
     *n_out = 5;
@@ -600,6 +650,11 @@ lb_status lb_set_params(lb_ctx *c, const lb_params *params) {
     lb_status s = validate(&c->g, params);
     if (s != LB_OK) return s;
     if (params->storage != c->p.storage) return fail(LB_EINVAL, "storage cannot change on an existing context");
+    // the FP16 encodings' shift weights and scales derive from rho_r0, rho_b0: a stored state
+    // would decode to other populations under new ones
+    if (c->p.storage != LB_STORE_FP32 && c->initialized &&
+        (params->rho_r0 != c->p.rho_r0 || params->rho_b0 != c->p.rho_b0))
+        return fail(LB_EINVAL, "rho_r0 and rho_b0 cannot change on an initialised FP16 context");
     c->p = *params;
     c->adj.valid = false;
     return upload_disc(c);
@@ -644,14 +699,19 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
             fr = stage; fb = stage + c->nn; fu = stage + 2 * c->nn;
         }
     }
-    StepArgs sa = make_args(c);  // cur = 0: the state is written into pop[0] / ph4[0]
+    StepArgs sa = make_args(c);  // cur = 0: the state is written into pop[0] / ph4[0] / vp[0]
     sa.pout = c->pop[0];
     sa.ph_cur = c->ph4[0];
+    sa.vp_cur = c->vp[0];
     InitArgs ia{c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz,
                 a[0], a[1], a[2], a[3], a[4], sa.rho_r0, sa.rho_b0, sa.alpha_r, sa.alpha_b};
     if (c->p.storage == LB_STORE_FP16) {
-        init_phase_kernel<<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, c->ph4[0], sa.inv_rho_r0, sa.inv_rho_b0);
+        init_phase_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
         init_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
+        c->launches += 2;
+    } else if (c->p.storage == LB_STORE_FP16_FIT) {
+        init_phase_kernel<STORE_FP16_FIT><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
+        init_kernel<STORE_FP16_FIT><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
         c->launches += 2;
     } else {
         init_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
@@ -706,6 +766,8 @@ lb_status lb_fields(lb_ctx *c, uint32_t mask, float *const *outs, int32_t on_dev
     for (int j = 0; j < LB_NFIELDS; ++j) fo.o[j] = dst[j];
     if (c->p.storage == LB_STORE_FP16)
         fields_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, fo, sa.gx, sa.gy, sa.gz);
+    else if (c->p.storage == LB_STORE_FP16_FIT)
+        fields_kernel<STORE_FP16_FIT><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, fo, sa.gx, sa.gy, sa.gz);
     else
         fields_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, fo, sa.gx, sa.gy, sa.gz);
     c->launches += 1;
@@ -730,6 +792,8 @@ lb_status lb_populations(lb_ctx *c, float *out, int32_t on_device) {
         float *dst = on_device ? out + (size_t)k * 27 * c->nn : stage;
         if (c->p.storage == LB_STORE_FP16)
             canonical_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, k, dst);
+        else if (c->p.storage == LB_STORE_FP16_FIT)
+            canonical_kernel<STORE_FP16_FIT><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, k, dst);
         else
             canonical_kernel<STORE_FP32><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(sa, k, dst);
         c->launches += 1;
@@ -794,8 +858,11 @@ struct SaveHeader {
 };
 
 // Checkpoint layout: header, the raw current population buffer (internal storage layout),
-// for FP16 storage the phase entries it was encoded for, then the outflow history plane.
-static size_t shift_bytes(const lb_ctx *c) { return c->p.storage == LB_STORE_FP16 ? 16 * (size_t)c->nn : 0; }
+// for FP16 storage the phase entries it was encoded for (FP16_FIT: and their odd fits), then
+// the outflow history plane.
+static size_t shift_bytes(const lb_ctx *c) {
+    return c->p.storage == LB_STORE_FP32 ? 0 : (c->p.storage == LB_STORE_FP16_FIT ? 24 : 16) * (size_t)c->nn;
+}
 
 lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     if (!c || !nbytes) return fail(LB_EINVAL, "ctx and nbytes must not be NULL");
@@ -812,7 +879,10 @@ lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     std::memcpy(buf, &h, sizeof(h));
     char *p = (char *)buf + sizeof(h);
     LB_CUDA(cudaMemcpyAsync(p, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
-    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->ph4[c->cur], sb, cudaMemcpyDeviceToHost, c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->ph4[c->cur], 16 * (size_t)c->nn, cudaMemcpyDeviceToHost, c->stream));
+    if (sb > 16 * (size_t)c->nn)
+        LB_CUDA(cudaMemcpyAsync(p + pb + 16 * (size_t)c->nn, c->vp[c->cur], 8 * (size_t)c->nn, cudaMemcpyDeviceToHost,
+                                c->stream));
     LB_CUDA(cudaMemcpyAsync(p + pb + sb, c->hist[c->hcur], hb, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     *nbytes = total;
@@ -833,7 +903,10 @@ lb_status lb_load(lb_ctx *c, const void *buf, size_t nbytes) {
     c->cur = 0;
     c->hcur = 0;
     LB_CUDA(cudaMemcpyAsync(c->pop[0], p, pb, cudaMemcpyHostToDevice, c->stream));
-    if (sb) LB_CUDA(cudaMemcpyAsync(c->ph4[0], p + pb, sb, cudaMemcpyHostToDevice, c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(c->ph4[0], p + pb, 16 * (size_t)c->nn, cudaMemcpyHostToDevice, c->stream));
+    if (sb > 16 * (size_t)c->nn)
+        LB_CUDA(cudaMemcpyAsync(c->vp[0], p + pb + 16 * (size_t)c->nn, 8 * (size_t)c->nn, cudaMemcpyHostToDevice,
+                                c->stream));
     LB_CUDA(cudaMemcpyAsync(c->hist[0], p + pb + sb, hb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = h.step;

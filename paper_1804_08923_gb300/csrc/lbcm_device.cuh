@@ -6,6 +6,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 namespace lbcm {
@@ -169,7 +170,16 @@ enum { BC_PERIODIC = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_CONVECTIVE = 3 };
 // equilibrium of the node d = y + c_i that will read it (pull streaming), so that a node
 // decodes everything it gathers with its own colour densities.  Those come from a float4
 // (phi, rho, rho_r, rho_b) phase buffer that pairs with each population buffer.
-enum { STORE_FP32 = 0, STORE_FP16 = 1 };
+// FP16_FIT: the same layout, with h_i^k = S_h (f_i^k - P_i^k(d)) against a per-reader
+// prediction P_i^k = A_k k_q(i) + w_i c_i . v_k / S_v.  A_k = rho_k (1 - alpha-bar) is the even
+// (rest-equilibrium) part with the mixture's alpha-bar; v_k, the odd part, is the least-squares
+// fit sum_i (f_i^k - w_i c_i . v)^2 -> min over the 26 moving populations the reader gathered
+// in the step before (v_k = 72 sum_i w_i c_i f_i^k, since sum_i w_i^2 c_ix^2 = 1/72), stored
+// as FP8 e4m3 scaled by the power of two S_v.  The phase buffer holds (phi, rho, A_r, A_b) and
+// a uint2 of the six FP8 values; S_h is a power of two that lifts the deviations out of the
+// FP16 subnormal range.  Near an interface the recolouring and the reader-writer density
+// difference make h large under the rest shift; the fitted prediction removes most of it.
+enum { STORE_FP32 = 0, STORE_FP16 = 1, STORE_FP16_FIT = 2 };
 
 // Everything a step kernel needs, passed by value.
 struct StepArgs {
@@ -178,6 +188,9 @@ struct StepArgs {
     float2 *__restrict__ phase;         // FP32 storage: post-stream (phi, rho) of step t+1
     const float4 *__restrict__ ph_prev; // FP16: (phi, rho, rho_r, rho_b) that S(t) was encoded with
     float4 *__restrict__ ph_cur;        // FP16: post-stream (phi, rho, rho_r, rho_b) of step t+1
+                                        // (FP16_FIT: (phi, rho, A_r, A_b))
+    const uint2 *__restrict__ vp_prev;  // FP16_FIT: FP8 odd fits (v_r, v_b) paired with ph_prev
+    uint2 *__restrict__ vp_cur;         // FP16_FIT: FP8 odd fits paired with ph_cur
     const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
     float *__restrict__ hist_out;       // outflow plane f(N, t+1)
     float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]
@@ -194,6 +207,9 @@ struct StepArgs {
     float s0, s1, s2b, s3, s4, s5, s6;
     float u_in, noise_amp, xc, yc;
     float shift_r[4], shift_b[4];       // varphi_i(alpha_k) by speed class |c|^2 = 1..3 (FP16 shift)
+    float wv[4];                        // FP16_FIT: w_q / S_v by speed class
+    float dev_scale, inv_dev_scale;     // FP16_FIT: S_h, 1/S_h (powers of two)
+    float v_scale;                      // FP16_FIT: S_v (power of two)
     float fourier[16];                  // inlet profile coefficients a_1, b_1, ..., a_8, b_8
     // optional outputs for the adjoint's recompute (NULL otherwise): the collision inputs of
     // every node, rec[0..3][NN] = (rho_r, rho_b, jx, jy), (jz, Pxx, Pyy, Pzz), (Pxy, Pxz, Pyz,
@@ -211,12 +227,54 @@ __device__ __forceinline__ float2 shift_w(const StepArgs &a, int i) {
     return make_float2(a.shift_r[csq(i)], a.shift_b[csq(i)]);
 }
 
+// What a reading node decodes its incoming populations with: FP16, A = (rho_r, rho_b);
+// FP16_FIT, A = (A_r, A_b) and v[d] = (v_r, v_b) along axis d, times S_v, widened from FP8 to
+// half precision (exactly).  Unused for FP32.
+struct Own {
+    float2 A;
+    __half2 v[3];
+};
+
+__device__ __forceinline__ __half2 fp8x2_to_half2(unsigned int bits) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits & 0xffffu), __NV_E4M3);
+    return __half2(h);
+}
+
+template <int S>
+__device__ __forceinline__ Own own_of(const float4 *ph, const uint2 *vp, int n) {
+    Own o{};
+    if constexpr (S != STORE_FP32) {
+        const float4 v = __ldg(ph + n);
+        o.A = make_float2(v.z, v.w);
+    }
+    if constexpr (S == STORE_FP16_FIT) {
+        const uint2 b = __ldg(vp + n);
+        o.v[0] = fp8x2_to_half2(b.x);
+        o.v[1] = fp8x2_to_half2(b.x >> 16);
+        o.v[2] = fp8x2_to_half2(b.y);
+    }
+    return o;
+}
+
+// FP16_FIT prediction P^k for the slot of direction j (class of i = class of j): one fixed
+// sequence of operations, so that the writer and the reader get the same bits.  The odd sum
+// c_j . v runs on both colours at once in half precision (a prediction needs no more).
+__device__ __forceinline__ float2 fit_pred(const StepArgs &a, int i, int j, const Own &o) {
+    __half2 dh = __float2half2_rn(0.0f);
+    if (cx(j) > 0) dh = __hadd2(dh, o.v[0]); else if (cx(j) < 0) dh = __hsub2(dh, o.v[0]);
+    if (cy(j) > 0) dh = __hadd2(dh, o.v[1]); else if (cy(j) < 0) dh = __hsub2(dh, o.v[1]);
+    if (cz(j) > 0) dh = __hadd2(dh, o.v[2]); else if (cz(j) < 0) dh = __hsub2(dh, o.v[2]);
+    const float2 d = __half22float2(dh);
+    const float wq = a.wv[csq(i)], kq = varphi_k(i);
+    return make_float2(fmaf(o.A.x, kq, wq * d.x), fmaf(o.A.y, kq, wq * d.y));
+}
+
 // Populations (red, blue) of direction j stored at node src, decoded to FP32; for FP16,
-// own = (rho_r, rho_b) of the reading node, the node the value was encoded for.  i is a
+// own holds what the reading node, the node the value was encoded for, decodes with.  i is a
 // direction with |c_i| = |c_j| (j itself, or the direction j is reflected from at a side wall):
 // it selects the shift weight, so that an unrolled caller indexes the weights at compile time.
 template <int S>
-__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, float2 own, int j) {
+__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, const Own &own, int j) {
     if constexpr (S == STORE_FP32) {
         return __ldg(reinterpret_cast<const float2 *>(a.pin) + (size_t)j * a.NN + src);
     } else {
@@ -224,31 +282,31 @@ __device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, fl
         if (i == 0) return __ldg(rest + src);
         const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
         const float2 h = __half22float2(__ldg(mov + (size_t)(j - 1) * a.NN + src));
-        const float2 w = shift_w(a, i);
-        return make_float2(fmaf(own.x, w.x, h.x), fmaf(own.y, w.y, h.y));
+        if constexpr (S == STORE_FP16) {
+            const float2 w = shift_w(a, i);
+            return make_float2(fmaf(own.A.x, w.x, h.x), fmaf(own.A.y, w.y, h.y));
+        } else {
+            const float2 p = fit_pred(a, i, j, own);
+            return make_float2(fmaf(h.x, a.inv_dev_scale, p.x), fmaf(h.y, a.inv_dev_scale, p.y));
+        }
     }
 }
 template <int S>
-__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, float2 own) {
+__device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, const Own &own) {
     return load_pop<S>(a, i, src, own, i);
 }
 
-// Colour densities a node decodes its gathered populations with (FP16; unused for FP32).
+// What node n decodes its gathered populations with (the entries S(t) was encoded for).
 template <int S>
-__device__ __forceinline__ float2 reader_shift(const StepArgs &a, int n) {
-    if constexpr (S == STORE_FP32) {
-        return make_float2(0.0f, 0.0f);
-    } else {
-        const float4 v = __ldg(a.ph_prev + n);
-        return make_float2(v.z, v.w);
-    }
+__device__ __forceinline__ Own reader_shift(const StepArgs &a, int n) {
+    return own_of<S>(a.ph_prev, a.vp_prev, n);
 }
 
-// Store populations f of direction i at node n; dest = (rho_r, rho_b) of the node n + c_i
-// that will read them (FP16).  Returns the values that node will decode, so the caller can
+// Store populations f of direction i at node n; dest = what the node n + c_i that will read
+// them decodes with (FP16).  Returns the values that node will decode, so the caller can
 // account for the storage rounding.
 template <int S>
-__device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, float2 f, float2 dest) {
+__device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, float2 f, const Own &dest) {
     if constexpr (S == STORE_FP32) {
         reinterpret_cast<float2 *>(a.pout)[(size_t)i * a.NN + n] = f;
         return f;
@@ -258,12 +316,50 @@ __device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, flo
             rest[n] = f;
             return f;
         }
-        const float2 w = shift_w(a, i);
-        const __half2 h = __floats2half2_rn(fmaf(-dest.x, w.x, f.x), fmaf(-dest.y, w.y, f.y));
-        reinterpret_cast<__half2 *>(rest + a.NN)[(size_t)(i - 1) * a.NN + n] = h;
-        const float2 hf = __half22float2(h);
-        return make_float2(fmaf(dest.x, w.x, hf.x), fmaf(dest.y, w.y, hf.y));
+        __half2 *slot = reinterpret_cast<__half2 *>(rest + a.NN) + (size_t)(i - 1) * a.NN + n;
+        if constexpr (S == STORE_FP16) {
+            const float2 w = shift_w(a, i);
+            const __half2 h = __floats2half2_rn(fmaf(-dest.A.x, w.x, f.x), fmaf(-dest.A.y, w.y, f.y));
+            *slot = h;
+            const float2 hf = __half22float2(h);
+            return make_float2(fmaf(dest.A.x, w.x, hf.x), fmaf(dest.A.y, w.y, hf.y));
+        } else {
+            const float2 p = fit_pred(a, i, i, dest);
+            const __half2 h = __floats2half2_rn((f.x - p.x) * a.dev_scale, (f.y - p.y) * a.dev_scale);
+            *slot = h;
+            const float2 hf = __half22float2(h);
+            return make_float2(fmaf(hf.x, a.inv_dev_scale, p.x), fmaf(hf.y, a.inv_dev_scale, p.y));
+        }
     }
+}
+__device__ __forceinline__ Own no_shift() { return Own{}; }
+
+// FP16_FIT odd fit of one colour's gathered populations, times S_v, packed as FP8 e4m3
+// pairs (red, blue) per axis: bits 0-15 x, 16-31 y, 32-47 z.
+__device__ __forceinline__ uint2 fit_odd_fp8(const StepArgs &a, const float (&fr)[27], const float (&fb)[27]) {
+    float vr[3] = {0.0f, 0.0f, 0.0f}, vb[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 1; i < 27; i += 2) {  // c_{i+1} = -c_i: the pair contributes w_i c_i (f_i - f_{i+1})
+        const float dr = wgt(i) * (fr[i] - fr[i + 1]), db = wgt(i) * (fb[i] - fb[i + 1]);
+        if (cx(i) > 0) { vr[0] += dr; vb[0] += db; } else if (cx(i) < 0) { vr[0] -= dr; vb[0] -= db; }
+        if (cy(i) > 0) { vr[1] += dr; vb[1] += db; } else if (cy(i) < 0) { vr[1] -= dr; vb[1] -= db; }
+        if (cz(i) > 0) { vr[2] += dr; vb[2] += db; } else if (cz(i) < 0) { vr[2] -= dr; vb[2] -= db; }
+    }
+    const float sc = 72.0f * a.v_scale;
+    unsigned int q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        q[d] = (unsigned int)__nv_cvt_float2_to_fp8x2(make_float2(vr[d] * sc, vb[d] * sc), __NV_SATFINITE, __NV_E4M3);
+    return make_uint2(q[0] | (q[1] << 16), q[2]);
+}
+
+// FP16_FIT even part A_k = rho_k (1 - alpha-bar) of a node with colour densities (rr, rb).
+__device__ __forceinline__ float2 fit_even(const StepArgs &a, float rr, float rb) {
+    const float rho = rr + rb, inv_rho = 1.0f / rho;
+    const float phi = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
+    const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
+    const float oma = 1.0f - alpha_bar(a.alpha_mix, rr, rb, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
+    return make_float2(rr * oma, rb * oma);
 }
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
@@ -314,19 +410,14 @@ struct Nbr {
     __device__ __forceinline__ bool gy(int j) const { return cy(j) < 0 ? wyl : (cy(j) > 0 ? wyh : false); }
 };
 
-// Colour densities of the node that will read direction i from node nb.n (FP16 encoding).
+// What the node that will read direction i from node nb.n decodes with (FP16 encodings).
 template <int S>
-__device__ __forceinline__ float2 dest_shift(const StepArgs &a, const Nbr &nb, int i) {
-    if constexpr (S == STORE_FP32) {
-        return make_float2(0.0f, 0.0f);
-    } else {
-        const float4 v = __ldg(a.ph_cur + nb.nbr(i));
-        return make_float2(v.z, v.w);
-    }
+__device__ __forceinline__ Own dest_shift(const StepArgs &a, const Nbr &nb, int i) {
+    return own_of<S>(a.ph_cur, a.vp_cur, nb.nbr(i));
 }
 
-// Populations (red, blue) of direction i stored at node nb.n, decoded (for FP16 with the
-// densities of the node that reads them; a.ph_cur must pair with a.pin).
+// Populations (red, blue) of direction i stored at node nb.n, decoded (for FP16 with what
+// the node that reads them decodes with; a.ph_cur / a.vp_cur must pair with a.pin).
 template <int S>
 __device__ __forceinline__ float2 stored_pop(const StepArgs &a, const Nbr &nb, int i) {
     return load_pop<S>(a, i, nb.n, dest_shift<S>(a, nb, i));

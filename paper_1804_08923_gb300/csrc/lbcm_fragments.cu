@@ -186,6 +186,8 @@ cudaError_t launch_fragments_label(const StepArgs &a, int storage, int connectiv
     FragGeom g{a.nx, a.ny, a.nz, a.bc_zlo == BC_PERIODIC, connectivity, a.wall_x, a.wall_y, a.NN, a.plane};
     if (storage == STORE_FP16)
         frag_init_kernel<STORE_FP16><<<frag_grid(a.NN), 256, 0, s>>>(a, label);
+    else if (storage == STORE_FP16_FIT)
+        frag_init_kernel<STORE_FP16_FIT><<<frag_grid(a.NN), 256, 0, s>>>(a, label);
     else
         frag_init_kernel<STORE_FP32><<<frag_grid(a.NN), 256, 0, s>>>(a, label);
     frag_union_kernel<<<frag_grid(a.NN), 256, 0, s>>>(g, label, err);

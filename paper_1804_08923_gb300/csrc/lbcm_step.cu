@@ -142,10 +142,15 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
     }
     const float rr = mr.total(), rb = mb.total();
     const float ph = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
-    if constexpr (S == STORE_FP32)
+    if constexpr (S == STORE_FP32) {
         a.phase[nb.n] = make_float2(ph, rr + rb);
-    else
+    } else if constexpr (S == STORE_FP16) {
         a.ph_cur[nb.n] = make_float4(ph, rr + rb, rr, rb);  // also the FP16 shift densities of S(t+1)
+    } else {  // the prediction S(t+1) is encoded against
+        const float2 A = fit_even(a, rr, rb);
+        a.ph_cur[nb.n] = make_float4(ph, rr + rb, A.x, A.y);
+        a.vp_cur[nb.n] = fit_odd_fp8(a, fr, fb);
+    }
 }
 
 // 1-D shifted moment sweep: values at c = -1, 0, +1 -> central moments of order 0, 1, 2
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
         sum_b.add(i, d.y);
     }
     // rest direction as the per-colour remainder (see collide_from_moments)
-    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r.s, rho_b - sum_b.s), make_float2(0.0f, 0.0f));
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r.s, rho_b - sum_b.s), no_shift());
 }
 
 
@@ -447,13 +452,13 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     // they will be read back; this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32
     // rounding of the lattice constants and any storage rounding from drifting the colour
     // masses step after step (the pairwise sum above is MassAcc's association).
-    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), make_float2(0.0f, 0.0f));
+    store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), no_shift());
 }
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
 // kRec (FP32, adjoint recompute): also writes the node's collision inputs to a.rec / a.rec4.
 template <bool kForce, int S, bool kRec, bool W>
-__global__ void __launch_bounds__(128, (S == STORE_FP16 ? 5 : 6)) collide_kernel(StepArgs a) {
+__global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : 5)) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -518,6 +523,8 @@ cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEven
                         bool collide) {
     if (storage == STORE_FP16)
         launch_step_s<STORE_FP16>(a, s, ev, launches, collide);
+    else if (storage == STORE_FP16_FIT)
+        launch_step_s<STORE_FP16_FIT>(a, s, ev, launches, collide);
     else
         launch_step_s<STORE_FP32>(a, s, ev, launches, collide);
     return cudaGetLastError();

@@ -56,6 +56,15 @@ def test_buffer_sizes_and_validation(lib):
     nodes = 96 * 96 * 384
     assert n.value == 5 and sizes[0] >= 54 * 4 * nodes and sizes[1] == sizes[0] and sizes[2] >= 8 * nodes
     assert all(int(sizes[j]) % 256 == 0 for j in range(n.value))
+    # FP16 storage: 112 B per node per population buffer; the phase buffer holds two float4
+    # entries per node, and two uint2 FP8 fits more with the fitted encoding
+    by = {}
+    for st in (_abi.STORE_FP16, _abi.STORE_FP16_FIT):
+        ps = _abi.make_params(dict(rho_r0=1.0, rho_b0=2 / 3, nu_r=4e-4, nu_b=4e-4, sigma=4e-4, storage=st))
+        assert lib.lb_buffer_sizes(C.byref(g), C.byref(ps), sizes, C.byref(n)) == 0
+        by[st] = [int(sizes[j]) for j in range(n.value)]
+        assert 112 * nodes <= by[st][0] < 112 * nodes + 256
+    assert by[_abi.STORE_FP16][2] >= 32 * nodes and by[_abi.STORE_FP16_FIT][2] >= 48 * nodes
     bad = [
         (_abi.make_grid(0, 4, 4), p),
         (_abi.make_grid(4, 4, 4, _abi.BC_INLET, _abi.BC_PERIODIC), p),
@@ -65,6 +74,7 @@ def test_buffer_sizes_and_validation(lib):
         (g, _abi.make_params(dict(nu_r=-1.0))),
         (g, _abi.make_params(dict(s3=2.5))),
         (g, _abi.make_params(dict(storage=9))),
+        (g, _abi.make_params(dict(storage=-1))),
     ]
     for gg, pp in bad:
         assert lib.lb_buffer_sizes(C.byref(gg), C.byref(pp), sizes, C.byref(n)) == 1
