@@ -296,6 +296,40 @@ __device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, co
     return load_pop<S>(a, i, src, own, i);
 }
 
+// FP16_FIT decoding of pulls reflected at side walls.  The slot read is j = i with the
+// crossing velocity components reversed; instead of evaluating c_j . v with a run-time j, the
+// node negates its odd fit once per side (xp: components of directions with c_x > 0, xn: c_x <
+// 0, likewise y), so the sum runs over compile-time signs of i.  The sums equal those of
+// fit_pred for slot j bit for bit: 0 + (-v) = 0 - v and d + (-v) = d - v exactly.
+struct OwnFlip {
+    float2 A;
+    __half2 xp, xn, yp, yn, z;
+};
+__device__ __forceinline__ OwnFlip flip_own(const Own &o, bool wxl, bool wxh, bool wyl, bool wyh) {
+    OwnFlip f;
+    f.A = o.A;
+    f.xp = wxl ? __hneg2(o.v[0]) : o.v[0];
+    f.xn = wxh ? __hneg2(o.v[0]) : o.v[0];
+    f.yp = wyl ? __hneg2(o.v[1]) : o.v[1];
+    f.yn = wyh ? __hneg2(o.v[1]) : o.v[1];
+    f.z = o.v[2];
+    return f;
+}
+__device__ __forceinline__ float2 load_pop_flip(const StepArgs &a, int i, int src, const OwnFlip &o, int j) {
+    const float2 *rest = reinterpret_cast<const float2 *>(a.pin);
+    if (i == 0) return __ldg(rest + src);
+    const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
+    const float2 h = __half22float2(__ldg(mov + (size_t)(j - 1) * a.NN + src));
+    __half2 dh = __float2half2_rn(0.0f);
+    if (cx(i) > 0) dh = __hadd2(dh, o.xp); else if (cx(i) < 0) dh = __hsub2(dh, o.xn);
+    if (cy(i) > 0) dh = __hadd2(dh, o.yp); else if (cy(i) < 0) dh = __hsub2(dh, o.yn);
+    if (cz(i) > 0) dh = __hadd2(dh, o.z); else if (cz(i) < 0) dh = __hsub2(dh, o.z);
+    const float2 d = __half22float2(dh);
+    const float wq = a.wv[csq(i)], kq = varphi_k(i);
+    const float2 p = make_float2(fmaf(o.A.x, kq, wq * d.x), fmaf(o.A.y, kq, wq * d.y));
+    return make_float2(fmaf(h.x, a.inv_dev_scale, p.x), fmaf(h.y, a.inv_dev_scale, p.y));
+}
+
 // What node n decodes its gathered populations with (the entries S(t) was encoded for).
 template <int S>
 __device__ __forceinline__ Own reader_shift(const StepArgs &a, int n) {

@@ -60,8 +60,25 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
     bool reflect = false;
     if constexpr (W) reflect = __any_sync(__activemask(), nb.wxl || nb.wxh || nb.wyl || nb.wyh);
     if (reflect) {
+        if constexpr (S == STORE_FP16_FIT) {
+            const OwnFlip of = flip_own(own, nb.wxl, nb.wxh, nb.wyl, nb.wyh);
 #pragma unroll
-        for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, nb.pulled(i), fr, fb);
+            for (int i = 0; i < 27; ++i) {
+                const float2 v = load_pop_flip(a, i, nb.src(i), of, nb.pulled(i));
+                fr[i] = v.x;
+                fb[i] = v.y;
+                if (cz(i) == 1 && lo) {
+                    fr[i] = a.zin[zrank(i) * P + nb.pxy];
+                    fb[i] = a.zin[(9 + zrank(i)) * P + nb.pxy];
+                } else if (cz(i) == -1 && slip_hi) {
+                    fr[i] = a.zout[zrank(i) * P + nb.pxy];
+                    fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, nb.pulled(i), fr, fb);
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, i, fr, fb);
