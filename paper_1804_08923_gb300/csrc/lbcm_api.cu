@@ -205,7 +205,7 @@ __global__ void init_phase_kernel(InitArgs ia, StepArgs sa) {
         if constexpr (S == STORE_FP16) {
             sa.ph_cur[n] = make_float4(ph, rr + rb, rr, rb);
         } else {
-            const float2 A = fit_even(sa, rr, rb);
+            const float2 A = fit_even(sa, rr, rb, ph);
             sa.ph_cur[n] = make_float4(ph, rr + rb, A.x, A.y);
             const float usq = ux * ux + uy * uy + uz * uz;
             float fr[27], fb[27];

@@ -256,17 +256,32 @@ __device__ __forceinline__ Own own_of(const float4 *ph, const uint2 *vp, int n) 
     return o;
 }
 
-// FP16_FIT prediction P^k for the slot of direction j (class of i = class of j): one fixed
-// sequence of operations, so that the writer and the reader get the same bits.  The odd sum
-// c_j . v runs on both colours at once in half precision (a prediction needs no more).
-__device__ __forceinline__ float2 fit_pred(const StepArgs &a, int i, int j, const Own &o) {
+// FP16_FIT prediction P^k for the slot of direction j (class q of i = class of j):
+//   P = fl(fl(A k_q) + fl(w_q/S_v (c_j . v))),
+// one fixed sequence of operations, so that the writer and the reader get the same bits.  The
+// odd sum c_j . v runs on both colours at once in half precision (a prediction needs no more).
+// Opposite slots share fl(A k_q) and get exactly opposite odd terms (negation is exact), which
+// lets a reader decode a pair of opposite pulls with one odd sum (gather_fit).  The products
+// and sums are __fmul_rn / __fadd_rn, which the compiler never contracts into an FMA, so every
+// call site rounds the same way.
+__device__ __forceinline__ __half2 odd_sum(int j, const Own &o) {
     __half2 dh = __float2half2_rn(0.0f);
     if (cx(j) > 0) dh = __hadd2(dh, o.v[0]); else if (cx(j) < 0) dh = __hsub2(dh, o.v[0]);
     if (cy(j) > 0) dh = __hadd2(dh, o.v[1]); else if (cy(j) < 0) dh = __hsub2(dh, o.v[1]);
     if (cz(j) > 0) dh = __hadd2(dh, o.v[2]); else if (cz(j) < 0) dh = __hsub2(dh, o.v[2]);
+    return dh;
+}
+__device__ __forceinline__ float2 fit_base(float2 A, int i) {
+    return make_float2(__fmul_rn(A.x, varphi_k(i)), __fmul_rn(A.y, varphi_k(i)));
+}
+__device__ __forceinline__ float2 fit_odd(const StepArgs &a, int i, __half2 dh) {
     const float2 d = __half22float2(dh);
-    const float wq = a.wv[csq(i)], kq = varphi_k(i);
-    return make_float2(fmaf(o.A.x, kq, wq * d.x), fmaf(o.A.y, kq, wq * d.y));
+    const float wq = a.wv[csq(i)];
+    return make_float2(__fmul_rn(wq, d.x), __fmul_rn(wq, d.y));
+}
+__device__ __forceinline__ float2 fit_pred(const StepArgs &a, int i, int j, const Own &o) {
+    const float2 b = fit_base(o.A, i), e = fit_odd(a, i, odd_sum(j, o));
+    return make_float2(__fadd_rn(b.x, e.x), __fadd_rn(b.y, e.y));
 }
 
 // Populations (red, blue) of direction j stored at node src, decoded to FP32; for FP16,
@@ -324,9 +339,8 @@ __device__ __forceinline__ float2 load_pop_flip(const StepArgs &a, int i, int sr
     if (cx(i) > 0) dh = __hadd2(dh, o.xp); else if (cx(i) < 0) dh = __hsub2(dh, o.xn);
     if (cy(i) > 0) dh = __hadd2(dh, o.yp); else if (cy(i) < 0) dh = __hsub2(dh, o.yn);
     if (cz(i) > 0) dh = __hadd2(dh, o.z); else if (cz(i) < 0) dh = __hsub2(dh, o.z);
-    const float2 d = __half22float2(dh);
-    const float wq = a.wv[csq(i)], kq = varphi_k(i);
-    const float2 p = make_float2(fmaf(o.A.x, kq, wq * d.x), fmaf(o.A.y, kq, wq * d.y));
+    const float2 b = fit_base(o.A, i), e = fit_odd(a, i, dh);
+    const float2 p = make_float2(__fadd_rn(b.x, e.x), __fadd_rn(b.y, e.y));
     return make_float2(fmaf(h.x, a.inv_dev_scale, p.x), fmaf(h.y, a.inv_dev_scale, p.y));
 }
 
@@ -387,12 +401,14 @@ __device__ __forceinline__ uint2 fit_odd_fp8(const StepArgs &a, const float (&fr
     return make_uint2(q[0] | (q[1] << 16), q[2]);
 }
 
-// FP16_FIT even part A_k = rho_k (1 - alpha-bar) of a node with colour densities (rr, rb).
-__device__ __forceinline__ float2 fit_even(const StepArgs &a, float rr, float rb) {
-    const float rho = rr + rb, inv_rho = 1.0f / rho;
-    const float phi = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
-    const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
-    const float oma = 1.0f - alpha_bar(a.alpha_mix, rr, rb, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
+// FP16_FIT even part A_k = rho_k (1 - alpha-bar) of a node with colour densities (rr, rb) and
+// order parameter phi (either reading of alpha-bar; one division only for the mass fraction).
+__device__ __forceinline__ float2 fit_even(const StepArgs &a, float rr, float rb, float phi) {
+    float oma;
+    if (a.alpha_mix)
+        oma = (rr * (1.0f - a.alpha_r) + rb * (1.0f - a.alpha_b)) / (rr + rb);
+    else
+        oma = 1.0f - (0.5f * (1.0f + phi) * a.alpha_r + 0.5f * (1.0f - phi) * a.alpha_b);
     return make_float2(rr * oma, rb * oma);
 }
 

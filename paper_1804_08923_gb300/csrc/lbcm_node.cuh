@@ -79,6 +79,36 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
 #pragma unroll
             for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, nb.pulled(i), fr, fb);
         }
+    } else if constexpr (S == STORE_FP16_FIT) {
+        // opposite pulls (i, i+1) were both encoded for this node, with odd terms of opposite
+        // sign: one odd sum and one base product decode the pair
+        const float2 *rest = reinterpret_cast<const float2 *>(a.pin);
+        const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
+        const float2 f0 = __ldg(rest + nb.src(0));
+        fr[0] = f0.x;
+        fb[0] = f0.y;
+#pragma unroll
+        for (int i = 1; i < 27; i += 2) {
+            const float2 hp = __half22float2(__ldg(mov + (size_t)(i - 1) * a.NN + nb.src(i)));
+            const float2 hm = __half22float2(__ldg(mov + (size_t)i * a.NN + nb.src(i + 1)));
+            const float2 b = fit_base(own.A, i), e = fit_odd(a, i, odd_sum(i, own));
+            const float2 pp = make_float2(__fadd_rn(b.x, e.x), __fadd_rn(b.y, e.y));
+            const float2 pm = make_float2(__fsub_rn(b.x, e.x), __fsub_rn(b.y, e.y));
+            fr[i] = fmaf(hp.x, a.inv_dev_scale, pp.x);
+            fb[i] = fmaf(hp.y, a.inv_dev_scale, pp.y);
+            fr[i + 1] = fmaf(hm.x, a.inv_dev_scale, pm.x);
+            fb[i + 1] = fmaf(hm.y, a.inv_dev_scale, pm.y);
+        }
+#pragma unroll
+        for (int i = 1; i < 27; ++i) {
+            if (cz(i) == 1 && lo) {
+                fr[i] = a.zin[zrank(i) * P + nb.pxy];
+                fb[i] = a.zin[(9 + zrank(i)) * P + nb.pxy];
+            } else if (cz(i) == -1 && slip_hi) {
+                fr[i] = a.zout[zrank(i) * P + nb.pxy];
+                fb[i] = a.zout[(9 + zrank(i)) * P + nb.pxy];
+            }
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, i, fr, fb);
