@@ -79,10 +79,9 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
 #pragma unroll
             for (int i = 0; i < 27; ++i) gather_one<S>(a, nb, i, lo, slip_hi, P, own, nb.pulled(i), fr, fb);
         }
-    } else if constexpr (S == STORE_FP16_FIT && !W) {
+    } else if constexpr (S == STORE_FP16_FIT) {
         // opposite pulls (i, i+1) were both encoded for this node, with odd terms of opposite
-        // sign: one odd sum and one base product decode the pair (with side walls the kernel
-        // also holds the reflecting path, and the paired form measured slower there)
+        // sign: one odd sum and one base product decode the pair
         const float2 *rest = reinterpret_cast<const float2 *>(a.pin);
         const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
         const float2 f0 = __ldg(rest + nb.src(0));

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
 
 // --------------------------------------------------------------- phase field (K_A)
 template <int S, bool W>
-__global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
+__device__ __forceinline__ void phase_field_node(const StepArgs &a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -151,6 +151,19 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
         a.ph_cur[nb.n] = make_float4(ph, rr + rb, A.x, A.y);
         a.vp_cur[nb.n] = fit_odd_fp8(a, fr, fb);
     }
+}
+
+// Lattices without side walls (and FP32 with them); and, with separate register bounds, the
+// FP16 encodings on lattices with side walls.  Measured on the 240x240x1200 UT lattice: FP16
+// 1.97 -> 1.80 ms with a one-block bound, FP16_FIT 3.12 -> 2.52 ms with five; FP32 went the
+// other way (2.17 -> 2.69 ms) and keeps the plain bound.
+template <int S, bool W>
+__global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
+    phase_field_node<S, W>(a);
+}
+template <int S>
+__global__ void __launch_bounds__(128, S == STORE_FP16_FIT ? 5 : 1) phase_field_wall_kernel(StepArgs a) {
+    phase_field_node<S, true>(a);
 }
 
 // 1-D shifted moment sweep: values at c = -1, 0, +1 -> central moments of order 0, 1, 2
@@ -492,7 +505,10 @@ static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, l
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
     dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
     if (ev) cudaEventRecord(ev[1], s);
-    phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
+    if constexpr (W && S != STORE_FP32)
+        phase_field_wall_kernel<S><<<grd, blk, 0, s>>>(a);
+    else
+        phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[2], s);
     *launches += 1;
     if (!collide) return;
