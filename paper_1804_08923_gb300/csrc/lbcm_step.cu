@@ -470,8 +470,11 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
 // kRec (FP32, adjoint recompute): also writes the node's collision inputs to a.rec / a.rec4.
+// Blocks per SM (register bound), as measured: FP32 6; FP16 5, or 4 with side walls (UT
+// lattice 6.19 -> 5.97 ms); FP16_FIT 4 (96x96x384 jet 0.374 -> 0.341 ms, UT lattice 8.98 ->
+// 7.49 ms), where 5 blocks spilled 90-160 B.
 template <bool kForce, int S, bool kRec, bool W>
-__global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : 5)) collide_kernel(StepArgs a) {
+__global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : ((W || S == STORE_FP16_FIT) ? 4 : 5))) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
