@@ -22,31 +22,62 @@ __host__ __device__ constexpr int cz(int i) { return (int)((kPackZ >> (2 * i)) &
 __host__ __device__ constexpr int csq(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
 // position of direction i in the 3x3x3 tensor-product array [cx+1][cy+1][cz+1]
 __host__ __device__ constexpr int cell(int i) { return (cx(i) + 1) * 9 + (cy(i) + 1) * 3 + (cz(i) + 1); }
-// direction with c_z flipped (specular reflection on a z wall)
-__host__ __device__ constexpr int mirror_z(int i) {
-    int r = 0;
-    for (int j = 0; j < 27; ++j)
-        if (cx(j) == cx(i) && cy(j) == cy(i) && cz(j) == -cz(i)) r = j;
-    return r;
-}
-// direction with velocity (x, y, z)
-__host__ __device__ constexpr int dir_of(int x, int y, int z) {
+// Inverse maps as packed tables built at compile time, so that a call with a run-time
+// argument (a lane's direction in the boundary kernels) is a shift and a mask, not a loop.
+__host__ __device__ constexpr int dir_search(int x, int y, int z) {
     int r = 0;
     for (int j = 0; j < 27; ++j)
         if (cx(j) == x && cy(j) == y && cz(j) == z) r = j;
     return r;
 }
+// 5-bit direction index of cell (x+1)*9 + (y+1)*3 + (z+1), 12 cells per word
+__host__ __device__ constexpr unsigned long long pack_dirs(int word) {
+    unsigned long long w = 0;
+    for (int k = 0; k < 12; ++k) {
+        const int c = word * 12 + k;
+        if (c < 27) w |= (unsigned long long)dir_search(c / 9 - 1, (c / 3) % 3 - 1, c % 3 - 1) << (5 * k);
+    }
+    return w;
+}
+constexpr unsigned long long kDirOf0 = pack_dirs(0), kDirOf1 = pack_dirs(1), kDirOf2 = pack_dirs(2);
+// direction with velocity (x, y, z)
+__host__ __device__ constexpr int dir_of(int x, int y, int z) {
+    const int c = (x + 1) * 9 + (y + 1) * 3 + (z + 1);
+    const unsigned long long w = c < 12 ? kDirOf0 : (c < 24 ? kDirOf1 : kDirOf2);
+    return (int)((w >> (5 * (c % 12))) & 31ull);
+}
+// direction with c_z flipped (specular reflection on a z wall)
+__host__ __device__ constexpr int mirror_z(int i) { return dir_of(cx(i), cy(i), -cz(i)); }
 // direction i with c_x, c_y or both reversed (specular reflection on a side wall)
 __host__ __device__ constexpr int flip_x(int i) { return dir_of(-cx(i), cy(i), cz(i)); }
 __host__ __device__ constexpr int flip_y(int i) { return dir_of(cx(i), -cy(i), cz(i)); }
 __host__ __device__ constexpr int flip_xy(int i) { return dir_of(-cx(i), -cy(i), cz(i)); }
-// rank of direction i among those with the same c_z = +1 (or -1), 0..8
-__host__ __device__ constexpr int zrank(int i) {
+// rank of direction i among those with the same c_z = +1 (or -1), 0..8; 4 bits per direction
+__host__ __device__ constexpr int zrank_search(int i) {
     int r = 0;
     for (int j = 0; j < i; ++j)
         if (cz(j) == cz(i)) ++r;
     return r;
 }
+__host__ __device__ constexpr unsigned long long pack_zrank(int word) {
+    unsigned long long w = 0;
+    for (int k = 0; k < 16; ++k)
+        if (word * 16 + k < 27) w |= (unsigned long long)zrank_search(word * 16 + k) << (4 * k);
+    return w;
+}
+constexpr unsigned long long kZrank0 = pack_zrank(0), kZrank1 = pack_zrank(1);
+__host__ __device__ constexpr int zrank(int i) {
+    return (int)(((i < 16 ? kZrank0 : kZrank1) >> (4 * (i & 15))) & 15ull);
+}
+// the tables against the searches they replace
+constexpr bool check_tables() {
+    for (int i = 0; i < 27; ++i) {
+        if (dir_of(cx(i), cy(i), cz(i)) != i || zrank(i) != zrank_search(i)) return false;
+        if (cz(mirror_z(i)) != -cz(i) || cx(flip_x(i)) != -cx(i) || cy(flip_y(i)) != -cy(i)) return false;
+    }
+    return true;
+}
+static_assert(check_tables(), "direction tables");
 
 // D3Q27 weights
 __host__ __device__ constexpr float wgt(int i) {
@@ -261,7 +292,7 @@ __device__ __forceinline__ Own own_of(const float4 *ph, const uint2 *vp, int n) 
 // one fixed sequence of operations, so that the writer and the reader get the same bits.  The
 // odd sum c_j . v runs on both colours at once in half precision (a prediction needs no more).
 // Opposite slots share fl(A k_q) and get exactly opposite odd terms (negation is exact), which
-// lets a reader decode a pair of opposite pulls with one odd sum (gather_fit).  The products
+// lets a reader decode a pair of opposite pulls with one odd sum (gather, lbcm_node.cuh).  The products
 // and sums are __fmul_rn / __fadd_rn, which the compiler never contracts into an FMA, so every
 // call site rounds the same way.
 __device__ __forceinline__ __half2 odd_sum(int j, const Own &o) {
