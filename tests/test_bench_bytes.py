@@ -1,0 +1,48 @@
+"""The algorithmic bytes per node update that bench.py's roofline uses follow from the buffer
+layout the library reports (no GPU work): populations read and written once, the phase entry
+written once and read once."""
+import ctypes as C
+
+import pytest
+
+import bench
+
+
+@pytest.fixture(scope="module")
+def abi():
+    import paper_1804_08923_gb300.build as b
+    b.build()
+    from paper_1804_08923_gb300 import _abi
+    return _abi
+
+
+def per_node(abi, storage, n=(64, 32, 48)):
+    g = abi.make_grid(*n, abi.BC_PERIODIC, abi.BC_PERIODIC)
+    p = abi.make_params(dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.1, nu_b=0.1, storage=storage))
+    sizes = (C.c_size_t * abi.MAX_BUFFERS)()
+    cnt = C.c_int32()
+    assert abi.library().lb_buffer_sizes(C.byref(g), C.byref(p), sizes, C.byref(cnt)) == 0
+    nodes = n[0] * n[1] * n[2]
+    # buffers 0 and 1: the two population buffers; buffer 2: the phase entries (one per
+    # population buffer for the FP16 encodings)
+    pop = sizes[0] / nodes
+    phase = sizes[2] / nodes / (1 if storage == abi.STORE_FP32 else 2)
+    return pop, phase
+
+
+def test_step_bytes_match_the_layout(abi):
+    pop, phase = per_node(abi, abi.STORE_FP32)
+    assert (pop, phase) == pytest.approx((216, 8), abs=0.01)
+    assert bench.BYTES_STEP == 2 * pop + 2 * phase
+    assert bench.BYTES_KERNEL["collide_kernel"] == 2 * pop + phase
+    assert bench.BYTES_KERNEL["phase_field_kernel"] == pop + phase
+    pop, phase = per_node(abi, abi.STORE_FP16)
+    assert (pop, phase) == pytest.approx((112, 16), abs=0.01)
+    assert bench.BYTES_STEP_FP16 == 2 * pop + 2 * phase
+    assert bench.BYTES_KERNEL_FP16["collide_kernel"] == 2 * pop + 2 * phase
+    assert bench.BYTES_KERNEL_FP16["phase_field_kernel"] == pop + 2 * phase
+    pop, phase = per_node(abi, abi.STORE_FP16_FIT)
+    assert (pop, phase) == pytest.approx((112, 24), abs=0.01)
+    assert bench.BYTES_STEP_FIT == 2 * pop + 2 * phase
+    assert bench.BYTES_KERNEL_FIT["collide_kernel"] == 2 * pop + 2 * phase
+    assert bench.BYTES_KERNEL_FIT["phase_field_kernel"] == pop + 2 * phase
