@@ -58,7 +58,7 @@ def balls(shape, spec):
     return jet
 
 
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 1, 2])
 def test_balls_with_periodic_wrap(lb, storage):
     jet = balls((20, 18, 37), [((4.2, 5.0, 5.0), 2.6), ((30.0, 12.3, 6.0), 3.1), ((0.4, 9.0, 14.5), 3.4)])
     gpu, ref = both(lb, jet, storage=storage)
