@@ -40,15 +40,15 @@ BYTES_KERNEL = {"collide_kernel": 440, "phase_field_kernel": 224}
 # step 32, write 112; phase field: read 112 + own previous phase 16, write 16.
 BYTES_STEP_FP16 = 112 + 112 + 16 + 16
 BYTES_KERNEL_FP16 = {"collide_kernel": 256, "phase_field_kernel": 144}
-# fitted FP16 encoding: the phase entry grows by the reader's FP8 odd fit (uint2, 8 B) to 24 B
-BYTES_STEP_FIT = 112 + 112 + 24 + 24
-BYTES_KERNEL_FIT = {"collide_kernel": 272, "phase_field_kernel": 160}
+# fitted FP16 encoding: the same bytes (the FP8 odd fit is packed into the 16-byte phase entry)
+BYTES_STEP_FIT = BYTES_STEP_FP16
+BYTES_KERNEL_FIT = dict(BYTES_KERNEL_FP16)
 STORAGE_TEXT = {
     1: "moving populations as half-precision deviations from the reading node's rest equilibrium, "
        "rest population FP32",
     2: "moving populations as half-precision deviations from a prediction of the reading node "
-       "(rho_k (1 - alpha-bar) k_q plus an FP8 least-squares odd fit of its previous gather), rest "
-       "population FP32"}
+       "(rho_k (1 - alpha-bar) k_q plus an FP8 least-squares odd fit of its previous gather, packed "
+       "in its 16-byte phase entry), rest population FP32"}
 
 
 def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,), checkpoint=0):

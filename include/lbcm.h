@@ -76,9 +76,9 @@ typedef struct {
  * each colour's remainder of the moving ones as they are read back, so per-node colour mass
  * is kept to FP32 rounding.  FP16_FIT: the same layout, with the deviation taken from a
  * prediction of the reading node, rho_k (1 - alpha-bar) k_q plus an odd part w_i c_i . v_k
- * fitted to the populations it gathered in the step before (v_k kept in FP8 beside its
- * densities, 8 more bytes per node and phase buffer); about 4x smaller deviations near
- * interfaces, at some extra arithmetic.  Arithmetic is FP32 in all three.  The adjoint needs
+ * fitted to the populations it gathered in the step before (v_k kept in FP8 inside the same
+ * 16-byte phase entry); about 4x smaller deviations near interfaces, at some extra
+ * arithmetic.  Arithmetic is FP32 in all three.  The adjoint needs
  * FP32. */
 typedef enum { LB_STORE_FP32 = 0, LB_STORE_FP16 = 1, LB_STORE_FP16_FIT = 2 } lb_storage;
 

@@ -46,11 +46,10 @@ size_t pop_buffer_bytes(size_t nn, int storage) {
     return storage != LB_STORE_FP32 ? 8 * nn + 4 * 26 * nn : 8 * 27 * nn;
 }
 
-// Bytes of the phase buffer: FP32 float2[NN]; FP16 two float4[NN] (one per population buffer);
-// FP16_FIT also two uint2[NN] of FP8 odd fits.
+// Bytes of the phase buffer: FP32 float2[NN]; either FP16 encoding two float4[NN] (one per
+// population buffer).
 size_t phase_buffer_bytes(size_t nn, int storage) {
-    if (storage == LB_STORE_FP32) return align_up(8 * nn);
-    return 2 * align_up(16 * nn) + (storage == LB_STORE_FP16_FIT ? 2 * align_up(8 * nn) : 0);
+    return storage == LB_STORE_FP32 ? align_up(8 * nn) : 2 * align_up(16 * nn);
 }
 
 struct AuxLayout {
@@ -126,7 +125,6 @@ struct lb_ctx {
     void *pop[2] = {nullptr, nullptr};
     float2 *phase = nullptr;               // FP32: (phi, rho) of the current step
     float4 *ph4[2] = {nullptr, nullptr};   // FP16: (phi, rho, rho_r, rho_b) paired with pop[0], pop[1]
-    uint2 *vp[2] = {nullptr, nullptr};     // FP16_FIT: FP8 odd fits paired with pop[0], pop[1]
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -193,8 +191,8 @@ __device__ __forceinline__ void init_fields_at(const InitArgs &ia, long long n, 
 }
 
 // FP16: phase entries (phi, rho, rho_r, rho_b) of the initial state, which its populations
-// are encoded for.  FP16_FIT: (phi, rho, A_r, A_b) and the odd fit of the node's own initial
-// populations (the same prediction the phase-field pass makes from gathered ones).
+// are encoded for.  FP16_FIT: the packed entry of phi, A, rho and the odd fit of the node's own
+// initial populations (the same prediction the phase-field pass makes from gathered ones).
 template <int S>
 __global__ void init_phase_kernel(InitArgs ia, StepArgs sa) {
     const long long NN = (long long)ia.nx * ia.ny * ia.nz;
@@ -205,8 +203,6 @@ __global__ void init_phase_kernel(InitArgs ia, StepArgs sa) {
         if constexpr (S == STORE_FP16) {
             sa.ph_cur[n] = make_float4(ph, rr + rb, rr, rb);
         } else {
-            const float2 A = fit_even(sa, rr, rb, ph);
-            sa.ph_cur[n] = make_float4(ph, rr + rb, A.x, A.y);
             const float usq = ux * ux + uy * uy + uz * uz;
             float fr[27], fb[27];
 #pragma unroll
@@ -216,7 +212,7 @@ __global__ void init_phase_kernel(InitArgs ia, StepArgs sa) {
                 fr[i] = rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw);
                 fb[i] = rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw);
             }
-            sa.vp_cur[n] = fit_odd_fp8(sa, fr, fb);
+            sa.ph_cur[n] = pack_fit_entry(ph, rr + rb, fit_even(sa, rr, rb, ph), fit_odd_fp8(sa, fr, fb));
         }
     }
 }
@@ -422,13 +418,9 @@ lb_status setup_ctx(lb_ctx *c) {
     c->pop[0] = c->bufs[0];
     c->pop[1] = c->bufs[1];
     if (c->p.storage != LB_STORE_FP32) {
-        const size_t b4 = align_up(16 * (size_t)c->nn), b2 = align_up(8 * (size_t)c->nn);
+        const size_t b4 = align_up(16 * (size_t)c->nn);
         c->ph4[0] = (float4 *)c->bufs[2];
         c->ph4[1] = (float4 *)((char *)c->bufs[2] + b4);
-        if (c->p.storage == LB_STORE_FP16_FIT) {
-            c->vp[0] = (uint2 *)((char *)c->bufs[2] + 2 * b4);
-            c->vp[1] = (uint2 *)((char *)c->bufs[2] + 2 * b4 + b2);
-        }
     } else {
         c->phase = (float2 *)c->bufs[2];
     }
@@ -452,8 +444,6 @@ StepArgs make_args(const lb_ctx *c) {
     a.phase = c->phase;
     a.ph_prev = c->ph4[c->cur];
     a.ph_cur = c->ph4[c->cur ^ 1];
-    a.vp_prev = c->vp[c->cur];
-    a.vp_cur = c->vp[c->cur ^ 1];
     a.hist_in = c->hist[c->hcur];
     a.hist_out = c->hist[c->hcur ^ 1];
     a.zin = c->zin;
@@ -511,8 +501,6 @@ StepArgs state_args(const lb_ctx *c) {
     StepArgs a = make_args(c);
     a.ph_cur = c->ph4[c->cur];
     a.ph_prev = c->ph4[c->cur];
-    a.vp_cur = c->vp[c->cur];
-    a.vp_prev = c->vp[c->cur];
     return a;
 }
 
@@ -699,10 +687,9 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
             fr = stage; fb = stage + c->nn; fu = stage + 2 * c->nn;
         }
     }
-    StepArgs sa = make_args(c);  // cur = 0: the state is written into pop[0] / ph4[0] / vp[0]
+    StepArgs sa = make_args(c);  // cur = 0: the state is written into pop[0] / ph4[0]
     sa.pout = c->pop[0];
     sa.ph_cur = c->ph4[0];
-    sa.vp_cur = c->vp[0];
     InitArgs ia{c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz,
                 a[0], a[1], a[2], a[3], a[4], sa.rho_r0, sa.rho_b0, sa.alpha_r, sa.alpha_b};
     if (c->p.storage == LB_STORE_FP16) {
@@ -858,11 +845,8 @@ struct SaveHeader {
 };
 
 // Checkpoint layout: header, the raw current population buffer (internal storage layout),
-// for FP16 storage the phase entries it was encoded for (FP16_FIT: and their odd fits), then
-// the outflow history plane.
-static size_t shift_bytes(const lb_ctx *c) {
-    return c->p.storage == LB_STORE_FP32 ? 0 : (c->p.storage == LB_STORE_FP16_FIT ? 24 : 16) * (size_t)c->nn;
-}
+// for FP16 storage the phase entries it was encoded for, then the outflow history plane.
+static size_t shift_bytes(const lb_ctx *c) { return c->p.storage == LB_STORE_FP32 ? 0 : 16 * (size_t)c->nn; }
 
 lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     if (!c || !nbytes) return fail(LB_EINVAL, "ctx and nbytes must not be NULL");
@@ -879,10 +863,7 @@ lb_status lb_save(lb_ctx *c, void *buf, size_t *nbytes) {
     std::memcpy(buf, &h, sizeof(h));
     char *p = (char *)buf + sizeof(h);
     LB_CUDA(cudaMemcpyAsync(p, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, c->stream));
-    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->ph4[c->cur], 16 * (size_t)c->nn, cudaMemcpyDeviceToHost, c->stream));
-    if (sb > 16 * (size_t)c->nn)
-        LB_CUDA(cudaMemcpyAsync(p + pb + 16 * (size_t)c->nn, c->vp[c->cur], 8 * (size_t)c->nn, cudaMemcpyDeviceToHost,
-                                c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(p + pb, c->ph4[c->cur], sb, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaMemcpyAsync(p + pb + sb, c->hist[c->hcur], hb, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     *nbytes = total;
@@ -903,10 +884,7 @@ lb_status lb_load(lb_ctx *c, const void *buf, size_t nbytes) {
     c->cur = 0;
     c->hcur = 0;
     LB_CUDA(cudaMemcpyAsync(c->pop[0], p, pb, cudaMemcpyHostToDevice, c->stream));
-    if (sb) LB_CUDA(cudaMemcpyAsync(c->ph4[0], p + pb, 16 * (size_t)c->nn, cudaMemcpyHostToDevice, c->stream));
-    if (sb > 16 * (size_t)c->nn)
-        LB_CUDA(cudaMemcpyAsync(c->vp[0], p + pb + 16 * (size_t)c->nn, 8 * (size_t)c->nn, cudaMemcpyHostToDevice,
-                                c->stream));
+    if (sb) LB_CUDA(cudaMemcpyAsync(c->ph4[0], p + pb, sb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaMemcpyAsync(c->hist[0], p + pb + sb, hb, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = h.step;

@@ -206,9 +206,10 @@ enum { BC_PERIODIC = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_CONVECTIVE = 3 };
 // (rest-equilibrium) part with the mixture's alpha-bar; v_k, the odd part, is the least-squares
 // fit sum_i (f_i^k - w_i c_i . v)^2 -> min over the 26 moving populations the reader gathered
 // in the step before (v_k = 72 sum_i w_i c_i f_i^k, since sum_i w_i^2 c_ix^2 = 1/72), stored
-// as FP8 e4m3 scaled by the power of two S_v.  The phase buffer holds (phi, rho, A_r, A_b) and
-// a uint2 of the six FP8 values; S_h is a power of two that lifts the deviations out of the
-// FP16 subnormal range.  Near an interface the recolouring and the reader-writer density
+// as FP8 e4m3 scaled by the power of two S_v.  The phase entry packs it all into 16 bytes
+// (pack_fit_entry): phi (FP32), (A_r, A_b) as half2, the six FP8 values and rho in half
+// precision (rho enters only the gradient of the Phi correction); S_h is a power of two that
+// lifts the deviations out of the FP16 subnormal range.  Near an interface the recolouring and the reader-writer density
 // difference make h large under the rest shift; the fitted prediction removes most of it.
 enum { STORE_FP32 = 0, STORE_FP16 = 1, STORE_FP16_FIT = 2 };
 
@@ -219,9 +220,7 @@ struct StepArgs {
     float2 *__restrict__ phase;         // FP32 storage: post-stream (phi, rho) of step t+1
     const float4 *__restrict__ ph_prev; // FP16: (phi, rho, rho_r, rho_b) that S(t) was encoded with
     float4 *__restrict__ ph_cur;        // FP16: post-stream (phi, rho, rho_r, rho_b) of step t+1
-                                        // (FP16_FIT: (phi, rho, A_r, A_b))
-    const uint2 *__restrict__ vp_prev;  // FP16_FIT: FP8 odd fits (v_r, v_b) paired with ph_prev
-    uint2 *__restrict__ vp_cur;         // FP16_FIT: FP8 odd fits paired with ph_cur
+                                        // (FP16_FIT: the packed entry of pack_fit_entry)
     const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
     float *__restrict__ hist_out;       // outflow plane f(N, t+1)
     float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]
@@ -271,18 +270,31 @@ __device__ __forceinline__ __half2 fp8x2_to_half2(unsigned int bits) {
     return __half2(h);
 }
 
+// FP16_FIT phase entry, bit fields of a float4: x = phi (FP32); y = (A_r, A_b) as half2;
+// z = FP8 pairs (v_x | v_y << 16); w = FP8 pair v_z | half(rho) << 16.
+__device__ __forceinline__ float4 pack_fit_entry(float phi, float rho, float2 A, uint2 q) {
+    const __half2 Ah = __floats2half2_rn(A.x, A.y);
+    const unsigned int rh = (unsigned int)__half_as_ushort(__float2half_rn(rho));
+    return make_float4(phi, __uint_as_float(*reinterpret_cast<const unsigned int *>(&Ah)), __uint_as_float(q.x),
+                       __uint_as_float((q.y & 0xffffu) | (rh << 16)));
+}
+__device__ __forceinline__ float fit_entry_rho(float4 e) {
+    return __half2float(__ushort_as_half((unsigned short)(__float_as_uint(e.w) >> 16)));
+}
+
 template <int S>
-__device__ __forceinline__ Own own_of(const float4 *ph, const uint2 *vp, int n) {
+__device__ __forceinline__ Own own_of(const float4 *ph, int n) {
     Own o{};
-    if constexpr (S != STORE_FP32) {
+    if constexpr (S == STORE_FP16) {
         const float4 v = __ldg(ph + n);
         o.A = make_float2(v.z, v.w);
-    }
-    if constexpr (S == STORE_FP16_FIT) {
-        const uint2 b = __ldg(vp + n);
-        o.v[0] = fp8x2_to_half2(b.x);
-        o.v[1] = fp8x2_to_half2(b.x >> 16);
-        o.v[2] = fp8x2_to_half2(b.y);
+    } else if constexpr (S == STORE_FP16_FIT) {
+        const float4 v = __ldg(ph + n);
+        const unsigned int y = __float_as_uint(v.y), z = __float_as_uint(v.z), w = __float_as_uint(v.w);
+        o.A = __half22float2(*reinterpret_cast<const __half2 *>(&y));
+        o.v[0] = fp8x2_to_half2(z);
+        o.v[1] = fp8x2_to_half2(z >> 16);
+        o.v[2] = fp8x2_to_half2(w);
     }
     return o;
 }
@@ -378,7 +390,7 @@ __device__ __forceinline__ float2 load_pop_flip(const StepArgs &a, int i, int sr
 // What node n decodes its gathered populations with (the entries S(t) was encoded for).
 template <int S>
 __device__ __forceinline__ Own reader_shift(const StepArgs &a, int n) {
-    return own_of<S>(a.ph_prev, a.vp_prev, n);
+    return own_of<S>(a.ph_prev, n);
 }
 
 // Store populations f of direction i at node n; dest = what the node n + c_i that will read
@@ -413,8 +425,8 @@ __device__ __forceinline__ float2 store_pop(const StepArgs &a, int i, int n, flo
 }
 __device__ __forceinline__ Own no_shift() { return Own{}; }
 
-// FP16_FIT odd fit of one colour's gathered populations, times S_v, packed as FP8 e4m3
-// pairs (red, blue) per axis: bits 0-15 x, 16-31 y, 32-47 z.
+// FP16_FIT odd fit of the gathered populations, times S_v, as FP8 e4m3 pairs (red, blue) per
+// axis: .x = x | y << 16, .y = z.
 __device__ __forceinline__ uint2 fit_odd_fp8(const StepArgs &a, const float (&fr)[27], const float (&fb)[27]) {
     float vr[3] = {0.0f, 0.0f, 0.0f}, vb[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -494,11 +506,11 @@ struct Nbr {
 // What the node that will read direction i from node nb.n decodes with (FP16 encodings).
 template <int S>
 __device__ __forceinline__ Own dest_shift(const StepArgs &a, const Nbr &nb, int i) {
-    return own_of<S>(a.ph_cur, a.vp_cur, nb.nbr(i));
+    return own_of<S>(a.ph_cur, nb.nbr(i));
 }
 
 // Populations (red, blue) of direction i stored at node nb.n, decoded (for FP16 with what
-// the node that reads them decodes with; a.ph_cur / a.vp_cur must pair with a.pin).
+// the node that reads them decodes with; a.ph_cur must pair with a.pin).
 template <int S>
 __device__ __forceinline__ float2 stored_pop(const StepArgs &a, const Nbr &nb, int i) {
     return load_pop<S>(a, i, nb.n, dest_shift<S>(a, nb, i));

@@ -132,10 +132,14 @@ __device__ __forceinline__ void stencil_gradients(const StepArgs &a, const Nbr &
             const float2 v = __ldg(a.phase + nb.nbr(j));
             ph[j] = v.x;
             rh[j] = v.y;
-        } else {
+        } else if constexpr (S == STORE_FP16) {
             const float4 v = __ldg(a.ph_cur + nb.nbr(j));
             ph[j] = v.x;
             rh[j] = v.y;
+        } else {
+            const float4 v = __ldg(a.ph_cur + nb.nbr(j));
+            ph[j] = v.x;
+            rh[j] = fit_entry_rho(v);
         }
         if (cz(j) == -1 && inlet_lo) {
             if (a.disc[nb.yo[1 - cy(j)] + nb.xo[1 - cx(j)]]) {  // z = -1 inside the inlet disc

@@ -147,9 +147,7 @@ __device__ __forceinline__ void phase_field_node(const StepArgs &a) {
     } else if constexpr (S == STORE_FP16) {
         a.ph_cur[nb.n] = make_float4(ph, rr + rb, rr, rb);  // also the FP16 shift densities of S(t+1)
     } else {  // the prediction S(t+1) is encoded against
-        const float2 A = fit_even(a, rr, rb, ph);
-        a.ph_cur[nb.n] = make_float4(ph, rr + rb, A.x, A.y);
-        a.vp_cur[nb.n] = fit_odd_fp8(a, fr, fb);
+        a.ph_cur[nb.n] = pack_fit_entry(ph, rr + rb, fit_even(a, rr, rb, ph), fit_odd_fp8(a, fr, fb));
     }
 }
 

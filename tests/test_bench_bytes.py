@@ -42,7 +42,7 @@ def test_step_bytes_match_the_layout(abi):
     assert bench.BYTES_KERNEL_FP16["collide_kernel"] == 2 * pop + 2 * phase
     assert bench.BYTES_KERNEL_FP16["phase_field_kernel"] == pop + 2 * phase
     pop, phase = per_node(abi, abi.STORE_FP16_FIT)
-    assert (pop, phase) == pytest.approx((112, 24), abs=0.01)
+    assert (pop, phase) == pytest.approx((112, 16), abs=0.01)
     assert bench.BYTES_STEP_FIT == 2 * pop + 2 * phase
     assert bench.BYTES_KERNEL_FIT["collide_kernel"] == 2 * pop + 2 * phase
     assert bench.BYTES_KERNEL_FIT["phase_field_kernel"] == pop + 2 * phase
