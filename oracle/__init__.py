@@ -8,9 +8,11 @@ in ``workloads``.
 The arithmetic lives in ``lbcm_oracle.c`` (plain C, FP64, dense 27x27 matrices, every
 step in the paper's order).  This module compiles it with gcc and wraps it with ctypes.
 
-Parity unpinned: the inlet ghost placement and the clamp of the convective velocity
-(readings R7 and R8 in the C file) are fixed by no closed form or printed value; only
-the uniform-state invariants of the boundary tests constrain them.
+Parity unpinned: the inlet ghost placement (reading R7 in the C file) is fixed by no closed
+form or printed value; only the uniform-state invariants of the boundary tests constrain it.
+The convective outflow (R8) is pinned by the advection equation it discretises (harmonic and
+step responses, tests/test_oracle_outflow.py); its clamp of lambda to [0, 1] under backflow is
+a reading the paper is silent on.
 """
 from __future__ import annotations
 
