@@ -31,15 +31,19 @@ import workloads  # noqa: E402
 
 METRIC = "MLUPS & % HBM peak, FP32 vs FP16-storage at stated error; adjoint/forward ratio"
 # algorithmic bytes per node update (FP32): 54 population reads + 54 writes + rho_r/rho_b
-# write and read; per kernel: collide reads 54 + writes 54 populations + reads its own
-# rho_r, rho_b; the phase-field kernel reads 54 populations and writes rho_r, rho_b.
+# write and read (the method's minimum; the step's two passes also write and read the 48-byte
+# collision moments).  Per kernel: moment_kernel reads 54 populations and writes the 8-byte
+# phase entry and the 48-byte moments; collide_kernel reads the moments and the phase
+# entries of its stencil (8 B per node once cached) and writes 54 populations.
 BYTES_STEP = 448
-BYTES_KERNEL = {"collide_kernel": 440, "phase_field_kernel": 224}
+BYTES_MOMENTS = 48
+BYTES_KERNEL = {"collide_kernel": 216 + 8 + BYTES_MOMENTS, "moment_kernel": 216 + 8 + BYTES_MOMENTS}
 # FP16 storage: 26 half2 (4 B) + one float2 rest (8 B) = 112 B of populations per node; the
-# phase entries are float4 (16 B).  Collide: read 112 + own phase of the previous and current
-# step 32, write 112; phase field: read 112 + own previous phase 16, write 16.
+# phase entries are float4 (16 B).  moment_kernel: read 112 + own previous entry 16, write the
+# entry 16 + moments 48; collide_kernel: read the moments 48 + the stencil's entries 16, write
+# 112.
 BYTES_STEP_FP16 = 112 + 112 + 16 + 16
-BYTES_KERNEL_FP16 = {"collide_kernel": 256, "phase_field_kernel": 144}
+BYTES_KERNEL_FP16 = {"collide_kernel": 112 + 16 + BYTES_MOMENTS, "moment_kernel": 112 + 2 * 16 + BYTES_MOMENTS}
 # fitted FP16 encoding: the same bytes (the FP8 odd fit is packed into the 16-byte phase entry)
 BYTES_STEP_FIT = BYTES_STEP_FP16
 BYTES_KERNEL_FIT = dict(BYTES_KERNEL_FP16)

@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-#define LBCM_ABI_VERSION 1
+#define LBCM_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define LB_API __attribute__((visibility("default")))
@@ -114,9 +114,13 @@ LB_API void lb_params_default(lb_params *p);
 typedef struct lb_ctx lb_ctx;
 
 /* Number and byte sizes of the device buffers a context needs (at most LB_MAX_BUFFERS).
- * Buffer 0 and 1: population ping-pong, 54 * nodes * 4 bytes each; 2: order parameter
- * and total density of the current step; 3: outflow history ping-pong; 4: small tables
- * and reduction partials.  Returns LB_EINVAL for invalid grids or parameters. */
+ * Buffer 0 and 1: population ping-pong (FP32: 54 * nodes * 4 bytes each; FP16 encodings:
+ * 112 bytes per node); 2: order parameter and total density of the step being taken (FP16
+ * encodings: one 16-byte phase entry per node and population buffer); 3: outflow history
+ * ping-pong; 4: small tables and reduction partials; 5: the collision moments of the step
+ * being taken (48 bytes per node: colour densities, mass, momentum and raw second moment,
+ * written by the gather pass and read by the collision).  Returns LB_EINVAL for invalid
+ * grids or parameters. */
 #define LB_MAX_BUFFERS 8
 LB_API lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *sizes_out, int32_t *n_out);
 
@@ -209,7 +213,10 @@ LB_API lb_status lb_load(lb_ctx *ctx, const void *buf, size_t nbytes);
  * at most `capacity` steps (events are created here, not during stepping); capacity 0
  * disables.  lb_profile_read synchronises, writes per-kernel total device milliseconds
  * and launch counts (index LB_KERNEL_*, up to n_kinds entries), and clears the record. */
-enum { LB_KERNEL_BOUNDARY = 0, LB_KERNEL_PHASE_FIELD = 1, LB_KERNEL_COLLIDE = 2, LB_NKERNELS = 3 };
+/* Index 1 is the step's gather pass: moment_kernel with the paper's rates s3..s6 = 1
+ * (phase field and collision moments), phase_field_kernel otherwise. */
+enum { LB_KERNEL_BOUNDARY = 0, LB_KERNEL_GATHER = 1, LB_KERNEL_COLLIDE = 2, LB_NKERNELS = 3,
+       LB_KERNEL_PHASE_FIELD = LB_KERNEL_GATHER };
 LB_API lb_status lb_profile_enable(lb_ctx *ctx, int32_t capacity);
 LB_API lb_status lb_profile_read(lb_ctx *ctx, double *ms, int64_t *launches, int32_t n_kinds);
 

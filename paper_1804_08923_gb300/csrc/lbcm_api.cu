@@ -125,6 +125,7 @@ struct lb_ctx {
     void *pop[2] = {nullptr, nullptr};
     float2 *phase = nullptr;               // FP32: (phi, rho) of the current step
     float4 *ph4[2] = {nullptr, nullptr};   // FP16: (phi, rho, rho_r, rho_b) paired with pop[0], pop[1]
+    float4 *mom = nullptr;                 // collision moments written and read within a step
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -432,6 +433,7 @@ lb_status setup_ctx(lb_ctx *c) {
     c->zin = (float *)(aux + L.zin);
     c->zout = (float *)(aux + L.zout);
     c->partial = (double *)(aux + L.partial);
+    c->mom = (float4 *)c->bufs[5];
     return upload_disc(c);
 }
 
@@ -444,6 +446,7 @@ StepArgs make_args(const lb_ctx *c) {
     a.phase = c->phase;
     a.ph_prev = c->ph4[c->cur];
     a.ph_cur = c->ph4[c->cur ^ 1];
+    a.mom = c->mom;
     a.hist_in = c->hist[c->hcur];
     a.hist_out = c->hist[c->hcur ^ 1];
     a.zin = c->zin;
@@ -555,7 +558,8 @@ lb_status lb_buffer_sizes(const lb_grid *grid, const lb_params *params, size_t *
     sizes_out[2] = phase_buffer_bytes(nn, params->storage);  // phase field
     sizes_out[3] = 2 * align_up(54 * plane * sizeof(float));
     sizes_out[4] = aux_layout(*grid).total;
-    *n_out = 5;
+    sizes_out[5] = align_up(48 * nn);  // collision moments of the step being taken
+    *n_out = 6;
     return LB_OK;
 }
 

@@ -221,6 +221,8 @@ struct StepArgs {
     const float4 *__restrict__ ph_prev; // FP16: (phi, rho, rho_r, rho_b) that S(t) was encoded with
     float4 *__restrict__ ph_cur;        // FP16: post-stream (phi, rho, rho_r, rho_b) of step t+1
                                         // (FP16_FIT: the packed entry of pack_fit_entry)
+    float4 *__restrict__ mom;           // collision moments of step t+1, written by the moment pass
+                                        // and read by the collision: [3][NN] float4
     const float *__restrict__ hist_in;  // outflow plane f(N, t): [2][27][ny][nx]
     float *__restrict__ hist_out;       // outflow plane f(N, t+1)
     float *__restrict__ zin;            // incoming z=0 populations (c_z = +1): [2][9][ny][nx]

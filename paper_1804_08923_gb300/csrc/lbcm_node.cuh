@@ -182,41 +182,48 @@ struct Moments {
     float rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
 };
 
-template <int S, bool W>
-__device__ __forceinline__ void gather_moments(const StepArgs &a, const Nbr &nb, int z, Moments &m) {
-    float rho_r, rho_b, sf = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+// The moments above of gathered populations (fr, fb).  Every step kernel that needs them
+// forms them here, in this one order, so that the moment pass and the adjoint's recompute
+// see the same bits.
+__device__ __forceinline__ void moments_of(const float (&fr)[27], const float (&fb)[27], Moments &m) {
+    float sf, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
-    {
-        float fr[27], fb[27];
-        gather<S, W>(a, nb, z, fr, fb);
-        MassAcc mr, mb;  // the phase-field kernel's association
+    MassAcc mr, mb;  // the phase-field kernel's association
 #pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            mr.add(i, fr[i]);
-            mb.add(i, fb[i]);
-        }
-        rho_r = mr.total();
-        rho_b = mb.total();
-        // opposite pairs (i, i+1): odd moments take the difference, even ones the sum
-        sf = fr[0] + fb[0];
-#pragma unroll
-        for (int i = 1; i < 27; i += 2) {
-            const float fp = fr[i] + fb[i], fm = fr[i + 1] + fb[i + 1];
-            const float s2 = fp + fm, d2 = fp - fm;
-            sf += s2;
-            if (cx(i) > 0) jx += d2; else if (cx(i) < 0) jx -= d2;
-            if (cy(i) > 0) jy += d2; else if (cy(i) < 0) jy -= d2;
-            if (cz(i) > 0) jz += d2; else if (cz(i) < 0) jz -= d2;
-            if (cx(i) != 0) pxx += s2;
-            if (cy(i) != 0) pyy += s2;
-            if (cz(i) != 0) pzz += s2;
-            if (cx(i) * cy(i) > 0) pxy += s2; else if (cx(i) * cy(i) < 0) pxy -= s2;
-            if (cx(i) * cz(i) > 0) pxz += s2; else if (cx(i) * cz(i) < 0) pxz -= s2;
-            if (cy(i) * cz(i) > 0) pyz += s2; else if (cy(i) * cz(i) < 0) pyz -= s2;
-        }
+    for (int i = 0; i < 27; ++i) {
+        mr.add(i, fr[i]);
+        mb.add(i, fb[i]);
     }
+    // opposite pairs (i, i+1): odd moments take the difference, even ones the sum
+    sf = fr[0] + fb[0];
+#pragma unroll
+    for (int i = 1; i < 27; i += 2) {
+        const float fp = fr[i] + fb[i], fm = fr[i + 1] + fb[i + 1];
+        const float s2 = fp + fm, d2 = fp - fm;
+        sf += s2;
+        if (cx(i) > 0) jx += d2; else if (cx(i) < 0) jx -= d2;
+        if (cy(i) > 0) jy += d2; else if (cy(i) < 0) jy -= d2;
+        if (cz(i) > 0) jz += d2; else if (cz(i) < 0) jz -= d2;
+        if (cx(i) != 0) pxx += s2;
+        if (cy(i) != 0) pyy += s2;
+        if (cz(i) != 0) pzz += s2;
+        if (cx(i) * cy(i) > 0) pxy += s2; else if (cx(i) * cy(i) < 0) pxy -= s2;
+        if (cx(i) * cz(i) > 0) pxz += s2; else if (cx(i) * cz(i) < 0) pxz -= s2;
+        if (cy(i) * cz(i) > 0) pyz += s2; else if (cy(i) * cz(i) < 0) pyz -= s2;
+    }
+    m = Moments{mr.total(), mb.total(), sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz};
+}
 
-    m = Moments{rho_r, rho_b, sf, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz};
+// The collision moments of a node as the moment pass stores them: three float4 planes of NN
+// entries, (rho_r, rho_b, sf, jx), (jy, jz, pxx, pyy), (pzz, pxy, pxz, pyz).
+__device__ __forceinline__ void store_moments(float4 *__restrict__ mom, size_t NN, int n, const Moments &m) {
+    mom[n] = make_float4(m.rho_r, m.rho_b, m.sf, m.jx);
+    mom[NN + n] = make_float4(m.jy, m.jz, m.pxx, m.pyy);
+    mom[2 * NN + n] = make_float4(m.pzz, m.pxy, m.pxz, m.pyz);
+}
+__device__ __forceinline__ Moments load_moments(const float4 *__restrict__ mom, size_t NN, int n) {
+    const float4 a = __ldg(mom + n), b = __ldg(mom + NN + n), c = __ldg(mom + 2 * NN + n);
+    return Moments{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 }
 
 }  // namespace lbcm

@@ -5,18 +5,23 @@
 //   1. boundary_plane_kernel  incoming z = 0 populations (inlet disc / free-slip mirror),
 //                             free-slip top, and the convective outflow plane
 //                             f(N, t+1) = [f(N, t) + lambda f(N-1, t+1)] / (1 + lambda)
-//                             (Section IV.A).  One thread per (x, y).
-//   2. phase_field_kernel     pull-gathers the 54 post-stream populations of a node and
-//                             writes its order parameter phi (Eq. order) and total density
-//                             rho (Section II, densities).  One thread per node.
-//   3. collide_kernel         pull-gathers again, takes the isotropic gradients of phi and
-//                             rho from the fields of step 2 (end of Section II), and
+//                             (Section IV.A).  One warp per (x, y) column.
+//   2. moment_kernel          pull-gathers the 54 post-stream populations of a node (the
+//                             step's only gather) and writes its order parameter phi
+//                             (Eq. order) and total density rho (Section II, densities) for
+//                             the gradient stencil, and the 12 moments the collision needs
+//                             (colour densities, mass, momentum, raw second moment).  One
+//                             thread per node.
+//   3. collide_kernel         reads a node's moments, takes the isotropic gradients of phi
+//                             and rho from the fields of step 2 (end of Section II), and
 //                             applies the central-moment collision with the enhanced
 //                             equilibrium and GMRT forcing (Eqs. scoll, EES, Phi, ketF,
 //                             ketFd), the perturbation (Eq. perturb) and the recolouring
 //                             (Eqs. op3r, op3b); writes the 54 post-collision populations
 //                             of the node (pull scheme: streaming happens in the next
 //                             step's gathers).
+// With relaxation rates other than the paper's, step 2 is phase_field_kernel (phase entry
+// only) and step 3 collide_general_kernel, which gathers the populations again.
 //
 // The collision applies T^-1 K T through the tensor-product central moments
 //   kappa_abc = sum_i f_i (c_ix - u_x)^a (c_iy - u_y)^b (c_iz - u_z)^c,  a, b, c in {0,1,2},
@@ -162,6 +167,43 @@ __global__ void __launch_bounds__(128) phase_field_kernel(StepArgs a) {
 template <int S>
 __global__ void __launch_bounds__(128, S == STORE_FP16_FIT ? 5 : 1) phase_field_wall_kernel(StepArgs a) {
     phase_field_node<S, true>(a);
+}
+
+// ------------------------------------------- moment pass (K_A with the paper's rates)
+// With s3 = s4 = s5 = s6 = 1 the collision needs only a node's colour densities, mass,
+// momentum and raw second moment (see the header), so the one pull gather of a step happens
+// here: the node's phase entry (as phase_field_kernel writes it) plus its 12 collision
+// moments go to a.mom, and collide_kernel reads those instead of gathering again.
+template <int S, bool W>
+__device__ __forceinline__ void moment_node(const StepArgs &a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.nx || y >= a.ny) return;
+    const Nbr nb(a, x, y, z);
+    float fr[27], fb[27];
+    gather<S, W>(a, nb, z, fr, fb);
+    Moments mo;
+    moments_of(fr, fb, mo);
+    const float rr = mo.rho_r, rb = mo.rho_b;
+    const float ph = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
+    if constexpr (S == STORE_FP32) {
+        a.phase[nb.n] = make_float2(ph, rr + rb);
+    } else if constexpr (S == STORE_FP16) {
+        a.ph_cur[nb.n] = make_float4(ph, rr + rb, rr, rb);
+    } else {
+        a.ph_cur[nb.n] = pack_fit_entry(ph, rr + rb, fit_even(a, rr, rb, ph), fit_odd_fp8(a, fr, fb));
+    }
+    store_moments(a.mom, (size_t)a.NN, nb.n, mo);
+}
+
+template <int S, bool W>
+__global__ void __launch_bounds__(128) moment_kernel(StepArgs a) {
+    moment_node<S, W>(a);
+}
+template <int S>
+__global__ void __launch_bounds__(128, S == STORE_FP16_FIT ? 5 : 1) moment_wall_kernel(StepArgs a) {
+    moment_node<S, true>(a);
 }
 
 // 1-D shifted moment sweep: values at c = -1, 0, +1 -> central moments of order 0, 1, 2
@@ -467,19 +509,19 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
 }
 
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
+// Reads the node's moments from the moment pass (no population gather), takes the
+// gradients from the 26 neighbours' phase entries and writes the 54 populations.
 // kRec (FP32, adjoint recompute): also writes the node's collision inputs to a.rec / a.rec4.
-// Blocks per SM (register bound), as measured: FP32 6; FP16 5, or 4 with side walls (UT
-// lattice 6.19 -> 5.97 ms); FP16_FIT 4 (96x96x384 jet 0.374 -> 0.341 ms, UT lattice 8.98 ->
-// 7.49 ms), where 5 blocks spilled 90-160 B.
-template <bool kForce, int S, bool kRec, bool W>
-__global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : ((W || S == STORE_FP16_FIT) ? 4 : 5))) collide_kernel(StepArgs a) {
+// Blocks per SM (register bound): FP32 6, FP16 5, FP16_FIT 4 (its encoding needs the most
+// registers).
+template <bool kForce, int S, bool kRec>
+__global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : (S == STORE_FP16 ? 5 : 4))) collide_kernel(StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
     const Nbr nb(a, x, y, z);
-    Moments mo;
-    gather_moments<S, W>(a, nb, z, mo);
+    const Moments mo = load_moments(a.mom, (size_t)a.NN, nb.n);
     float gpx, gpy, gpz, grx, gry, grz;
     stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
     if constexpr (kRec) {
@@ -506,10 +548,19 @@ static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, l
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
     dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
     if (ev) cudaEventRecord(ev[1], s);
-    if constexpr (W && S != STORE_FP32)
-        phase_field_wall_kernel<S><<<grd, blk, 0, s>>>(a);
-    else
-        phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
+    // pass 1: the step's pull gather (phase field, and the collision moments when the paper's
+    // rates let the collision work from them)
+    if (paper_rates) {
+        if constexpr (W && S != STORE_FP32)
+            moment_wall_kernel<S><<<grd, blk, 0, s>>>(a);
+        else
+            moment_kernel<S, W><<<grd, blk, 0, s>>>(a);
+    } else {
+        if constexpr (W && S != STORE_FP32)
+            phase_field_wall_kernel<S><<<grd, blk, 0, s>>>(a);
+        else
+            phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
+    }
     if (ev) cudaEventRecord(ev[2], s);
     *launches += 1;
     if (!collide) return;
@@ -517,13 +568,13 @@ static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, l
     if (!paper_rates)
         collide_general_kernel<S, W><<<grd, blk, 0, s>>>(a);
     else if (rec && force)
-        collide_kernel<true, S, S == STORE_FP32, W><<<grd, blk, 0, s>>>(a);
+        collide_kernel<true, S, S == STORE_FP32><<<grd, blk, 0, s>>>(a);
     else if (rec)
-        collide_kernel<false, S, S == STORE_FP32, W><<<grd, blk, 0, s>>>(a);
+        collide_kernel<false, S, S == STORE_FP32><<<grd, blk, 0, s>>>(a);
     else if (force)
-        collide_kernel<true, S, false, W><<<grd, blk, 0, s>>>(a);
+        collide_kernel<true, S, false><<<grd, blk, 0, s>>>(a);
     else
-        collide_kernel<false, S, false, W><<<grd, blk, 0, s>>>(a);
+        collide_kernel<false, S, false><<<grd, blk, 0, s>>>(a);
     if (ev) cudaEventRecord(ev[3], s);
     *launches += 1;
 }

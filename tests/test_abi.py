@@ -54,7 +54,8 @@ def test_buffer_sizes_and_validation(lib):
     n = C.c_int32()
     assert lib.lb_buffer_sizes(C.byref(g), C.byref(p), sizes, C.byref(n)) == 0
     nodes = 96 * 96 * 384
-    assert n.value == 5 and sizes[0] >= 54 * 4 * nodes and sizes[1] == sizes[0] and sizes[2] >= 8 * nodes
+    assert n.value == 6 and sizes[0] >= 54 * 4 * nodes and sizes[1] == sizes[0] and sizes[2] >= 8 * nodes
+    assert sizes[5] >= 48 * nodes  # the collision moments written and read within a step
     assert all(int(sizes[j]) % 256 == 0 for j in range(n.value))
     # FP16 storage: 112 B per node per population buffer; the phase buffer holds two float4
     # entries per node (the fitted encoding packs its FP8 fit into them)

@@ -24,25 +24,23 @@ def per_node(abi, storage, n=(64, 32, 48)):
     assert abi.library().lb_buffer_sizes(C.byref(g), C.byref(p), sizes, C.byref(cnt)) == 0
     nodes = n[0] * n[1] * n[2]
     # buffers 0 and 1: the two population buffers; buffer 2: the phase entries (one per
-    # population buffer for the FP16 encodings)
+    # population buffer for the FP16 encodings); buffer 5: the collision moments
     pop = sizes[0] / nodes
     phase = sizes[2] / nodes / (1 if storage == abi.STORE_FP32 else 2)
-    return pop, phase
+    mom = sizes[5] / nodes
+    return pop, phase, mom
 
 
 def test_step_bytes_match_the_layout(abi):
-    pop, phase = per_node(abi, abi.STORE_FP32)
-    assert (pop, phase) == pytest.approx((216, 8), abs=0.01)
+    pop, phase, mom = per_node(abi, abi.STORE_FP32)
+    assert (pop, phase, mom) == pytest.approx((216, 8, 48), abs=0.01)
     assert bench.BYTES_STEP == 2 * pop + 2 * phase
-    assert bench.BYTES_KERNEL["collide_kernel"] == 2 * pop + phase
-    assert bench.BYTES_KERNEL["phase_field_kernel"] == pop + phase
-    pop, phase = per_node(abi, abi.STORE_FP16)
-    assert (pop, phase) == pytest.approx((112, 16), abs=0.01)
-    assert bench.BYTES_STEP_FP16 == 2 * pop + 2 * phase
-    assert bench.BYTES_KERNEL_FP16["collide_kernel"] == 2 * pop + 2 * phase
-    assert bench.BYTES_KERNEL_FP16["phase_field_kernel"] == pop + 2 * phase
-    pop, phase = per_node(abi, abi.STORE_FP16_FIT)
-    assert (pop, phase) == pytest.approx((112, 16), abs=0.01)
-    assert bench.BYTES_STEP_FIT == 2 * pop + 2 * phase
-    assert bench.BYTES_KERNEL_FIT["collide_kernel"] == 2 * pop + 2 * phase
-    assert bench.BYTES_KERNEL_FIT["phase_field_kernel"] == pop + 2 * phase
+    assert bench.BYTES_KERNEL["collide_kernel"] == pop + phase + mom
+    assert bench.BYTES_KERNEL["moment_kernel"] == pop + phase + mom
+    for st, step, kern in ((abi.STORE_FP16, bench.BYTES_STEP_FP16, bench.BYTES_KERNEL_FP16),
+                           (abi.STORE_FP16_FIT, bench.BYTES_STEP_FIT, bench.BYTES_KERNEL_FIT)):
+        pop, phase, mom = per_node(abi, st)
+        assert (pop, phase, mom) == pytest.approx((112, 16, 48), abs=0.01)
+        assert step == 2 * pop + 2 * phase
+        assert kern["collide_kernel"] == pop + phase + mom
+        assert kern["moment_kernel"] == pop + 2 * phase + mom
