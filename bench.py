@@ -1,14 +1,17 @@
 """Benchmark of the D3Q27 colour-gradient central-moment LB step on GB300.
 
-One "step" is one full time step of the method over the whole lattice (boundary planes,
-phase field, fused collide-perturb-recolour with pull streaming).  The default workload
-is the 96x96x384 liquid-liquid jet (D = 16, u = 0.05, gamma = 1.5, Re = 2000, We = 100,
-1% inlet noise, convective outflow), FP32 populations; its 1.53 GB state is larger than
-the 129 MB L2, so no flush is needed between steps.
+One "step" is one full time step of the method over the whole lattice: the boundary planes,
+the gather pass (pull streaming, phase field, collision moments) and the collision pass
+(gradients, central-moment collision, perturbation, recolouring).  The default workload is
+the high-Re jet on 256x256x1024 (67 M nodes; D = 32, u = 0.04, gamma = 2, Re = 1e5,
+We = 1000, Fr = 100 with gravity along +z, 0.5% inlet noise, convective outflow), FP32
+populations as the headline, with both half-precision storages on the same lattice beside
+it; the 29 GB state is far larger than the 129 MB L2, so no flush is needed between steps.
 
 Prints one JSON line.  With torchrun (N > 1 ranks) every rank advances its own replica of
 the lattice (weak scaling; there is no data exchange), times are maxed over ranks.
 --impl reference times the FP64 CPU oracle on the host cores instead.
+--only-main times the headline loop alone (the command the ncu summaries are taken with).
 """
 from __future__ import annotations
 
@@ -19,7 +22,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -55,6 +57,244 @@ STORAGE_TEXT = {
        "in its 16-byte phase entry), rest population FP32"}
 
 
+
+STORAGE_NAMES = {0: "fp32", 1: "fp16", 2: "fp16_fit"}
+BYTES = {0: (BYTES_STEP, BYTES_KERNEL), 1: (BYTES_STEP_FP16, BYTES_KERNEL_FP16), 2: (BYTES_STEP_FIT, BYTES_KERNEL_FIT)}
+
+
+def init_state(lat, cfg):
+    lat.init_jet() if cfg["init"]["kind"] == "jet" else lat.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
+
+
+def with_storage(params, storage):
+    return dict(params, storage=storage)
+
+
+def timed_steps(lat, steps, torch, barrier=None):
+    """Device milliseconds of `steps` lb_step calls between CUDA events on the library's stream."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    (barrier or torch.cuda.synchronize)()
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    (barrier or torch.cuda.synchronize)()
+    return e0.elapsed_time(e1)
+
+
+def kernel_profile(lat, steps, nodes, storage, peak, cfg_name):
+    """Per-kernel device times from a second pass (events around each launch on the stream),
+    with each kernel's achieved algorithmic GB/s; the roofline entry is the kernel with the
+    largest share of the step."""
+    lat.profile_enable(steps)
+    lat.step(steps)
+    prof = lat.profile_read()
+    lat.profile_enable(0)
+    _, bk = BYTES[storage]
+    total = max(sum(v[0] for v in prof.values()), 1e-30)
+    kernels = {}
+    for name, (t, n) in prof.items():
+        if not n:
+            continue
+        k = {"avg_ms": t / n, "launches": n, "share": t / total}
+        if name in bk:
+            k["algorithmic_bytes_per_node"] = bk[name]
+            k["achieved_gbs"] = bk[name] * nodes / (t / n * 1e-3) / 1e9
+        kernels[name] = k
+    top = max((k for k in kernels if k in bk), key=lambda k: kernels[k]["share"])
+    tag = STORAGE_NAMES[storage]
+    traffic = profile_traffic(top if storage == 0 else f"{top}_{tag}", cfg_name)
+    achieved = kernels[top]["achieved_gbs"]
+    roofline = {"bound": "hbm", "kernel": top if storage == 0 else f"{top}<{tag}>", "achieved": achieved,
+                "peak": peak[0], "unit": "GB/s", "frac": achieved / peak[0], "peak_source": f"hbm_gbs of {peak[1]}",
+                "algorithmic_bytes_per_node": bk[top],
+                "traffic": traffic * 1.0 if traffic is not None else None,
+                "traffic_per_node": traffic / nodes if traffic is not None else None}
+    return kernels, roofline
+
+
+def storage_leg(lb, torch, cfg, storage, steps, warmup, peak, world, max_over_ranks, barrier):
+    """MLUPS, per-kernel times and the dominant kernel's roofline of one storage."""
+    nodes = int(np.prod(cfg["grid"]))
+    lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], storage), bc=cfg["bc"])
+    init_state(lat, cfg)
+    lat.step(warmup)
+    ms = max_over_ranks(timed_steps(lat, steps, torch, barrier))
+    kernels, roofline = kernel_profile(lat, steps, nodes, storage, peak, cfg["name"])
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    bs, _ = BYTES[storage]
+    v = job_mlups(nodes, steps, world, ms)
+    return {"value": v, "unit": "MLUPS", "ms_per_step": ms / steps, "steps": steps,
+            "storage": STORAGE_TEXT.get(storage, "fp32 populations"), "bytes_per_node_algorithmic": bs,
+            "hbm_pct_of_peak": 100.0 * v * 1e6 * bs / (peak[0] * 1e9) / world,
+            "roofline": roofline, "kernels": kernels}
+
+
+def error_vs_fp32(lb, torch, cfg, checkpoints):
+    """Both half-precision storages against FP32 on the same workload, stepped in lockstep:
+    relative L2 error of the velocity and the largest change of the order parameter at each
+    checkpoint step."""
+    lats = {s: lb.Lattice(cfg["grid"], with_storage(cfg["params"], s), bc=cfg["bc"]) for s in (0, 1, 2)}
+    for l in lats.values():
+        init_state(l, cfg)
+    out = {STORAGE_NAMES[s]: [] for s in (1, 2)}
+    done = 0
+    for cp in checkpoints:
+        for l in lats.values():
+            l.step(cp - done)
+        done = cp
+        F = {s: l.fields(names=("phi", "ux", "uy", "uz")) for s, l in lats.items()}
+        u32 = torch.stack([F[0][k] for k in ("ux", "uy", "uz")]).double()
+        for s in (1, 2):
+            du = torch.stack([F[s][k] - F[0][k] for k in ("ux", "uy", "uz")]).double()
+            out[STORAGE_NAMES[s]].append({"steps": cp, "rel_u_l2": float(du.norm() / u32.norm()),
+                                          "max_abs_dphi": float((F[s]["phi"] - F[0]["phi"]).abs().max())})
+        del F
+    for l in lats.values():
+        l.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def mass_drift_leg(lb, torch, name, steps_by_storage):
+    """MLUPS and the FP64 per-colour mass change over a run, per storage, on a large jet (blue
+    has neither source nor sink until the inlet's pressure wave reaches the outflow, so its
+    change is the storage's drift; red grows by the inlet flux)."""
+    cfg = workloads.CONFIGS[name]
+    nodes = int(np.prod(cfg["grid"]))
+    out = {"workload": cfg["text"], "nodes": nodes}
+    for s, steps in steps_by_storage.items():
+        lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], s), bc=cfg["bc"])
+        init_state(lat, cfg)
+        m0 = lat.mass()
+        ms = timed_steps(lat, steps, torch)
+        m1 = lat.mass()
+        out[STORAGE_NAMES[s]] = {"steps": steps, "value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                                 "ms_per_step": ms / steps, "mass_start": m0.tolist(), "mass_end": m1.tolist(),
+                                 "blue_rel_drift": float((m1[1] - m0[1]) / m0[1]),
+                                 "red_gain_per_step": float((m1[0] - m0[0]) / steps),
+                                 "device_gb": sum(b.numel() for b in lat._bufs) / 1e9}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    p = cfg["params"]
+    out["red_inflow_per_step_nominal"] = float(np.pi * (p["d_in"] / 2) ** 2 * p["u_in"] * p["rho_r0"])
+    return out
+
+
+def oracle_error_leg(lb, torch, steps=100):
+    """Every storage against the FP64 oracle on the 48x48x192 jet (D = 8, the 96x96x384
+    jet's lattice parameters): relative L2 error of the velocity and max |d phi| after
+    `steps` steps."""
+    import oracle
+    cfg = workloads.scaled_jet("jet96", 48, 48, 192, D=8)
+    nx, ny, nz = cfg["grid"]
+    t0 = time.perf_counter()
+    ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *cfg["bc"]), oracle.make_params(cfg["params"]))
+    ref.init_jet()
+    ref.step(steps)
+    R = ref.fields()
+    oracle_s = time.perf_counter() - t0
+    out = {"workload": "jet 48x48x192, D=8, the 96x96x384 jet's lattice parameters", "steps": steps,
+           "oracle_seconds": oracle_s, "oracle_cores": oracle.num_threads()}
+    un = np.linalg.norm(R["u"])
+    for s in (0, 1, 2):
+        lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], s), bc=cfg["bc"])
+        lat.init_jet()
+        lat.step(steps)
+        F = lat.fields(device=False)
+        du = np.stack([F[k].astype(np.float64) - R["u"][d] for d, k in enumerate(("ux", "uy", "uz"))])
+        out[STORAGE_NAMES[s]] = {"rel_u_l2": float(np.linalg.norm(du) / un),
+                                 "max_abs_dphi": float(np.abs(F["phi"] - R["phi"]).max())}
+        lat.close()
+    return out
+
+
+def fragments_leg(lb, torch):
+    """lb_fragments on a broken-up state: 1500 seeded random droplets (radii 1.5-4.5) on the
+    96x96x384 lattice, timed with CUDA events on the library's stream (the call also
+    allocates its scratch, sorts the kept fragments on the host and synchronises; its host
+    wall time is reported too)."""
+    cfg = workloads.CONFIGS["jet96"]
+    nx, ny, nz = cfg["grid"]
+    rr, rb, u = workloads.random_droplet_fields((nz, ny, nx), 1500, 1.5, 4.5, 7, 1.0, cfg["params"]["rho_b0"])
+    lat = lb.Lattice(cfg["grid"], cfg["params"], bc=(0, 0))
+    lat.init_fields(rr, rb, u)
+    lat.fragments(6, exclude_inlet=False)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(lat.stream)
+    fr = lat.fragments(6, exclude_inlet=False)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3
+    lat.close()
+    return {"state": "1500 random droplets, radii 1.5-4.5, 96x96x384 periodic", "connectivity": 6,
+            "n_fragments": int(len(fr["roots"])), "total_volume": fr["total_volume"],
+            "mass_median_diameter": fr["mass_median_diameter"], "device_ms": e0.elapsed_time(e1), "wall_ms": wall}
+
+
+def oracle_slab(cfg, seconds):
+    """An oracle lattice on a z-slab of the workload's lattice, deep enough for about
+    `seconds` of FP64 work per step, with the workload's boundaries and parameters."""
+    import oracle
+    nx, ny, nz = cfg["grid"]
+    probe = oracle.Lattice(oracle.make_grid(nx, ny, 4, *cfg["bc"]), oracle.make_params(cfg["params"]))
+    init_state(probe, cfg)
+    t0 = time.perf_counter()
+    probe.step(1)
+    rate = nx * ny * 4 / (time.perf_counter() - t0)
+    nzs = int(max(4, min(nz, rate * seconds / (nx * ny))))
+    lat = oracle.Lattice(oracle.make_grid(nx, ny, nzs, *cfg["bc"]), oracle.make_params(cfg["params"]))
+    init_state(lat, cfg)
+    return lat, nzs
+
+
+def cpu_baseline(cfg, seconds_target=15.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample of the
+    workload: whole oracle steps of a z-slab of the lattice (same boundaries and parameters)."""
+    import oracle
+    nx, ny, nz = cfg["grid"]
+    lat, nzs = oracle_slab(cfg, seconds_target / 4)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds_target and steps < 1000:
+        lat.step(1)
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": nx * ny * nzs * steps / el / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{steps} FP64 oracle step(s) of a {nx}x{ny}x{nzs} slab of the {nx}x{ny}x{nz} "
+                                        f"lattice, same boundaries and parameters ({el:.1f} s)"}
+
+
+def run_reference(args, cfg):
+    """Reference arm: the FP64 oracle on the host cores, timed on bounded samples of the
+    workload (a z-slab of the lattice with the same boundaries and parameters)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    nx, ny, nz = cfg["grid"]
+    # slab depth sized so that W + K oracle steps take about two minutes
+    lat, nzs = oracle_slab(cfg, 120.0 / max(1, args.steps + args.warmup))
+    lat.step(args.warmup)
+    t0 = time.perf_counter()
+    lat.step(args.steps)
+    el = time.perf_counter() - t0
+    v = nx * ny * nzs * args.steps / el / 1e6
+    sample = f"{nx}x{ny}x{nzs} slab of the {nx}x{ny}x{nz} lattice, same boundaries and parameters"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(cfg, 0),
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,), checkpoint=0):
     """Cost of lb_adjoint (T steps forward with ceil(sqrt T) checkpoints, objective, reverse
     sweep) against lb_step(T) from the same state, both timed with CUDA events."""
@@ -88,26 +328,6 @@ def adjoint_leg(lb, torch, name="jet64", T=500, objective="area", args=(1e-3,), 
             "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
             "work": "T forward steps with checkpoints + T recomputed forward steps + T reverse steps",
             "precision": "FP32 kernels, FP64 parameter-gradient accumulation"}
-
-
-def fp16_error(lb, cfg, steps, storage=1):
-    """FP16 (either encoding) against FP32 storage on the same workload after `steps` steps:
-    relative L2 error of the velocity and largest change of the order parameter."""
-    import torch
-    out = {}
-    lats = [lb.Lattice(cfg["grid"], dict(cfg["params"], storage=s), bc=cfg["bc"]) for s in (0, storage)]
-    for l in lats:
-        l.init_jet() if cfg["init"]["kind"] == "jet" else l.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
-        l.step(steps)
-    F = [l.fields(names=("phi", "ux", "uy", "uz")) for l in lats]
-    du = torch.stack([F[1][k] - F[0][k] for k in ("ux", "uy", "uz")]).double()
-    u32 = torch.stack([F[0][k] for k in ("ux", "uy", "uz")]).double()
-    out = {"steps": steps, "rel_u_l2": float(du.norm() / u32.norm()),
-           "max_abs_dphi": float((F[1]["phi"] - F[0]["phi"]).abs().max())}
-    for l in lats:
-        l.close()
-    torch.cuda.empty_cache()
-    return out
 
 
 def measured_peaks():
@@ -195,62 +415,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_baseline(cfg, seconds_target=15.0):
-    """The FP64 oracle as it stands, on the host cores, over a bounded sample of the
-    workload: whole oracle steps of the full lattice from the workload's initial state."""
-    import oracle
-    nx, ny, nz = cfg["grid"]
-    lat = oracle.Lattice(oracle.make_grid(nx, ny, nz, *cfg["bc"]), oracle.make_params(cfg["params"]))
-    lat.init_jet() if cfg["init"]["kind"] == "jet" else lat.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
-    t0 = time.perf_counter()
-    lat.step(1)
-    steps = 1
-    el = time.perf_counter() - t0
-    while el + el / steps < seconds_target:
-        lat.step(1)
-        steps += 1
-        el = time.perf_counter() - t0
-    el = time.perf_counter() - t0
-    return {"value": nx * ny * nz * steps / el / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"{steps} full FP64 oracle step(s) of the {nx}x{ny}x{nz} lattice "
-                                        f"({el:.1f} s)"}
-
-
-def run_reference(args, cfg):
-    """Reference arm: the FP64 oracle on the host cores, timed on bounded samples of the
-    workload (a z-slab of the lattice with the same boundaries and parameters)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    import oracle
-    nx, ny, nz = cfg["grid"]
-    # slab depth sized so that W + K oracle steps take about two minutes
-    probe = oracle.Lattice(oracle.make_grid(nx, ny, 4, *cfg["bc"]), oracle.make_params(cfg["params"]))
-    probe.init_jet()
-    t0 = time.perf_counter()
-    probe.step(1)
-    rate = nx * ny * 4 / (time.perf_counter() - t0)
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    nzs = int(max(3, min(nz, rate * budget / (nx * ny))))
-    lat = oracle.Lattice(oracle.make_grid(nx, ny, nzs, *cfg["bc"]), oracle.make_params(cfg["params"]))
-    lat.init_jet()
-    lat.step(args.warmup)
-    t0 = time.perf_counter()
-    lat.step(args.steps)
-    el = time.perf_counter() - t0
-    nodes = nx * ny * nzs
-    v = nodes * args.steps / el / 1e6
-    sample = f"{nx}x{ny}x{nzs} slab of the {nx}x{ny}x{nz} lattice, same boundaries and parameters"
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(cfg),
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 def reduce_max(v, dist, device):
     """Largest value over the ranks (the slowest rank times the job); identity without a group."""
     if dist is None or not dist.is_initialized():
@@ -266,26 +430,31 @@ def job_mlups(nodes_per_rank, steps, world, ms_max):
     return nodes_per_rank * steps * world / (ms_max * 1e-3) / 1e6
 
 
-def config_block(cfg):
+def config_block(cfg, storage):
     nx, ny, nz = cfg["grid"]
     return {"workload": f"{cfg['name']}: {cfg['text']}", "lattice": [nx, ny, nz], "nodes": nx * ny * nz,
-            "storage": "fp32 SoA populations [k][i][z][y][x]",
-            "l2": "state 2 x 54 x 4 B x nodes > 129 MB L2; no flush between steps",
+            "storage": {0: "fp32 SoA populations [i][z][y][x] of (red, blue) pairs"}.get(storage, STORAGE_TEXT.get(storage)),
+            "l2": "state >> 129 MB L2 (every population is read and written once per step); no flush between steps",
             "parallelism": "one lattice per GPU (replicas, no exchange)"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="jet96")
+    ap.add_argument("--config", default="jet256")
+    ap.add_argument("--storage", type=int, default=0, choices=[0, 1, 2],
+                    help="storage of the headline loop (0 FP32, 1 FP16, 2 FP16_FIT)")
+    ap.add_argument("--only-main", action="store_true", help="the headline loop alone (ncu summaries)")
+    ap.add_argument("--error-steps", default="100,500,2000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
-    ap.add_argument("--error-steps", type=int, default=500)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-paper-workload", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 384x384x1536 mass-drift leg")
+    ap.add_argument("--no-oracle-error", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint leg (lb_adjoint against lb_step on the 64x64x256 jet)")
     ap.add_argument("--adjoint-steps", type=int, default=500)
@@ -314,11 +483,6 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    nx, ny, nz = cfg["grid"]
-    nodes = nx * ny * nz
-    lat = lb.Lattice(cfg["grid"], cfg["params"], bc=cfg["bc"])
-    lat.init_jet() if cfg["init"]["kind"] == "jet" else lat.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
-    stream = lat.stream
 
     def barrier():
         torch.cuda.synchronize()
@@ -328,6 +492,14 @@ def main():
 
     def max_over_ranks(v):
         return reduce_max(v, dist, "cuda")
+
+    nx, ny, nz = cfg["grid"]
+    nodes = nx * ny * nz
+    peak = measured_peaks()
+    st = args.storage
+    lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], st), bc=cfg["bc"])
+    init_state(lat, cfg)
+    stream = lat.stream
 
     # ---- warm-up, then the timed region (device events on the library's stream)
     lat.step(args.warmup)
@@ -344,80 +516,33 @@ def main():
     ms_step = ms / args.steps
     value = job_mlups(nodes, args.steps, world, ms)
     clocks = clk.summary()
+    bytes_step, _ = BYTES[st]
+    kernels, roofline = kernel_profile(lat, args.steps, nodes, st, peak, cfg["name"])
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if st == 0 else "f32 arithmetic, f16 population storage",
+            "data": "synthetic", "config": config_block(cfg, st),
+            "hbm_pct_of_peak": 100.0 * value * 1e6 * bytes_step / (peak[0] * 1e9) / world,
+            "bytes_per_node_algorithmic": bytes_step,
+            "bytes_per_node_design": 2 * BYTES[st][1]["collide_kernel"] if st == 0 else
+            BYTES[st][1]["collide_kernel"] + BYTES[st][1]["moment_kernel"],
+            "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
+    if args.only_main:
+        lat.close()
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
-    # ---- per-kernel durations over a second timed pass of the same length
-    lat.profile_enable(args.steps)
-    barrier()
-    lat.step(args.steps)
-    prof = lat.profile_read()
-    lat.profile_enable(0)
-    peak, peak_kind = measured_peaks()
-    k_ms, k_n = prof["collide_kernel"]
-    coll_ms = k_ms / max(k_n, 1)
-    achieved = BYTES_KERNEL["collide_kernel"] * nodes / (coll_ms * 1e-3) / 1e9
-    traffic = profile_traffic("collide_kernel", cfg["name"])
-    kernels = {name: {"avg_ms": t / max(n, 1), "launches": n,
-                      "share": t / max(sum(v[0] for v in prof.values()), 1e-30)} for name, (t, n) in prof.items() if n}
-    roofline = {"bound": "hbm", "kernel": "collide_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                "algorithmic_bytes_per_node": BYTES_KERNEL["collide_kernel"],
-                "traffic": traffic * 1.0 if traffic is not None else None}
-
-    # ---- the same workload with the paper's free-slip side walls (Section IV.A) in place of
-    #      periodic x and y: throughput only
-    sw = lb.Lattice(cfg["grid"], cfg["params"], bc=tuple(cfg["bc"])[:2] + (1, 1))
-    sw.init_jet() if cfg["init"]["kind"] == "jet" else sw.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
-    sw.step(args.warmup)
-    sw_steps = min(args.steps, 500)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    s0.record(sw.stream)
-    sw.step(sw_steps)
-    s1.record(sw.stream)
-    barrier()
-    sw_ms = max_over_ranks(s0.elapsed_time(s1))
-    side_walls = {"value": job_mlups(nodes, sw_steps, world, sw_ms), "unit": "MLUPS", "steps": sw_steps,
-                  "ms_per_step": sw_ms / sw_steps, "boundaries": "free-slip walls at x and y (Section IV.A)"}
-    sw.close()
-    del sw
-
-    # ---- the paper's own workload: UT Case 1 (240x240x1200 melt jet, free-slip side walls,
-    #      gravity), whose 20 000 iterations the paper reports as about 32 hours
-    paper = None
-    if world == 1 and not args.no_paper_workload:
-        ucfg = workloads.CONFIGS["ut1"]
-        un = int(np.prod(ucfg["grid"]))
-        ut = lb.Lattice(ucfg["grid"], ucfg["params"], bc=ucfg["bc"])
-        ut.init_jet()
-        ut.step(args.warmup)
-        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        u0.record(ut.stream)
-        ut.step(200)
-        u1.record(ut.stream)
-        torch.cuda.synchronize()
-        ums = u0.elapsed_time(u1)
-        paper = {"workload": ucfg["text"], "nodes": un, "steps": 200, "value": un * 200 / (ums * 1e-3) / 1e6,
-                 "unit": "MLUPS", "ms_per_step": ums / 200, "hours_for_20000_steps": ums / 200 * 20000 / 3.6e6,
-                 "paper": "about 32 h for 20 000 iterations on unstated hardware: 12 MLUPS for the 69.12 M nodes "
-                          "of this lattice (1.2 MLUPS for the 6.912 M nodes the text prints)"}
-        ut.close()
-        del ut
-        torch.cuda.empty_cache()
-
-    # ---- fragment analysis of the state the timed steps reached (lb_fragments, Section IV.B)
-    fr_t0 = time.perf_counter()
-    frag = lat.fragments(6)
-    fr_ms = (time.perf_counter() - fr_t0) * 1e3
-    fragments = {"connectivity": 6, "n_fragments": int(len(frag["roots"])),
-                 "column_volume": frag["column_volume"], "mass_median_diameter": frag["mass_median_diameter"],
-                 "wall_ms": fr_ms, "state": f"after {args.warmup + 2 * args.steps} steps of the workload"}
-
-    # ---- end to end through the public API with host buffers
-    rr = torch.zeros(cfg["grid"][::-1], dtype=torch.float32).pin_memory()
-    rb = torch.full(cfg["grid"][::-1], cfg["params"]["rho_b0"], dtype=torch.float32).pin_memory()
-    uu = torch.zeros((3,) + tuple(cfg["grid"][::-1]), dtype=torch.float32).pin_memory()
-    outs = {k: torch.empty(cfg["grid"][::-1], dtype=torch.float32).pin_memory() for k in ("rho_r", "rho_b", "ux", "uy", "uz")}
+    # ---- end to end through the public API with host buffers: host fields -> lb_init,
+    #      K x lb_step, lb_fields -> host (pinned), all inside the timed region
+    shp = cfg["grid"][::-1]
+    rr = torch.zeros(shp, dtype=torch.float32).pin_memory()
+    rb = torch.full(shp, cfg["params"]["rho_b0"], dtype=torch.float32).pin_memory()
+    uu = torch.zeros((3,) + tuple(shp), dtype=torch.float32).pin_memory()
+    outs = {k: torch.empty(shp, dtype=torch.float32).pin_memory() for k in ("rho_r", "rho_b", "ux", "uy", "uz")}
     barrier()
     t0 = time.perf_counter()
     lat.init_fields(rr.numpy(), rb.numpy(), uu.numpy())
@@ -427,65 +552,76 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     h2d = 5 * 4 * nodes
     d2h = 4 * nodes * len(got)
-    e2e = {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "job": f"host fields -> lb_init, {args.steps} x lb_step, lb_fields -> host (pinned)"}
+    line["e2e"] = {"value": nodes * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+                   "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                   "job": f"host fields -> lb_init, {args.steps} x lb_step, lb_fields -> host (pinned)"}
+    lat.close()
+    del lat, rr, rb, uu, outs
+    torch.cuda.empty_cache()
 
-    # ---- FP16 storage (both encodings) on the same workload: throughput, roofline, error vs FP32
-    def fp16_leg(storage, bytes_step, bytes_kernel, tag):
-        h = lb.Lattice(cfg["grid"], dict(cfg["params"], storage=storage), bc=cfg["bc"])
-        h.init_jet() if cfg["init"]["kind"] == "jet" else h.init_droplet(cfg["init"]["R"], cfg["init"]["W"])
-        h.step(args.warmup)
-        barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(h.stream)
-        h.step(args.steps)
-        f1.record(h.stream)
-        barrier()
-        ms16 = max_over_ranks(f0.elapsed_time(f1))
-        h.profile_enable(args.steps)
-        h.step(args.steps)
-        p16 = h.profile_read()
-        h.profile_enable(0)
-        c_ms = p16["collide_kernel"][0] / max(p16["collide_kernel"][1], 1)
-        h.close()
-        del h
-        torch.cuda.empty_cache()
-        achieved = bytes_kernel["collide_kernel"] * nodes / (c_ms * 1e-3) / 1e9
-        return {"value": nodes * args.steps * world / (ms16 * 1e-3) / 1e6, "unit": "MLUPS",
-                "ms_per_step": ms16 / args.steps, "storage": STORAGE_TEXT[storage],
-                "bytes_per_node_algorithmic": bytes_step,
-                "roofline": {"bound": "hbm", "kernel": f"collide_kernel<{tag}>", "achieved": achieved,
-                             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                             "algorithmic_bytes_per_node": bytes_kernel["collide_kernel"], "traffic": None},
-                "kernels": {name: {"avg_ms": t / max(n, 1), "launches": n} for name, (t, n) in p16.items() if n},
-                "error_vs_fp32": fp16_error(lb, cfg, args.error_steps, storage)}
-
-    fp16 = fit = None
+    # ---- the other storages on the same lattice, and their error against FP32
     if not args.no_fp16:
-        lat.close()
-        del lat
-        torch.cuda.empty_cache()
-        fp16 = fp16_leg(1, BYTES_STEP_FP16, BYTES_KERNEL_FP16, "fp16")
-        fit = fp16_leg(2, BYTES_STEP_FIT, BYTES_KERNEL_FIT, "fp16_fit")
+        for s in (0, 1, 2):
+            if s != st:
+                line[f"{STORAGE_NAMES[s]}_storage"] = storage_leg(lb, torch, cfg, s, args.steps, args.warmup, peak,
+                                                                  world, max_over_ranks, barrier)
+        cps = [int(v) for v in args.error_steps.split(",") if v.strip()]
+        if cps:
+            line["error_vs_fp32"] = error_vs_fp32(lb, torch, cfg, cps)
+            line["error_vs_fp32"]["note"] = ("velocity relative L2 and max |d phi| against FP32 on the same "
+                                             "lattice; by step 2000 the high-Re jet is chaotic and the two "
+                                             "runs diverge on their own")
 
-    if rank == 0:
-        base = None
-        adjoint = None
-        if world == 1 and not args.no_adjoint:
+    # ---- the paper's free-slip side walls (Section IV.A) in place of periodic x and y
+    sw = lb.Lattice(cfg["grid"], cfg["params"], bc=tuple(cfg["bc"])[:2] + (1, 1))
+    init_state(sw, cfg)
+    sw.step(args.warmup)
+    sw_ms = max_over_ranks(timed_steps(sw, args.steps, torch, barrier))
+    line["side_walls"] = {"value": job_mlups(nodes, args.steps, world, sw_ms), "unit": "MLUPS",
+                          "steps": args.steps, "ms_per_step": sw_ms / args.steps,
+                          "boundaries": "free-slip walls at x and y (Section IV.A)"}
+    sw.close()
+    del sw
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1:
+        # ---- the 96x96x384 jet (FP32), a smaller lattice of the same kind
+        if args.config != "jet96":
+            line["jet96"] = storage_leg(lb, torch, workloads.CONFIGS["jet96"], 0, max(args.steps, 100), args.warmup,
+                                        peak, 1, lambda v: v, None)
+        # ---- the 384x384x1536 atomisation jet: throughput and FP64 colour-mass drift
+        if not args.no_large:
+            line["jet384"] = mass_drift_leg(lb, torch, "jet384", {0: 300, 1: 1000, 2: 1000})
+        # ---- the paper's own workload: UT Case 1 (240x240x1200 melt jet, free-slip side
+        #      walls, gravity), whose 20 000 iterations the paper reports as about 32 hours
+        if not args.no_paper_workload:
+            ucfg = workloads.CONFIGS["ut1"]
+            un = int(np.prod(ucfg["grid"]))
+            ut = lb.Lattice(ucfg["grid"], ucfg["params"], bc=ucfg["bc"])
+            ut.init_jet()
+            ut.step(args.warmup)
+            ums = timed_steps(ut, 200, torch)
+            line["paper_workload"] = {
+                "workload": ucfg["text"], "nodes": un, "steps": 200, "value": un * 200 / (ums * 1e-3) / 1e6,
+                "unit": "MLUPS", "ms_per_step": ums / 200, "hours_for_20000_steps": ums / 200 * 20000 / 3.6e6,
+                "paper": "about 32 h for 20 000 iterations on unstated hardware: 12 MLUPS for the 69.12 M nodes "
+                         "of this lattice (1.2 MLUPS for the 6.912 M nodes the text prints)"}
+            ut.close()
+            del ut
+            torch.cuda.empty_cache()
+        # ---- fragment analysis (Section IV.B) of a broken-up state
+        line["fragments"] = fragments_leg(lb, torch)
+        # ---- adjoint against forward cost
+        if not args.no_adjoint:
             adjoint = adjoint_leg(lb, torch, T=args.adjoint_steps, checkpoint=args.adjoint_checkpoint)
-        if world == 1 and not args.no_cpu_baseline:
-            base = cpu_baseline(cfg)
-        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_block(cfg),
-                "hbm_pct_of_peak": 100.0 * value * 1e6 * BYTES_STEP / (peak * 1e9) / world,
-                "bytes_per_node_algorithmic": BYTES_STEP,
-                "roofline": roofline, "kernels": kernels, "cpu_baseline": base, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks,
-                "fp16_storage": fp16, "fp16_fit_storage": fit, "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None,
-                "adjoint": adjoint, "fragments": fragments, "side_walls": side_walls,
-                "paper_workload": paper}
+            line["adjoint"] = adjoint
+            line["adjoint_forward_ratio"] = adjoint["ratio"]
+        # ---- error of every storage against the FP64 oracle
+        if not args.no_oracle_error:
+            line["error_vs_oracle"] = oracle_error_leg(lb, torch)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

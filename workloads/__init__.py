@@ -138,3 +138,27 @@ def shear_wave_fields(shape, u0, rho_r=1.0, rho_b=0.0):
     u = np.zeros((3,) + shape)
     u[0] = u0 * np.sin(2 * np.pi * y / ny)
     return (np.full(shape, rho_r, dtype=np.float64), np.full(shape, rho_b, dtype=np.float64), u)
+
+
+def random_droplet_fields(shape, n, r_min, r_max, seed, rho_r0=1.0, rho_b0=1.0, phi_abs=0.9):
+    """Seeded broken-up state: n red balls with radii uniform in [r_min, r_max) at uniform
+    random centres (distances wrap periodically in x, y and z; overlapping balls merge) in
+    blue.  Binarised like a settled interface: phi = +phi_abs inside, -phi_abs outside, so
+    (rho_r, rho_b) = ((1 + phi)/2 rho_r0, (1 - phi)/2 rho_b0), at rest.  shape = (nz, ny, nx);
+    returns float32 rho_r, rho_b, u (3, nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    red = np.zeros(shape, dtype=bool)
+    for _ in range(n):
+        c = rng.uniform(0.0, 1.0, 3) * np.array([nx, ny, nz])
+        r = rng.uniform(r_min, r_max)
+        k = int(np.ceil(r))
+        ax = [(np.arange(int(np.floor(c[d])) - k, int(np.floor(c[d])) + k + 2)) for d in range(3)]
+        dx, dy, dz = (ax[d] - c[d] for d in range(3))
+        inside = (dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2) < r * r
+        iz, iy, ix = np.nonzero(inside)
+        red[ax[2][iz] % nz, ax[1][iy] % ny, ax[0][ix] % nx] = True
+    phi = np.where(red, phi_abs, -phi_abs)
+    rho_r = (0.5 * rho_r0 * (1.0 + phi)).astype(np.float32)
+    rho_b = (0.5 * rho_b0 * (1.0 - phi)).astype(np.float32)
+    return rho_r, rho_b, np.zeros((3,) + shape, dtype=np.float32)
