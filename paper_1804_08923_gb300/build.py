@@ -24,6 +24,8 @@ def flags(verbose_ptxas: bool = False):
          "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"), "-I", CSRC] + ARCH
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]
+    # extra nvcc options for tuning builds (e.g. -DLBCM_ADJ_MIN_BLOCKS=4); empty by default
+    f += os.environ.get("LBCM_NVCC_EXTRA", "").split()
     return f
 
 

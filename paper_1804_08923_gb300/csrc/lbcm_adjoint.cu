@@ -172,13 +172,10 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
 
     // ---- the forward step's collision inputs of this node (recorded in the recompute)
     const size_t NN = (size_t)a.NN;
-    const float4 r0 = __ldg(g.rec + nb.n), r1 = __ldg(g.rec + NN + nb.n), r2 = __ldg(g.rec + 2 * NN + nb.n),
-                 r3 = __ldg(g.rec + 3 * NN + nb.n);
-    Moments mo;
-    mo.rho_r = r0.x; mo.rho_b = r0.y; mo.jx = r0.z; mo.jy = r0.w;
-    mo.jz = r1.x; mo.pxx = r1.y; mo.pyy = r1.z; mo.pzz = r1.w;
-    mo.pxy = r2.x; mo.pxz = r2.y; mo.pyz = r2.z;
-    const float gpx = r2.w, gpy = r3.x, gpz = r3.y, grx = r3.z, gry = r3.w, grz = __ldg(g.rec4 + nb.n);
+    const Moments mo = load_moments(g.mom, NN, nb.n);
+    const float4 r3 = __ldg(g.grad4 + nb.n);
+    const float2 r4 = __ldg(g.grad2 + nb.n);
+    const float gpx = r3.x, gpy = r3.y, gpz = r3.z, grx = r3.w, gry = r4.x, grz = r4.y;
     const float rr = mo.rho_r, rb = mo.rho_b;
     const float rho = rr + rb, inv_rho = 1.0f / rho;
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
@@ -522,8 +519,8 @@ __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g)
         lrho = fmaf(w3, cxj * A.w + cyj * B.x + czj * B.y, lrho);
     }
     float phv, S_;  // phi and rho_r/rho_r0 + rho_b/rho_b0 of this node
-    if (g.rec) {
-        const float4 r0 = __ldg(g.rec + nb.n);
+    if (g.mom) {
+        const float4 r0 = __ldg(g.mom + nb.n);  // (rho_r, rho_b, sf, jx)
         phv = order_parameter(r0.x, r0.y, a.inv_rho_r0, a.inv_rho_b0);
         S_ = r0.x * a.inv_rho_r0 + r0.y * a.inv_rho_b0;
     } else {

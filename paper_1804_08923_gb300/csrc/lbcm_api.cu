@@ -142,9 +142,10 @@ struct lb_ctx {
         void *base = nullptr;
         size_t bytes = 0;
         float2 *ckpt_pop = nullptr, *seg_pop = nullptr, *lp[2] = {}, *lr[2] = {}, *lgb = nullptr, *objph = nullptr;
-        float *ckpt_hist = nullptr, *seg_rec4 = nullptr, *seg_fm = nullptr, *seg_hist = nullptr, *lc = nullptr,
-              *li = nullptr, *lh[2] = {};
-        float4 *lga = nullptr, *seg_rec = nullptr;
+        float *ckpt_hist = nullptr, *seg_fm = nullptr, *seg_hist = nullptr, *lc = nullptr, *li = nullptr,
+              *lh[2] = {};
+        float4 *lga = nullptr, *seg_mom = nullptr, *seg_g4 = nullptr;
+        float2 *seg_g2 = nullptr;
         double *acc_coll = nullptr, *acc_inlet = nullptr, *acc_obj = nullptr, *out = nullptr;
         long long nblk_coll = 0, nblk_inlet = 0;
         int cl = 0;
@@ -961,12 +962,14 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     const size_t pb = 27 * NN * sizeof(float2), hb = 54 * P * sizeof(float), nb2 = NN * sizeof(float2);
     StepArgs a0 = make_args(c);
     const long long nblk_coll = adj_collide_blocks(a0), nblk_inlet = adj_boundary_blocks(a0);
-    // per recomputed step: the collision inputs (68 B a node), f(N-1) and hist(n+1) of the
-    // outflow plane; the populations themselves only in two alternating buffers
-    const size_t parts[] = {nseg * pb, nseg * hb, 2 * pb, k * 4 * NN * sizeof(float4), k * NN * sizeof(float),
-                            k * hb, (k + 1) * hb, pb, pb, nb2, nb2, NN * sizeof(float4), nb2,
+    // per recorded step: the collision inputs (the moment pass's 48 B and the 24 B of gradients
+    // a node), f(N-1) and hist(n+1) of the outflow plane; the populations themselves only in
+    // two alternating buffers
+    const size_t parts[] = {nseg * pb, nseg * hb, 2 * pb, k * 3 * NN * sizeof(float4), k * NN * sizeof(float4),
+                            k * nb2, k * hb, (k + 1) * hb, pb, pb, nb2, nb2, NN * sizeof(float4), nb2,
                             hb, 9 * P * sizeof(float), hb, hb, nblk_coll * 3 * sizeof(double),
                             nblk_inlet * 17 * sizeof(double), nblk_coll * sizeof(double), 32 * sizeof(double), nb2};
+    constexpr int kParts = (int)(sizeof(parts) / sizeof(parts[0]));
     size_t need = 0;
     for (size_t v : parts) need += align_up(v);
     if (need > c->adj.bytes) {
@@ -984,16 +987,16 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
         char *p = (char *)c->adj.base;
         size_t j = 0;
         auto take = [&](void *&dst) { dst = p; p += align_up(parts[j++]); };
-        void *v[22];
-        for (int q = 0; q < 22; ++q) take(v[q]);
+        void *v[kParts];
+        for (int q = 0; q < kParts; ++q) take(v[q]);
         auto &w = c->adj;
         w.ckpt_pop = (float2 *)v[0]; w.ckpt_hist = (float *)v[1]; w.seg_pop = (float2 *)v[2];
-        w.seg_rec = (float4 *)v[3]; w.seg_rec4 = (float *)v[4]; w.seg_fm = (float *)v[5];
-        w.seg_hist = (float *)v[6]; w.lp[0] = (float2 *)v[7]; w.lp[1] = (float2 *)v[8]; w.lr[0] = (float2 *)v[9];
-        w.lr[1] = (float2 *)v[10]; w.lga = (float4 *)v[11]; w.lgb = (float2 *)v[12]; w.lc = (float *)v[13];
-        w.li = (float *)v[14]; w.lh[0] = (float *)v[15]; w.lh[1] = (float *)v[16]; w.acc_coll = (double *)v[17];
-        w.acc_inlet = (double *)v[18]; w.acc_obj = (double *)v[19]; w.out = (double *)v[20];
-        w.objph = (float2 *)v[21];
+        w.seg_mom = (float4 *)v[3]; w.seg_g4 = (float4 *)v[4]; w.seg_g2 = (float2 *)v[5]; w.seg_fm = (float *)v[6];
+        w.seg_hist = (float *)v[7]; w.lp[0] = (float2 *)v[8]; w.lp[1] = (float2 *)v[9]; w.lr[0] = (float2 *)v[10];
+        w.lr[1] = (float2 *)v[11]; w.lga = (float4 *)v[12]; w.lgb = (float2 *)v[13]; w.lc = (float *)v[14];
+        w.li = (float *)v[15]; w.lh[0] = (float *)v[16]; w.lh[1] = (float *)v[17]; w.acc_coll = (double *)v[18];
+        w.acc_inlet = (double *)v[19]; w.acc_obj = (double *)v[20]; w.out = (double *)v[21];
+        w.objph = (float2 *)v[22];
         w.nblk_coll = nblk_coll;
         w.nblk_inlet = nblk_inlet;
     }
@@ -1009,20 +1012,37 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     LB_CUDA(cudaMemsetAsync(w.lc, 0, hb, st));
     LB_CUDA(cudaMemsetAsync(w.li, 0, 9 * P * sizeof(float), st));
 
-    // forward pass with a checkpoint at the start of every segment
+    // what the reverse needs of step t of a segment: the collision inputs, f(N-1) and the
+    // outflow history before and after the step
+    auto record = [&](StepArgs &a, long long t) {
+        a.hist_in = w.seg_hist + t * 54 * P;
+        a.hist_out = w.seg_hist + (t + 1) * 54 * P;
+        a.mom = w.seg_mom + t * 3 * NN;
+        a.grad4 = w.seg_g4 + t * NN;
+        a.grad2 = w.seg_g2 + t * NN;
+        a.fm_out = conv ? w.seg_fm + t * 54 * P : nullptr;
+    };
+    // forward pass with a checkpoint at the start of every segment; the last segment records
+    // as it goes, so the reverse sweep needs no recompute for it
     const int64_t step0 = c->step;
     for (long long sg = 0; sg < nseg; ++sg) {
         LB_CUDA(cudaMemcpyAsync(w.ckpt_pop + sg * 27 * NN, c->pop[c->cur], pb, cudaMemcpyDeviceToDevice, st));
         if (conv)
             LB_CUDA(cudaMemcpyAsync(w.ckpt_hist + sg * 54 * P, c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
         const long long len = std::min<long long>(k, T - sg * k);
+        const bool last = sg == nseg - 1;
+        if (last) LB_CUDA(cudaMemcpyAsync(w.seg_hist, c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
         for (long long t = 0; t < len; ++t) {
-            cudaError_t e = launch_step(make_args(c), LB_STORE_FP32, st, nullptr, &c->launches);
+            StepArgs a = make_args(c);
+            if (last) record(a, t);
+            cudaError_t e = launch_step(a, LB_STORE_FP32, st, nullptr, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "launch_step");
             c->cur ^= 1;
-            if (conv) c->hcur ^= 1;
+            if (conv && !last) c->hcur ^= 1;
             c->step += 1;
         }
+        if (last && conv)
+            LB_CUDA(cudaMemcpyAsync(c->hist[c->hcur], w.seg_hist + len * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
     }
 
     // objective of S(T) and its adjoint
@@ -1039,33 +1059,34 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
         if (e != cudaSuccess) return cuda_fail(e, "launch_objective");
     }
 
-    // reverse sweep: recompute each segment from its checkpoint, then step back through it
-    // step t of a segment: populations alternate between two buffers; the phase field and the
-    // boundary planes are the context's scratch; what the reverse needs is kept per step
+    // reverse sweep: recompute each segment from its checkpoint (the last one was recorded by
+    // the forward pass), then step back through it.  Step t of a segment: populations alternate
+    // between two buffers; the phase field and the boundary planes are the context's scratch;
+    // what the reverse needs is kept per step
     auto seg_args = [&](long long t, int64_t step) {
         StepArgs a = make_args(c);
         a.pin = w.seg_pop + (t & 1) * 27 * NN;
         a.pout = w.seg_pop + ((t + 1) & 1) * 27 * NN;
-        a.hist_in = w.seg_hist + t * 54 * P;
-        a.hist_out = w.seg_hist + (t + 1) * 54 * P;
-        a.rec = w.seg_rec + t * 4 * NN;
-        a.rec4 = w.seg_rec4 + t * NN;
-        a.fm_out = conv ? w.seg_fm + t * 54 * P : nullptr;
+        record(a, t);
         a.step = step;
         return a;
     };
     for (long long sg = nseg - 1; sg >= 0; --sg) {
         const long long n0 = sg * k, len = std::min<long long>(k, T - n0);
-        LB_CUDA(cudaMemcpyAsync(w.seg_pop, w.ckpt_pop + sg * 27 * NN, pb, cudaMemcpyDeviceToDevice, st));
-        if (conv) LB_CUDA(cudaMemcpyAsync(w.seg_hist, w.ckpt_hist + sg * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
-        for (long long t = 0; t < len; ++t) {
-            cudaError_t e = launch_step(seg_args(t, step0 + n0 + t), LB_STORE_FP32, st, nullptr, &c->launches);
-            if (e != cudaSuccess) return cuda_fail(e, "launch_step (recompute)");
+        if (sg != nseg - 1) {
+            LB_CUDA(cudaMemcpyAsync(w.seg_pop, w.ckpt_pop + sg * 27 * NN, pb, cudaMemcpyDeviceToDevice, st));
+            if (conv)
+                LB_CUDA(cudaMemcpyAsync(w.seg_hist, w.ckpt_hist + sg * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
+            for (long long t = 0; t < len; ++t) {
+                cudaError_t e = launch_step(seg_args(t, step0 + n0 + t), LB_STORE_FP32, st, nullptr, &c->launches);
+                if (e != cudaSuccess) return cuda_fail(e, "launch_step (recompute)");
+            }
         }
         for (long long t = len - 1; t >= 0; --t) {
             AdjArgs gs = g;
-            gs.rec = w.seg_rec + t * 4 * NN;
-            gs.rec4 = w.seg_rec4 + t * NN;
+            gs.mom = w.seg_mom + t * 3 * NN;
+            gs.grad4 = w.seg_g4 + t * NN;
+            gs.grad2 = w.seg_g2 + t * NN;
             gs.fm = w.seg_fm + t * 54 * P;
             gs.lp_in = w.lp[cl]; gs.lr_in = w.lr[cl];
             gs.lp_out = w.lp[cl ^ 1]; gs.lr_out = w.lr[cl ^ 1];

@@ -243,12 +243,12 @@ struct StepArgs {
     float dev_scale, inv_dev_scale;     // FP16_FIT: S_h, 1/S_h (powers of two)
     float v_scale;                      // FP16_FIT: S_v (power of two)
     float fourier[16];                  // inlet profile coefficients a_1, b_1, ..., a_8, b_8
-    // optional outputs for the adjoint's recompute (NULL otherwise): the collision inputs of
-    // every node, rec[0..3][NN] = (rho_r, rho_b, jx, jy), (jz, Pxx, Pyy, Pzz), (Pxy, Pxz, Pyz,
-    // gpx), (gpy, gpz, grx, gry) and rec4[NN] = grz; fm_out[2][27][nx ny] = f(N-1, t+1) of the
-    // outflow columns
-    float4 *__restrict__ rec;
-    float *__restrict__ rec4;
+    // optional outputs for the adjoint's recompute (NULL otherwise): the gradients of every
+    // node, grad4[NN] = (gpx, gpy, gpz, grx) and grad2[NN] = (gry, grz) (with the moments the
+    // moment pass writes to mom, the collision's inputs); fm_out[2][27][nx ny] = f(N-1, t+1) of
+    // the outflow columns
+    float4 *__restrict__ grad4;
+    float2 *__restrict__ grad2;
     float *__restrict__ fm_out;
     unsigned long long seed;
     long long step;  // index of the step being taken (state t -> t+1 uses t)

@@ -22,11 +22,14 @@ cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEven
 //   lh_in / lh_out  lambda of the outflow history hist(n+1) / hist(n) [54][nx ny]
 //   acc_coll        FP64 per-block sums of dJ/d(sigma, nu_r, nu_b) [blocks][3]
 //   acc_inlet       FP64 per-block sums of dJ/d(u_in, a_1, b_1, ..., a_8, b_8) [blocks][17]
-//   rec, rec4       the forward step's collision inputs per node (as StepArgs::rec, rec4)
+//   mom             the forward step's collision moments per node, [3][NN] float4 as the moment
+//                   pass writes them: (rho_r, rho_b, sf, jx), (jy, jz, pxx, pyy), (pzz, pxy, pxz, pyz)
+//   grad4, grad2    its gradients per node (as StepArgs::grad4, grad2)
 //   fm              the forward step's f(N-1) of the outflow columns [54][nx ny]
 struct AdjArgs {
-    const float4 *rec;
-    const float *rec4, *fm;
+    const float4 *mom, *grad4;
+    const float2 *grad2;
+    const float *fm;
     const float2 *lp_in, *lr_in;
     float2 *lp_out, *lr_out;
     float4 *lga;
@@ -41,7 +44,8 @@ struct AdjArgs {
 long long adj_collide_blocks(const StepArgs &a);
 long long adj_boundary_blocks(const StepArgs &a);
 // Reverse of the step described by a (hist_in / hist_out as the forward step n wrote them;
-// its populations are not read: g.rec and g.fm hold what the reverse needs of step n).
+// its populations are not read: g.mom, g.grad4, g.grad2 and g.fm hold what the reverse needs of
+// step n).
 cudaError_t launch_adjoint_step(const StepArgs &a, const AdjArgs &g, cudaStream_t s, long long *launches);
 // Objective of the state a.pin (0 interface area, args[0] = eps; 1 penetration length,
 // args[0] = delta): scalar[0] = J; writes lambda_S(T) into g.lp_out / g.lr_out.

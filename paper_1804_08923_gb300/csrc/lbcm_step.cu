@@ -511,7 +511,8 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
 // -------- collide, perturb, recolour (K_B) with the paper's rates s3 = s4 = s5 = s6 = 1
 // Reads the node's moments from the moment pass (no population gather), takes the
 // gradients from the 26 neighbours' phase entries and writes the 54 populations.
-// kRec (FP32, adjoint recompute): also writes the node's collision inputs to a.rec / a.rec4.
+// kRec (FP32, adjoint recompute): also writes the node's gradients to a.grad4 / a.grad2 (its
+// moments are already in a.mom).
 // Blocks per SM (register bound): FP32 6, FP16 5, FP16_FIT 4 (its encoding needs the most
 // registers).
 template <bool kForce, int S, bool kRec>
@@ -525,12 +526,8 @@ __global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : (S == STORE_FP16 ?
     float gpx, gpy, gpz, grx, gry, grz;
     stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
     if constexpr (kRec) {
-        const size_t NN = (size_t)a.NN;
-        a.rec[nb.n] = make_float4(mo.rho_r, mo.rho_b, mo.jx, mo.jy);
-        a.rec[NN + nb.n] = make_float4(mo.jz, mo.pxx, mo.pyy, mo.pzz);
-        a.rec[2 * NN + nb.n] = make_float4(mo.pxy, mo.pxz, mo.pyz, gpx);
-        a.rec[3 * NN + nb.n] = make_float4(gpy, gpz, grx, gry);
-        a.rec4[nb.n] = grz;
+        a.grad4[nb.n] = make_float4(gpx, gpy, gpz, grx);
+        a.grad2[nb.n] = make_float2(gry, grz);
     }
     collide_from_moments<kForce, S>(a, nb, mo, gpx, gpy, gpz, grx, gry, grz);
 }
@@ -564,7 +561,7 @@ static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, l
     if (ev) cudaEventRecord(ev[2], s);
     *launches += 1;
     if (!collide) return;
-    const bool rec = S == STORE_FP32 && a.rec != nullptr;  // paper rates only (adjoint)
+    const bool rec = S == STORE_FP32 && a.grad4 != nullptr;  // paper rates only (adjoint)
     if (!paper_rates)
         collide_general_kernel<S, W><<<grd, blk, 0, s>>>(a);
     else if (rec && force)
