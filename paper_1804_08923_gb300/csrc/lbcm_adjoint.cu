@@ -490,6 +490,42 @@ __global__ void __launch_bounds__(128, LBCM_ADJ_MIN_BLOCKS) adj_collide_kernel(S
 // node x on z = 0 (z = N) reads y through the mirror ghost with c_j's z component flipped,
 // except inside the inlet disc, where the ghost is a constant.  Same for rho.  Then
 // lambda_rho_k(y) = lambda_phi dphi/drho_k + lambda_rho.
+// The 52 neighbour loads are issued in two batches of 13 neighbours before they are used (the
+// loop with a use after every load kept few loads in flight and stalled on each); planes away
+// from z walls take the stencil's signs at compile time.
+template <bool W, bool kZWall>
+__device__ __forceinline__ void adj_stencil_sums(const StepArgs &a, const AdjArgs &g, const Nbr &nb, int z,
+                                                 float &lphi, float &lrho) {
+    const int N = a.nz - 1;
+    const bool pz = a.bc_zlo == BC_PERIODIC;
+    const bool lo_const = kZWall && !pz && z == 0 && a.bc_zlo == BC_INLET && a.disc[nb.pxy];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float4 A[13];
+        float2 B[13];
+#pragma unroll
+        for (int q = 0; q < 13; ++q) {
+            const int src = nb.src(1 + 13 * h + q);  // clamped onto the wall layer: the mirrored reader
+            A[q] = __ldg(g.lga + src);
+            B[q] = __ldg(g.lgb + src);
+        }
+#pragma unroll
+        for (int q = 0; q < 13; ++q) {
+            const int j = 1 + 13 * h + q;
+            const bool below = kZWall && !pz && z == 0 && cz(j) == 1;   // x = y - c_j would sit on z = -1
+            const bool above = kZWall && !pz && z == N && cz(j) == -1;  // ... on z = N + 1
+            // beyond a wall the reader is on this layer and reached y through its mirror ghost
+            // with that component of c reversed
+            const float czj = (below || above) ? -(float)cz(j) : (float)cz(j);
+            const float cxj = W && nb.fx(j) ? -(float)cx(j) : (float)cx(j);
+            const float cyj = W && nb.fy(j) ? -(float)cy(j) : (float)cy(j);
+            const float w3 = (below && lo_const) ? 0.0f : 3.0f * wgt(j);  // the disc ghost is a constant
+            lphi = fmaf(w3, cxj * A[q].x + cyj * A[q].y + czj * A[q].z, lphi);
+            lrho = fmaf(w3, cxj * A[q].w + cyj * B[q].x + czj * B[q].y, lrho);
+        }
+    }
+}
+
 template <bool W>
 __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -497,27 +533,11 @@ __global__ void __launch_bounds__(128) adj_stencil_kernel(StepArgs a, AdjArgs g)
     const int z = blockIdx.z;
     if (x >= a.nx || y >= a.ny) return;
     const Nbr nb(a, x, y, z);
-    const int N = a.nz - 1;
-    const bool pz = a.bc_zlo == BC_PERIODIC;
-    const bool lo_const = !pz && z == 0 && a.bc_zlo == BC_INLET && a.disc[nb.pxy];
     float lphi = 0.0f, lrho = 0.0f;
-#pragma unroll
-    for (int j = 1; j < 27; ++j) {
-        const bool below = !pz && z == 0 && cz(j) == 1;   // x = y - c_j would sit on z = -1
-        const bool above = !pz && z == N && cz(j) == -1;  // ... on z = N + 1
-        if (below && lo_const) continue;
-        // beyond a wall the reader is on this layer and reached y through its mirror ghost
-        // with that component of c reversed
-        const float czj = (below || above) ? -(float)cz(j) : (float)cz(j);
-        const float cxj = W && nb.fx(j) ? -(float)cx(j) : (float)cx(j);
-        const float cyj = W && nb.fy(j) ? -(float)cy(j) : (float)cy(j);
-        const int src = nb.src(j);  // clamped onto the wall layer: the mirrored reader
-        const float4 A = __ldg(g.lga + src);
-        const float2 B = __ldg(g.lgb + src);
-        const float w3 = 3.0f * wgt(j);
-        lphi = fmaf(w3, cxj * A.x + cyj * A.y + czj * A.z, lphi);
-        lrho = fmaf(w3, cxj * A.w + cyj * B.x + czj * B.y, lrho);
-    }
+    if (a.bc_zlo != BC_PERIODIC && (z == 0 || z == a.nz - 1))
+        adj_stencil_sums<W, true>(a, g, nb, z, lphi, lrho);
+    else
+        adj_stencil_sums<W, false>(a, g, nb, z, lphi, lrho);
     float phv, S_;  // phi and rho_r/rho_r0 + rho_b/rho_b0 of this node
     if (g.mom) {
         const float4 r0 = __ldg(g.mom + nb.n);  // (rho_r, rho_b, sf, jx)
@@ -628,7 +648,12 @@ __global__ void __launch_bounds__(128) adj_boundary_kernel(StepArgs a, AdjArgs g
             }
         }
     }
-    block_accumulate<17>(part, g.acc_inlet, block_id());
+    // only blocks holding inlet-disc columns have inlet gradients; the others skip the reduction
+    // (the decision is block-uniform, so every thread of a block takes the same branch)
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 17; ++k) any |= part[k] != 0.0f;
+    if (__syncthreads_or(any)) block_accumulate<17>(part, g.acc_inlet, block_id());
 }
 
 // ------------------------------------------------------------------- objectives

@@ -142,10 +142,13 @@ struct lb_ctx {
         void *base = nullptr;
         size_t bytes = 0;
         float2 *ckpt_pop = nullptr, *seg_pop = nullptr, *lp[2] = {}, *lr[2] = {}, *lgb = nullptr, *objph = nullptr;
-        float *ckpt_hist = nullptr, *seg_fm = nullptr, *seg_hist = nullptr, *lc = nullptr, *li = nullptr,
-              *lh[2] = {};
-        float4 *lga = nullptr, *seg_mom = nullptr, *seg_g4 = nullptr;
-        float2 *seg_g2 = nullptr;
+        float *ckpt_hist = nullptr, *seg_fm[2] = {}, *seg_hist[2] = {}, *lc = nullptr, *li = nullptr, *lh[2] = {};
+        float4 *lga = nullptr, *seg_mom[2] = {}, *seg_g4[2] = {};
+        float2 *seg_g2[2] = {};
+        // a second stream recomputes the next segment while the context's stream steps back
+        // through the current one; events order the two
+        cudaStream_t s2 = nullptr;
+        cudaEvent_t ev_fwd = nullptr, ev_rec[2] = {}, ev_rev[2] = {};
         double *acc_coll = nullptr, *acc_inlet = nullptr, *acc_obj = nullptr, *out = nullptr;
         long long nblk_coll = 0, nblk_inlet = 0;
         int cl = 0;
@@ -631,6 +634,15 @@ static void free_profile(lb_ctx *c) {
 void lb_destroy(lb_ctx *c) {
     if (!c) return;
     free_profile(c);
+    if (c->adj.s2) {
+        cudaStreamSynchronize(c->adj.s2);
+        cudaStreamDestroy(c->adj.s2);
+        cudaEventDestroy(c->adj.ev_fwd);
+        for (int r = 0; r < 2; ++r) {
+            cudaEventDestroy(c->adj.ev_rec[r]);
+            cudaEventDestroy(c->adj.ev_rev[r]);
+        }
+    }
     if (c->adj.base) cudaFree(c->adj.base);
     if (c->owns)
         for (int j = 0; j < c->nbufs; ++j)
@@ -957,18 +969,22 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     k = std::max(1ll, std::min<long long>(k, T));
     const long long nseg = (T + k - 1) / k;
 
-    // workspace: checkpoints every k steps, one segment of k recomputed steps, adjoint state
+    // workspace: checkpoints every k steps; two sets of per-step records (one segment is
+    // recomputed into one set while the reverse sweep steps back through the other); the
+    // adjoint state
     const size_t NN = (size_t)c->nn, P = (size_t)c->plane;
     const size_t pb = 27 * NN * sizeof(float2), hb = 54 * P * sizeof(float), nb2 = NN * sizeof(float2);
     StepArgs a0 = make_args(c);
     const long long nblk_coll = adj_collide_blocks(a0), nblk_inlet = adj_boundary_blocks(a0);
     // per recorded step: the collision inputs (the moment pass's 48 B and the 24 B of gradients
-    // a node), f(N-1) and hist(n+1) of the outflow plane; the populations themselves only in
-    // two alternating buffers
-    const size_t parts[] = {nseg * pb, nseg * hb, 2 * pb, k * 3 * NN * sizeof(float4), k * NN * sizeof(float4),
-                            k * nb2, k * hb, (k + 1) * hb, pb, pb, nb2, nb2, NN * sizeof(float4), nb2,
-                            hb, 9 * P * sizeof(float), hb, hb, nblk_coll * 3 * sizeof(double),
-                            nblk_inlet * 17 * sizeof(double), nblk_coll * sizeof(double), 32 * sizeof(double), nb2};
+    // a node), f(N-1) and hist(n+1) of the outflow plane; the recomputed populations
+    // themselves only in two alternating buffers
+    const size_t rmom = k * 3 * NN * sizeof(float4), rg4 = k * NN * sizeof(float4), rg2 = k * nb2, rfm = k * hb,
+                 rhist = (k + 1) * hb;
+    const size_t parts[] = {nseg * pb, nseg * hb, 2 * pb, rmom, rg4, rg2, rfm, rhist, rmom, rg4, rg2, rfm, rhist,
+                            pb, pb, nb2, nb2, NN * sizeof(float4), nb2, hb, 9 * P * sizeof(float), hb, hb,
+                            nblk_coll * 3 * sizeof(double), nblk_inlet * 17 * sizeof(double),
+                            nblk_coll * sizeof(double), 32 * sizeof(double), nb2};
     constexpr int kParts = (int)(sizeof(parts) / sizeof(parts[0]));
     size_t need = 0;
     for (size_t v : parts) need += align_up(v);
@@ -991,19 +1007,31 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
         for (int q = 0; q < kParts; ++q) take(v[q]);
         auto &w = c->adj;
         w.ckpt_pop = (float2 *)v[0]; w.ckpt_hist = (float *)v[1]; w.seg_pop = (float2 *)v[2];
-        w.seg_mom = (float4 *)v[3]; w.seg_g4 = (float4 *)v[4]; w.seg_g2 = (float2 *)v[5]; w.seg_fm = (float *)v[6];
-        w.seg_hist = (float *)v[7]; w.lp[0] = (float2 *)v[8]; w.lp[1] = (float2 *)v[9]; w.lr[0] = (float2 *)v[10];
-        w.lr[1] = (float2 *)v[11]; w.lga = (float4 *)v[12]; w.lgb = (float2 *)v[13]; w.lc = (float *)v[14];
-        w.li = (float *)v[15]; w.lh[0] = (float *)v[16]; w.lh[1] = (float *)v[17]; w.acc_coll = (double *)v[18];
-        w.acc_inlet = (double *)v[19]; w.acc_obj = (double *)v[20]; w.out = (double *)v[21];
-        w.objph = (float2 *)v[22];
+        for (int r = 0; r < 2; ++r) {
+            w.seg_mom[r] = (float4 *)v[3 + 5 * r]; w.seg_g4[r] = (float4 *)v[4 + 5 * r];
+            w.seg_g2[r] = (float2 *)v[5 + 5 * r]; w.seg_fm[r] = (float *)v[6 + 5 * r];
+            w.seg_hist[r] = (float *)v[7 + 5 * r];
+        }
+        w.lp[0] = (float2 *)v[13]; w.lp[1] = (float2 *)v[14]; w.lr[0] = (float2 *)v[15];
+        w.lr[1] = (float2 *)v[16]; w.lga = (float4 *)v[17]; w.lgb = (float2 *)v[18]; w.lc = (float *)v[19];
+        w.li = (float *)v[20]; w.lh[0] = (float *)v[21]; w.lh[1] = (float *)v[22]; w.acc_coll = (double *)v[23];
+        w.acc_inlet = (double *)v[24]; w.acc_obj = (double *)v[25]; w.out = (double *)v[26];
+        w.objph = (float2 *)v[27];
         w.nblk_coll = nblk_coll;
         w.nblk_inlet = nblk_inlet;
     }
     auto &w = c->adj;
     w.valid = false;
+    if (!w.s2) {
+        LB_CUDA(cudaStreamCreateWithFlags(&w.s2, cudaStreamNonBlocking));
+        LB_CUDA(cudaEventCreateWithFlags(&w.ev_fwd, cudaEventDisableTiming));
+        for (int r = 0; r < 2; ++r) {
+            LB_CUDA(cudaEventCreateWithFlags(&w.ev_rec[r], cudaEventDisableTiming));
+            LB_CUDA(cudaEventCreateWithFlags(&w.ev_rev[r], cudaEventDisableTiming));
+        }
+    }
     const bool conv = c->g.bc_zhi == LB_BC_CONVECTIVE;
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream, s2 = w.s2;
     LB_CUDA(cudaMemsetAsync(w.acc_coll, 0, nblk_coll * 3 * sizeof(double), st));
     LB_CUDA(cudaMemsetAsync(w.acc_inlet, 0, nblk_inlet * 17 * sizeof(double), st));
     LB_CUDA(cudaMemsetAsync(w.acc_obj, 0, nblk_coll * sizeof(double), st));
@@ -1012,29 +1040,32 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
     LB_CUDA(cudaMemsetAsync(w.lc, 0, hb, st));
     LB_CUDA(cudaMemsetAsync(w.li, 0, 9 * P * sizeof(float), st));
 
-    // what the reverse needs of step t of a segment: the collision inputs, f(N-1) and the
-    // outflow history before and after the step
-    auto record = [&](StepArgs &a, long long t) {
-        a.hist_in = w.seg_hist + t * 54 * P;
-        a.hist_out = w.seg_hist + (t + 1) * 54 * P;
-        a.mom = w.seg_mom + t * 3 * NN;
-        a.grad4 = w.seg_g4 + t * NN;
-        a.grad2 = w.seg_g2 + t * NN;
-        a.fm_out = conv ? w.seg_fm + t * 54 * P : nullptr;
+    // what the reverse needs of step t of a segment (record set r = segment index & 1): the
+    // collision inputs, f(N-1) and the outflow history before and after the step
+    auto record = [&](StepArgs &a, long long t, int r) {
+        a.hist_in = w.seg_hist[r] + t * 54 * P;
+        a.hist_out = w.seg_hist[r] + (t + 1) * 54 * P;
+        a.mom = w.seg_mom[r] + t * 3 * NN;
+        a.grad4 = w.seg_g4[r] + t * NN;
+        a.grad2 = w.seg_g2[r] + t * NN;
+        a.fm_out = conv ? w.seg_fm[r] + t * 54 * P : nullptr;
     };
     // forward pass with a checkpoint at the start of every segment; the last segment records
     // as it goes, so the reverse sweep needs no recompute for it
     const int64_t step0 = c->step;
     for (long long sg = 0; sg < nseg; ++sg) {
-        LB_CUDA(cudaMemcpyAsync(w.ckpt_pop + sg * 27 * NN, c->pop[c->cur], pb, cudaMemcpyDeviceToDevice, st));
-        if (conv)
-            LB_CUDA(cudaMemcpyAsync(w.ckpt_hist + sg * 54 * P, c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
         const long long len = std::min<long long>(k, T - sg * k);
         const bool last = sg == nseg - 1;
-        if (last) LB_CUDA(cudaMemcpyAsync(w.seg_hist, c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
+        const int r = (int)(sg & 1);
+        if (!last) {  // the recorded last segment is never recomputed
+            LB_CUDA(cudaMemcpyAsync(w.ckpt_pop + sg * 27 * NN, c->pop[c->cur], pb, cudaMemcpyDeviceToDevice, st));
+            if (conv)
+                LB_CUDA(cudaMemcpyAsync(w.ckpt_hist + sg * 54 * P, c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
+        }
+        if (last) LB_CUDA(cudaMemcpyAsync(w.seg_hist[r], c->hist[c->hcur], hb, cudaMemcpyDeviceToDevice, st));
         for (long long t = 0; t < len; ++t) {
             StepArgs a = make_args(c);
-            if (last) record(a, t);
+            if (last) record(a, t, r);
             cudaError_t e = launch_step(a, LB_STORE_FP32, st, nullptr, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "launch_step");
             c->cur ^= 1;
@@ -1042,7 +1073,7 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
             c->step += 1;
         }
         if (last && conv)
-            LB_CUDA(cudaMemcpyAsync(c->hist[c->hcur], w.seg_hist + len * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
+            LB_CUDA(cudaMemcpyAsync(c->hist[c->hcur], w.seg_hist[r] + len * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
     }
 
     // objective of S(T) and its adjoint
@@ -1059,42 +1090,62 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
         if (e != cudaSuccess) return cuda_fail(e, "launch_objective");
     }
 
-    // reverse sweep: recompute each segment from its checkpoint (the last one was recorded by
-    // the forward pass), then step back through it.  Step t of a segment: populations alternate
-    // between two buffers; the phase field and the boundary planes are the context's scratch;
-    // what the reverse needs is kept per step
-    auto seg_args = [&](long long t, int64_t step) {
+    // reverse sweep.  Segment sg is recomputed from its checkpoint on the second stream into
+    // record set sg & 1 while the context's stream steps back through segment sg + 1 (set
+    // (sg + 1) & 1); the recompute of a segment waits for the reverse that last used its set,
+    // the reverse of a segment for its recompute.  The recompute alone uses the population
+    // buffers seg_pop and the context's phase field, moments and boundary planes (the reverse
+    // kernels read none of them).
+    auto seg_args = [&](long long t, int64_t step, int r) {
         StepArgs a = make_args(c);
         a.pin = w.seg_pop + (t & 1) * 27 * NN;
         a.pout = w.seg_pop + ((t + 1) & 1) * 27 * NN;
-        record(a, t);
+        record(a, t, r);
         a.step = step;
         return a;
     };
-    for (long long sg = nseg - 1; sg >= 0; --sg) {
+    LB_CUDA(cudaEventRecord(w.ev_fwd, st));
+    LB_CUDA(cudaStreamWaitEvent(s2, w.ev_fwd, 0));
+    auto recompute = [&](long long sg) -> lb_status {
+        const int r = (int)(sg & 1);
         const long long n0 = sg * k, len = std::min<long long>(k, T - n0);
-        if (sg != nseg - 1) {
-            LB_CUDA(cudaMemcpyAsync(w.seg_pop, w.ckpt_pop + sg * 27 * NN, pb, cudaMemcpyDeviceToDevice, st));
-            if (conv)
-                LB_CUDA(cudaMemcpyAsync(w.seg_hist, w.ckpt_hist + sg * 54 * P, hb, cudaMemcpyDeviceToDevice, st));
-            for (long long t = 0; t < len; ++t) {
-                cudaError_t e = launch_step(seg_args(t, step0 + n0 + t), LB_STORE_FP32, st, nullptr, &c->launches);
-                if (e != cudaSuccess) return cuda_fail(e, "launch_step (recompute)");
-            }
+        LB_CUDA(cudaMemcpyAsync(w.seg_pop, w.ckpt_pop + sg * 27 * NN, pb, cudaMemcpyDeviceToDevice, s2));
+        if (conv)
+            LB_CUDA(cudaMemcpyAsync(w.seg_hist[r], w.ckpt_hist + sg * 54 * P, hb, cudaMemcpyDeviceToDevice, s2));
+        for (long long t = 0; t < len; ++t) {
+            cudaError_t e = launch_step(seg_args(t, step0 + n0 + t, r), LB_STORE_FP32, s2, nullptr, &c->launches);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_step (recompute)");
         }
+        LB_CUDA(cudaEventRecord(w.ev_rec[r], s2));
+        return LB_OK;
+    };
+    if (nseg >= 2) {
+        lb_status rs = recompute(nseg - 2);
+        if (rs != LB_OK) return rs;
+    }
+    for (long long sg = nseg - 1; sg >= 0; --sg) {
+        const int r = (int)(sg & 1);
+        const long long n0 = sg * k, len = std::min<long long>(k, T - n0);
+        if (sg != nseg - 1) LB_CUDA(cudaStreamWaitEvent(st, w.ev_rec[r], 0));
         for (long long t = len - 1; t >= 0; --t) {
             AdjArgs gs = g;
-            gs.mom = w.seg_mom + t * 3 * NN;
-            gs.grad4 = w.seg_g4 + t * NN;
-            gs.grad2 = w.seg_g2 + t * NN;
-            gs.fm = w.seg_fm + t * 54 * P;
+            gs.mom = w.seg_mom[r] + t * 3 * NN;
+            gs.grad4 = w.seg_g4[r] + t * NN;
+            gs.grad2 = w.seg_g2[r] + t * NN;
+            gs.fm = w.seg_fm[r] + t * 54 * P;
             gs.lp_in = w.lp[cl]; gs.lr_in = w.lr[cl];
             gs.lp_out = w.lp[cl ^ 1]; gs.lr_out = w.lr[cl ^ 1];
             gs.lh_in = w.lh[ch]; gs.lh_out = w.lh[ch ^ 1];
-            cudaError_t e = launch_adjoint_step(seg_args(t, step0 + n0 + t), gs, st, &c->launches);
+            cudaError_t e = launch_adjoint_step(seg_args(t, step0 + n0 + t, r), gs, st, &c->launches);
             if (e != cudaSuccess) return cuda_fail(e, "launch_adjoint_step");
             cl ^= 1;
             if (conv) ch ^= 1;
+        }
+        LB_CUDA(cudaEventRecord(w.ev_rev[r], st));
+        if (sg >= 2) {  // segment sg - 2 reuses this set
+            LB_CUDA(cudaStreamWaitEvent(s2, w.ev_rev[r], 0));
+            lb_status rs = recompute(sg - 2);
+            if (rs != LB_OK) return rs;
         }
     }
     {
