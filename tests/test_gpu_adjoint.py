@@ -2,9 +2,10 @@
 of the oracle and against the oracle's forward-mode (complex-step) tangent, same seeded inputs
 on both sides; the oracle never sees a GPU value.
 
-Gradient error norm: max over parameters of |g_adjoint - g_fd| / max over parameters of
-|g_fd| (the gradient's own scale), bar 1e-4; the directional derivative along a random state
-perturbation has the same bar.
+Gradient error norms: max over parameters of |g_adjoint - g_fd| / max over parameters of
+|g_fd| (the gradient's own scale), bar 1e-4; and every component whose reference exceeds 1e-3
+of that scale against its own value, bar 1e-4 as well (check_components).  The directional
+derivative along a random state perturbation has the same bar.
 """
 import numpy as np
 import pytest
@@ -91,6 +92,18 @@ def tangent_gradient(grid, bc, params, init, T, objective, args, names):
     return out
 
 
+TOL_COMP = 1e-4
+
+
+def check_components(g, ref, names):
+    """Each component whose reference exceeds 1e-3 of the largest, relative to its own value."""
+    big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    rel = np.abs(g - ref)[big] / np.abs(ref)[big]
+    worst = [(n, float(a), float(b)) for n, a, b, k in zip(names, g, ref, big) if k]
+    assert rel.size and rel.max() < TOL_COMP, (float(rel.max()), worst)
+    return float(rel.max())
+
+
 def jet_case():
     cfg = workloads.scaled_jet("jet64", 16, 14, 18, D=8)
     params = dict(cfg["params"])
@@ -117,6 +130,8 @@ def test_adjoint_jet_parameters_match_finite_differences(lb, objective, args):
     g_tan = tangent_gradient(grid, bc, params, lambda r: r.init_jet(), T, objective, args, NAMES)
     err_t = np.abs(g - g_tan).max() / np.abs(g_tan).max()
     assert err_t < TOL, (err_t, list(zip(NAMES, g, g_tan)))
+    check_components(g, g_tan, NAMES)
+    check_components(g, g_fd, NAMES)
 
 
 @pytest.mark.parametrize("bc,g", [((0, 0), (1e-5, 0.0, 2e-5)), ((1, 1), (0.0, 0.0, 3e-5))])
@@ -239,6 +254,7 @@ def test_adjoint_full_size_jet_short_horizon(lb):
     got = np.array([g[NAMES.index(n)] for n in names])
     err = np.abs(got - g_tan).max() / np.abs(g_tan).max()
     assert err < TOL, (err, got, g_tan)
+    check_components(got, g_tan, names)
 
 
 def test_adjoint_with_side_walls(lb):
@@ -256,6 +272,7 @@ def test_adjoint_with_side_walls(lb):
     g_tan = tangent_gradient(grid, bc, params, init, T, "area", (1e-3,), names)
     err = np.abs(g[idx] - g_tan).max() / np.abs(g_tan).max()
     assert err < TOL, (err, g[idx], g_tan)
+    check_components(g[idx], g_tan, names)
     g_fd = fd_gradient(grid, bc, params, init, T, "area", (1e-3,), names)
     assert np.abs(g[idx] - g_fd).max() / np.abs(g_fd).max() < TOL
 
@@ -294,3 +311,26 @@ def test_adjoint_with_mass_fraction_alpha(lb):
     g_tan = tangent_gradient(grid, bc, params, lambda r: r.init_jet(), T, "area", (1e-3,), names)
     got = np.array([g[NAMES.index(n)] for n in names])
     assert np.abs(got - g_tan).max() / np.abs(g_tan).max() < TOL, (got, g_tan)
+    check_components(got, g_tan, names)
+
+
+def test_adjoint_long_horizon_against_the_tangent(lb):
+    """100 steps of a 24x24x48 jet (D = 8, inlet noise and profile, convective outflow), the
+    default checkpoint interval (10 segments of 10, the last recorded by the forward pass, the
+    others recomputed on the second stream): J and six gradients against the oracle's
+    complex-step tangent, each component against its own value."""
+    cfg = workloads.scaled_jet("jet64", 24, 24, 48, D=8)
+    params = dict(cfg["params"])
+    params["noise_amp"] = 0.02
+    params["fourier"] = tuple(0.05 * np.random.default_rng(5).standard_normal(16))
+    grid, bc, T = (24, 24, 48), cfg["bc"], 100
+    lat = lb.Lattice(grid, params, bc=bc)
+    lat.init_jet()
+    J, g = lat.adjoint(T, "area", (1e-3,))
+    names = ("u_in", "sigma", "nu_r", "nu_b", "a1", "b2")
+    g_tan = tangent_gradient(grid, bc, params, lambda r: r.init_jet(), T, "area", (1e-3,), names)
+    J_ref = oracle_J(grid, bc, params, lambda r: r.init_jet(), T, "area", (1e-3,))
+    assert abs(J / J_ref - 1) < 1e-5, (J, J_ref)
+    got = np.array([g[NAMES.index(n)] for n in names])
+    assert np.abs(got - g_tan).max() / np.abs(g_tan).max() < TOL, (got, g_tan)
+    check_components(got, g_tan, names)

@@ -332,6 +332,36 @@ def test_fp16_storage_parity(lb, case, storage):
         assert np.abs(F[nm] - R["u"][d]).max() < 2e-2 * u_ref + 1e-4
 
 
+@pytest.mark.parametrize("case", ["two_phase", "jet"])
+def test_fitted_fp16_fields_within_1e3_of_the_oracle(lb, case):
+    """The fitted half-precision storage against the FP64 oracle after 50 steps: largest
+    |phi - phi_oracle| <= 1e-3 and relative L2 error of the velocity <= 1e-3, the precision
+    target for FP16 population storage.  (The rest-shift storage, LB_STORE_FP16, does not hold
+    1e-3 on longer runs: it is tested with the population bar above only.)"""
+    if case == "two_phase":
+        shape, bc = (12, 9, 40), (0, 0)
+        params = dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.08, sigma=0.003, g=(0.0, 0.0, 1e-5))
+    else:
+        cfg = workloads.scaled_jet("jet96", 36, 34, 40, D=10)
+        shape, bc, params = (40, 34, 36), cfg["bc"], dict(cfg["params"])
+    gpu, ref = pair(lb, shape, dict(params, storage=2), bc=bc)
+    if case == "two_phase":
+        fields = workloads.random_two_phase_fields(shape, 1, 1.0, 0.5, u_amp=0.03)
+        gpu.init_fields(*fields)
+        ref.init_fields(*fields)
+    else:
+        gpu.init_jet()
+        ref.init_jet()
+    run_both(gpu, ref, 50)
+    F = gpu.fields(device=False)
+    R = ref.fields()
+    dphi = np.abs(F["phi"] - R["phi"]).max()
+    du = np.stack([F[k].astype(np.float64) - R["u"][d] for d, k in enumerate(("ux", "uy", "uz"))])
+    rel_u = np.linalg.norm(du) / np.linalg.norm(R["u"])
+    print(f"FP16_FIT vs oracle, {case}: max|dphi| {dphi:.3e}, rel L2 u {rel_u:.3e}")
+    assert dphi <= 1e-3 and rel_u <= 1e-3, (dphi, rel_u)
+
+
 @pytest.mark.parametrize("storage", [1, 2])
 def test_fp16_storage_conserves_colour_mass(lb, storage):
     """The FP32 rest population absorbs the half-precision rounding of the moving ones, so
