@@ -6,9 +6,9 @@
  *
  * One context holds one D3Q27 lattice resident on one GPU.  lb_step advances it by the
  * paper's time step (Section II): pull streaming with the Section IV.A boundaries, the
- * phase field and its isotropic gradient, the central-moment collision (Eq. scoll with
- * Eqs. EES, Phi, ketF, ketFd), the perturbation (Eq. perturb) and the recolouring
- * (Eqs. op3r, op3b).
+ * phase field and its isotropic gradient, the central-moment collision (Eq. (11) with
+ * Eqs. (18), (21), (28), (29)), the perturbation (Eq. (30)) and the recolouring
+ * (Eqs. (33), (34)).
  *
  * Conventions for every entry point:
  *  - Pointers marked "device" must be CUDA device pointers on the context's device;
@@ -19,7 +19,7 @@
  *  - Errors are returned as lb_status; a message for the calling thread is available from
  *    lb_last_error().  No call aborts or throws across this interface.
  *  - Populations are laid out [k][i][z][y][x] (k = 0 red, 1 blue; i in the order of
- *    Eq. velVec; x fastest), single precision.
+ *    Eq. (8); x fastest), single precision.
  */
 #ifndef LBCM_H
 #define LBCM_H
@@ -50,8 +50,9 @@ typedef enum {
     LB_ENOTIMPL = 7    /* entry point declared but not provided by this build */
 } lb_status;
 
-/* Boundary kinds.  x and y are always periodic.  z_lo: PERIODIC, FREESLIP or INLET;
- * z_hi: PERIODIC, FREESLIP or CONVECTIVE; PERIODIC must be given for both or neither. */
+/* Boundary kinds.  z_lo: PERIODIC, FREESLIP or INLET; z_hi: PERIODIC, FREESLIP or CONVECTIVE;
+ * PERIODIC must be given for both z ends or neither.  x and y (lb_grid.bc_x, bc_y): PERIODIC
+ * or FREESLIP side walls. */
 typedef enum {
     LB_BC_PERIODIC = 0,
     LB_BC_FREESLIP = 1,   /* half-way specular reflection (Section IV.A, wall boundaries) */
@@ -72,7 +73,7 @@ typedef struct {
 /* Population storage.  FP32: every population in single precision.  FP16: the 26 moving
  * populations of each colour are stored in half precision as deviations from the rest
  * equilibrium of the node that will read them (pull streaming), h_i^k = f_i^k -
- * rho_k varphi_i(alpha_k) (Eq. varphi_ik), the rest population in single precision; it takes
+ * rho_k varphi_i(alpha_k) (Eq. (20)), the rest population in single precision; it takes
  * each colour's remainder of the moving ones as they are read back, so per-node colour mass
  * is kept to FP32 rounding.  FP16_FIT: the same layout, with the deviation taken from a
  * prediction of the reading node, rho_k (1 - alpha-bar) k_q plus an odd part w_i c_i . v_k
@@ -83,11 +84,11 @@ typedef struct {
 typedef enum { LB_STORE_FP32 = 0, LB_STORE_FP16 = 1, LB_STORE_FP16_FIT = 2 } lb_storage;
 
 typedef struct {
-    double rho_r0, rho_b0;  /* initial densities (Eq. order); gamma = rho_r0/rho_b0 >= 19/27 */
-    double nu_r, nu_b;      /* kinematic viscosities, > 0; s_2nu from Eq. (shear) */
-    double sigma;           /* interfacial tension; A = 9 sigma / (4 tau(x)) from Eq. (sigma) */
-    double beta;            /* recolouring parameter of Eqs. (op3r, op3b); 0.7 in the paper */
-    double g[3];            /* gravity in the body force F = (rho - rho_b0) g (Eq. bodyForceJet) */
+    double rho_r0, rho_b0;  /* initial densities (Eq. (23)); gamma = rho_r0/rho_b0 >= 19/27 */
+    double nu_r, nu_b;      /* kinematic viscosities, > 0; s_2nu from Eq. (16) */
+    double sigma;           /* interfacial tension; A = 9 sigma / (4 tau(x)) from Eq. (32) */
+    double beta;            /* recolouring parameter of Eqs. (33), (34); 0.7 in the paper */
+    double g[3];            /* gravity in the body force F = (rho - rho_b0) g (Eq. (48)) */
     double s0, s1;          /* rates of the conserved moments; 0 in the paper */
     double s2b, s3, s4, s5, s6; /* bulk and higher-order rates; 1 in the paper */
     double u_in;            /* inlet plug velocity u_j0 along +z */
@@ -101,7 +102,7 @@ typedef struct {
                                theta the polar angle of the inlet column about the disc centre;
                                stored a_1, b_1, ..., a_8, b_8 (not in the paper: the parameters the
                                adjoint differentiates); all 0 = the paper's uniform inlet */
-    int32_t alpha_mix;      /* alpha-bar of Eqs. (varphi_ik, press): 0 = the printed interpolation by
+    int32_t alpha_mix;      /* alpha-bar of Eqs. (20), (26): 0 = the printed interpolation by
                                (1 +- phi)/2; 1 = by mass fractions rho_k/rho, which makes the
                                equation of state additive over the colours (the reading under
                                which the paper's high-density-ratio droplets stay stable) */
@@ -144,21 +145,21 @@ typedef enum {
 } lb_init_kind;
 
 /* Sets populations from fields: f_i^k = rho_k [varphi_i(alpha_k) + w_i (3 cu + 9/2 cu^2
- * - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2)] (the equilibrium of Eq. EES per colour with Phi = 0),
+ * - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2)] (the equilibrium of Eq. (18) per colour with Phi = 0),
  * copies the outflow plane into the history, and resets the step counter to 0.
  * fields_on_device: 1 if rho_r/rho_b/u are device pointers, 0 for host pointers. */
 LB_API lb_status lb_init(lb_ctx *ctx, int32_t kind, const double *args, int32_t nargs,
                   const float *rho_r, const float *rho_b, const float *u, int32_t fields_on_device);
 
-/* Advances the lattice by n >= 0 time steps (Eq. LBE with the operator split of Section II). */
+/* Advances the lattice by n >= 0 time steps (Eq. (9) with the operator split of Section II). */
 LB_API lb_status lb_step(lb_ctx *ctx, int64_t n);
 
 /* Number of steps taken since lb_init / lb_load. */
 LB_API int64_t lb_step_count(const lb_ctx *ctx);
 
 /* Macroscopic fields of the current post-collision state, one float per node each:
- * rho_r, rho_b (sums of the colour populations), phi (Eq. order), u_x, u_y, u_z
- * (rho u = sum_i f_i c_i - F/2, the collision having added F), p (Eq. press with rho and
+ * rho_r, rho_b (sums of the colour populations), phi (Eq. (23)), u_x, u_y, u_z
+ * (rho u = sum_i f_i c_i - F/2, the collision having added F), p (Eq. (26) with rho and
  * alpha-bar).  mask selects outputs (bit j = LB_FIELD_*); outs[j] receives field j when
  * its bit is set.  on_device: outs are device (1) or host (0) pointers. */
 enum { LB_FIELD_RHO_R = 0, LB_FIELD_RHO_B = 1, LB_FIELD_PHI = 2, LB_FIELD_UX = 3,
@@ -190,9 +191,10 @@ LB_API lb_status lb_mass(lb_ctx *ctx, double out[2]);
  * nodes must lie in [1, LB_MASS_NOALLOC_MAX_NODES]; larger inputs return LB_EINVAL.
  *
  * The scratch is one file-scope device array of LB_MASS_NOALLOC_SCRATCH_BYTES that every
- * GPU loading the library holds until process exit.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) with the device current and caches
- * it; make that first call before any stream capture.  All calls share the array and it
+ * GPU loading the library holds until process exit.  Every call looks up that array's device
+ * address (cudaGetSymbolAddress) for the current device and context, so the address stays
+ * right after cudaDeviceReset; the first call on a device also loads the library's device
+ * code there, so make that first call before any stream capture.  All calls share the array and it
  * keeps the last call's contents; every slot a call reads is written by the same call
  * first, so nothing needs clearing.  Calls whose work overlaps on the GPU (other streams
  * or other host threads) race on the array and must be serialised by the caller. */
@@ -239,7 +241,7 @@ LB_API lb_status lb_set_params(lb_ctx *ctx, const lb_params *params);
  *
  * objective:
  *   LB_OBJ_INTERFACE_AREA  J = sum over nodes with 1 <= z <= nz-2 of sqrt(|grad phi|^2 + eps^2),
- *                          grad phi the isotropic stencil of the order parameter (Eq. order) of
+ *                          grad phi the isotropic stencil of the order parameter (Eq. (23)) of
  *                          rho_k = sum_i S_i^k; obj_args[0] = eps > 0.
  *   LB_OBJ_PENETRATION     J = delta log sum_n H(phi_n) exp(z_n / delta), H(phi) = ((1 + phi)/2)^2,
  *                          a smooth maximum of z over the red region (H = 1 in pure red, 0 in
@@ -262,7 +264,7 @@ LB_API lb_status lb_adjoint_state(lb_ctx *ctx, float *out, int32_t on_device);
 
 /* ----------------------------------------------------------------- fragment analysis
  * Fragments of the current state (Section IV.B, diameter procedure): the jet region is
- * phi > 0 (Eq. order) of the state's colour densities; fragments are its connected components
+ * phi > 0 (Eq. (23)) of the state's colour densities; fragments are its connected components
  * with face (connectivity 6) or full (26) neighbourhoods, wrapping across periodic boundaries;
  * each has a volume V (nodes) and equivalent spherical diameter d = (6V/pi)^(1/3) (lattice
  * units).  With exclude_inlet on an inlet lattice, components with a node on z = 0 are the

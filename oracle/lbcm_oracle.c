@@ -10,29 +10,29 @@
  *
  * Every step follows the paper's equations in the paper's order with dense
  * 27x27 matrices:
- *   - velocity set c_i                       Eq. (velVec)
- *   - LB equation, operator split            Eq. (LBE) and the Omega^(3)[Omega^(1)+Omega^(2)] split
- *   - GMRT collision -T^-1 K T (f - f^e) + F Eq. (scoll) with T = N M (Eq. momentSet)
- *   - densities, Guo momentum                Eq. (Momentum)
- *   - relaxation matrix K, nu(s_2nu)         Eq. (shear), text below Eq. (bulk)
- *   - enhanced equilibrium, varphi_i, Phi_i  Eqs. (EES), (varphi_ik), (Phi), G tensor
- *   - order parameter, alpha-bar, nu-bar     Eq. (order), harmonic mean, alpha-bar interpolation
- *   - forcing                                Eqs. (ketF), (ketFd)
- *   - perturbation, B_i, sigma               Eqs. (perturb), (B_i), (sigma)
- *   - recolouring                            Eqs. (op3r), (op3b)
- *   - isotropic gradient                     the 27-point central scheme at the end of Section II
+ *   - velocity set c_i                       Eq. (8)
+ *   - LB equation, operator split            Eq. (9) and the Omega^(3)[Omega^(1)+Omega^(2)] split
+ *   - GMRT collision -T^-1 K T (f - f^e) + F Eq. (11) with T = N M (Eq. (14))
+ *   - densities, Guo momentum                Eq. (13)
+ *   - relaxation matrix K, nu(s_2nu)         Eq. (16), text below Eq. (17)
+ *   - enhanced equilibrium, varphi_i, Phi_i  Eqs. (18), (20), (21), G tensor Eq. (24)
+ *   - order parameter, alpha-bar, nu-bar     Eq. (23), harmonic mean Eq. (22), alpha-bar Eq. (27)
+ *   - forcing                                Eqs. (28), (29)
+ *   - perturbation, B_i, sigma               Eqs. (30), (31), (32)
+ *   - recolouring                            Eqs. (33), (34)
+ *   - isotropic gradient                     Eq. (40), the 27-point central scheme of Section II
  *   - inlet / free-slip / convective outflow Section IV.A (Lou-type implicit convective scheme)
- *   - body force F = (rho - rho_b^0) g       Eq. (bodyForceJet)
+ *   - body force F = (rho - rho_b^0) g       Eq. (48)
  *   - static droplet initial state           Section III
  *
  * Readings of passages the paper leaves open (the same on the CUDA side):
- *   R1  Eq. (perturb) prints the numerator (c_i . grad phi) unsquared; the squared
+ *   R1  Eq. (30) prints the numerator (c_i . grad phi) unsquared; the squared
  *       form is used (the only form with zero mass and momentum).
  *   R2  The perturbation is applied for each colour k = r, b with A_r = A_b = A, so the
  *       colour-blind population receives the sum of both; with the capillary stress
  *       S = -tau sum_i sum_k Omega_i^k(2) c_i c_i this is the form for which
- *       sigma = (4/9) A tau (Eq. sigma) holds.
- *   R3  |grad phi| in Eqs. (perturb) and cos(theta_i) is regularised as
+ *       sigma = (4/9) A tau (Eq. (32)) holds.
+ *   R3  |grad phi| in Eqs. (30) and cos(theta_i) is regularised as
  *       sqrt(|grad phi|^2 + eps^2); cos(theta_0) = 0.
  *   R4  A = 9 sigma / (4 tau) per node with tau = 1/s_2nu(x).
  *   R5  grad rho in Phi_i and G uses the total density rho.
@@ -44,8 +44,9 @@
  *       elsewhere the half-way specular (free-slip) mirror S_{m(i)}(x - c_ix, y - c_iy, 0)
  *       where m flips c_z.  u_in = u_j0 (a xi rhat_x, a xi rhat_y, 1), xi in [-1, 1)
  *       from SplitMix64 of (seed, step, x, y); a = 0 gives the paper's undisturbed inlet.
- *   R8  Convective outflow at z = N = nz - 1 acts on all 27 post-stream populations
- *       of both colours; lambda = u_z(x, y, N - 1, t + 1) clamped to [0, 1].
+ *   R8  Convective outflow at z = N = nz - 1 (Eqs. (45)-(47)) acts on all 27 post-stream
+ *       populations of both colours; lambda = U_c(t + 1) = u_z(x, y, N - 1, t + 1) as Eqs. (46)
+ *       and (47) give it, clamped to [0, 1] (the paper is silent on backflow).
  *   R9  Gradient ghosts: z = -1 is phi = 1, rho = rho_r^0 inside the inlet disc and the
  *       mirror of z = 0 elsewhere (or on a free-slip wall); z = N + 1 mirrors z = N.
  *   R10 Initial populations from fields (rho_r, rho_b, u):
@@ -117,7 +118,7 @@ typedef double real;
 #endif
 #define RABS(x) fabs(RE(x))
 
-/* ---------------------------------------------------------------- lattice (Eq. velVec) */
+/* ---------------------------------------------------------------- lattice (Eq. (8)) */
 static const int CX[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1, -1, 1};
 static const int CY[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1};
 static const int CZ[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, 1, -1};
@@ -131,7 +132,7 @@ typedef struct {
 } orc_grid;
 
 typedef struct {
-    real rho_r0, rho_b0;       /* initial densities rho_k^0 (Eq. order) */
+    real rho_r0, rho_b0;       /* initial densities rho_k^0 (Eq. (23)) */
     real nu_r, nu_b;           /* kinematic viscosities */
     real sigma;                /* interfacial tension */
     real beta;                 /* recolouring parameter */
@@ -153,7 +154,7 @@ static double weight(int i) {
     return 1.0 / 216.0;
 }
 
-/* Eq. (varphi_ik) */
+/* Eq. (20) */
 static real varphi(int i, real alpha) {
     int q = CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i];
     if (q == 0) return alpha;
@@ -162,7 +163,7 @@ static real varphi(int i, real alpha) {
     return (1.0 - alpha) / 152.0;
 }
 
-/* Eq. (B_i) with c = 1 */
+/* Eq. (31) with c = 1 */
 static double Bcoef(int i) {
     int q = CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i];
     if (q == 0) return -10.0 / 27.0;
@@ -232,7 +233,7 @@ int orc_num_threads(void) {
 
 #endif
 
-/* ---------------------------------------------------------- moment set (Eq. momentSet) */
+/* ---------------------------------------------------------- moment set (Eq. (14)) */
 /* T[a][i]: row a is the a-th nonorthogonal central moment evaluated at direction i,
  * with cbar = c_i - u. */
 void orc_build_T(const real *u, real *T) {
@@ -331,7 +332,7 @@ static void relaxation_diag(const orc_params *p, real s2nu, real *K) {
     K[26] = p->s6;
 }
 
-/* ------------------------------------------------------------ equilibrium (Eq. EES) */
+/* ------------------------------------------------------------ equilibrium (Eq. (18)) */
 void orc_equilibrium(real rho, const real *u, real alpha, real nu, const real *grho, real *fe) {
     real G[3][3];
     for (int a = 0; a < 3; ++a)
@@ -355,7 +356,7 @@ void orc_equilibrium(real rho, const real *u, real alpha, real nu, const real *g
     }
 }
 
-/* ------------------------------------------------------------ forcing (Eq. ketFd) */
+/* ------------------------------------------------------------ forcing (Eq. (29)) */
 void orc_forcing_prime(const real *u, const real *F, real *Fp) {
     for (int i = 0; i < 27; ++i) {
         real c[3] = {CX[i], CY[i], CZ[i]};
@@ -366,8 +367,8 @@ void orc_forcing_prime(const real *u, const real *F, real *Fp) {
     }
 }
 
-/* ----------------------------------------- GMRT collision (Eqs. scoll, ketF), literal */
-/* Omega1 = -T^-1 K T (f - fe) + T^-1 (I - K/2) T F' with T = N M built from Eq. momentSet. */
+/* ----------------------------------------- GMRT collision (Eqs. (11), (28)), literal */
+/* Omega1 = -T^-1 K T (f - fe) + T^-1 (I - K/2) T F' with T = N M built from Eq. (14). */
 int orc_collide(const real *f, const real *fe, const real *Fp, const real *u, const real *K, real *Omega1) {
     real T[729], LU[729];
     int piv[27];
@@ -390,7 +391,7 @@ int orc_collide(const real *f, const real *fe, const real *Fp, const real *u, co
     return 0;
 }
 
-/* --------------------------------- perturbation (Eqs. perturb, B_i), readings R1-R3 */
+/* --------------------------------- perturbation (Eqs. (30), (31)), readings R1-R3 */
 void orc_perturbation(real A, const real *gphi, real eps, real *Omega2) {
     real g2 = gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2];
     real gmag = SQRT(g2 + eps * eps);
@@ -403,7 +404,7 @@ void orc_perturbation(real A, const real *gphi, real eps, real *Omega2) {
     }
 }
 
-/* ------------------------------------------------ recolouring (Eqs. op3r, op3b) */
+/* ------------------------------------------------ recolouring (Eqs. (33), (34)) */
 void orc_recolor(const real *fstar, real rho_r, real rho_b, real alpha_bar, real nu_bar,
                  real beta, const real *gphi, real eps, real *fr, real *fb) {
     real rho = rho_r + rho_b;
@@ -477,7 +478,7 @@ static inline size_t pidx(const orc_grid *g, int k, int i, size_t n) {
 }
 static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
 
-/* --------------------------------------------------------- streaming (Eq. LBE, pull) */
+/* --------------------------------------------------------- streaming (Eq. (9), pull) */
 /* f[k][i](x) = S[k][i](x - c_i) with the boundary rules R7, R8.  `hist` holds the
  * post-stream populations of the outflow plane at the previous step; on return
  * `hist_out` holds those of this step. */
@@ -525,7 +526,7 @@ void orc_stream(const orc_grid *g, const orc_params *p, const real *S, const rea
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 size_t m = nidx(g, x, y, N - 1), n = nidx(g, x, y, N);
-                /* u_z at N-1 after streaming (Eq. Momentum with F = (rho - rho_b0) g) */
+                /* u_z at N-1 after streaming (Eq. (13) with F = (rho - rho_b0) g) */
                 real rho = 0.0, jz = 0.0;
                 for (int k = 0; k < 2; ++k)
                     for (int i = 0; i < 27; ++i) {
@@ -617,7 +618,7 @@ int orc_step(const orc_grid *g, const orc_params *p, const real *S_in, const rea
                 for (int i = 0; i < 27; ++i) fb_[i] = f[pidx(g, 0, i, n)] + f[pidx(g, 1, i, n)];
                 real rho_r = rr[n], rho_b = rb[n], rho = rho_r + rho_b;
                 real phi = (rho_r / p->rho_r0 - rho_b / p->rho_b0) / (rho_r / p->rho_r0 + rho_b / p->rho_b0);
-                /* body force (Eq. bodyForceJet) and Guo velocity (Eq. Momentum) */
+                /* body force (Eq. (48)) and Guo velocity (Eq. (13)) */
                 real F[3], u[3];
                 for (int d = 0; d < 3; ++d) F[d] = (rho - p->rho_b0) * p->g[d];
                 for (int d = 0; d < 3; ++d) {
@@ -629,9 +630,9 @@ int orc_step(const orc_grid *g, const orc_params *p, const real *S_in, const rea
                 real alpha_bar = p->alpha_mix ? (rho_r * alpha_r + rho_b * alpha_b) / rho
                                               : 0.5 * (1.0 + phi) * alpha_r + 0.5 * (1.0 - phi) * alpha_b;
                 real nu_bar = 1.0 / (0.5 * (1.0 + phi) / p->nu_r + 0.5 * (1.0 - phi) / p->nu_b);
-                real s2nu = 1.0 / (3.0 * nu_bar + 0.5); /* Eq. (shear) with c = dt = 1 */
+                real s2nu = 1.0 / (3.0 * nu_bar + 0.5); /* Eq. (16) with c = dt = 1 */
                 real tau = 1.0 / s2nu;
-                real A = 9.0 * p->sigma / (4.0 * tau); /* Eq. (sigma), R4 */
+                real A = 9.0 * p->sigma / (4.0 * tau); /* Eq. (32), R4 */
                 real K[27], fe[27], Fp[27], Om1[27], Om2[27], fs[27];
                 relaxation_diag(p, s2nu, K);
                 orc_equilibrium(rho, u, alpha_bar, nu_bar, grho, fe);
@@ -693,7 +694,7 @@ void orc_droplet_fields(const orc_grid *g, const orc_params *p, real R, real W, 
 
 /* --------------------------------------------------------------------- diagnostics */
 /* Fields of a post-collision state: rho_k = sum_i S_i^k; rho u = sum_i S_i c_i - F/2
- * (the collision adds F to the momentum, Eqs. scoll and ketF); p from Eq. (press)
+ * (the collision adds F to the momentum, Eqs. (11) and (28)); p from Eq. (26)
  * with rho and alpha-bar. */
 void orc_fields(const orc_grid *g, const orc_params *p, const real *S, real *rho_r, real *rho_b,
                 real *u, real *phi, real *pres) {

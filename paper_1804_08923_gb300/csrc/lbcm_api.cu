@@ -159,7 +159,7 @@ struct lb_ctx {
 namespace lbcm {
 
 // ------------------------------------------------------------ initial populations
-// f_i^k = rho_k [varphi_i(alpha_k) + w_i P(c_i.u, u^2)]  (Eq. EES per colour, Phi = 0); the
+// f_i^k = rho_k [varphi_i(alpha_k) + w_i P(c_i.u, u^2)]  (Eq. (18) per colour, Phi = 0); the
 // rest population takes each colour's remainder of the stored moving ones.
 struct InitArgs {
     float *hist;
@@ -290,7 +290,7 @@ __global__ void fields_kernel(StepArgs sa, FieldOut fo, float gx, float gy, floa
         if (fo.o[LB_FIELD_P]) {
             const float alpha = sa.alpha_mix ? (rr * sa.alpha_r + rb * sa.alpha_b) / rho
                                              : 0.5f * (1.0f + phi) * sa.alpha_r + 0.5f * (1.0f - phi) * sa.alpha_b;
-            fo.o[LB_FIELD_P][n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (press)
+            fo.o[LB_FIELD_P][n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (26)
         }
     }
 }
@@ -389,11 +389,6 @@ namespace {
 
 using namespace lbcm;
 
-// Device address of g_mass_noalloc_scratch per device, looked up once with that device
-// current (in host code the array's name is only a host-side stand-in).
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_addr[kMaxDevices] = {};
 
 // Inlet disc membership for the current d_in, and cleared boundary planes.
 lb_status upload_disc(lb_ctx *c) {
@@ -476,7 +471,7 @@ StepArgs make_args(const lb_ctx *c) {
     a.s4 = (float)p.s4; a.s5 = (float)p.s5; a.s6 = (float)p.s6;
     a.u_in = (float)p.u_in; a.noise_amp = (float)p.noise_amp;
     a.xc = (float)(0.5 * (g.nx - 1)); a.yc = (float)(0.5 * (g.ny - 1));
-    // FP16 shift weights varphi_i(alpha_k) by speed class (Eq. varphi_ik), one rounding
+    // FP16 shift weights varphi_i(alpha_k) by speed class (Eq. (20)), one rounding
     const double kq[4] = {0.0, 2.0 / 19.0, 1.0 / 38.0, 1.0 / 152.0};
     const double alpha_r = 1.0 - (1.0 - alpha_b) / (p.rho_r0 / p.rho_b0);
     for (int q = 0; q < 4; ++q) {
@@ -824,20 +819,17 @@ lb_status lb_mass_noalloc(const float *pop, int64_t nodes, double *out, void *st
         return fail(LB_EINVAL, "lb_mass_noalloc: nodes must lie in [1, " + std::to_string(LB_MASS_NOALLOC_MAX_NODES) +
                                    "] (static scratch of " + std::to_string(LB_MASS_NOALLOC_MAX_BLOCKS) +
                                    " blocks per colour); got " + std::to_string(nodes));
-    int dev = 0;
-    LB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(LB_EINVAL, "lb_mass_noalloc: device index out of range");
-    double *scratch = nullptr;
+    // Device address of the scratch array for the current device and context, looked up on
+    // every call (in host code the array's name is only a host-side stand-in, and a cached
+    // address would go stale after cudaDeviceReset or a new primary context).  The lookup
+    // allocates nothing; on the first call on a device it also loads the library's device code
+    // there.
+    void *sym = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_mass_noalloc_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_mass_noalloc_scratch)");
-            g_noalloc_addr[dev] = (double *)p;
-        }
-        scratch = g_noalloc_addr[dev];
+        cudaError_t e = cudaGetSymbolAddress(&sym, g_mass_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_mass_noalloc_scratch)");
     }
+    double *scratch = (double *)sym;
     const int nblocks = (int)((nodes + LB_MASS_NOALLOC_CHUNK - 1) / LB_MASS_NOALLOC_CHUNK);
     cudaStream_t s = (cudaStream_t)stream;
     mass_partial_kernel<<<dim3(nblocks, 2), kMassThreads, 0, s>>>(pop, nodes, scratch);

@@ -11,7 +11,7 @@
 
 namespace lbcm {
 
-// Velocity set of Eq. (velVec): c+1 packed two bits per direction.
+// Velocity set of Eq. (8): c+1 packed two bits per direction.
 constexpr unsigned long long kPackX = 0x20888895489549ull;
 constexpr unsigned long long kPackY = 0x0a089548a09495ull;
 constexpr unsigned long long kPackZ = 0x08a0a0a0954955ull;
@@ -83,18 +83,18 @@ static_assert(check_tables(), "direction tables");
 __host__ __device__ constexpr float wgt(int i) {
     return csq(i) == 0 ? 8.0f / 27.0f : csq(i) == 1 ? 2.0f / 27.0f : csq(i) == 2 ? 1.0f / 54.0f : 1.0f / 216.0f;
 }
-// Eq. (B_i)
+// Eq. (31)
 __host__ __device__ constexpr float bcoef(int i) {
     return csq(i) == 0 ? -10.0f / 27.0f : wgt(i);
 }
-// Eq. (varphi_ik): varphi_i(alpha) = alpha (rest) or k_q (1 - alpha)
+// Eq. (20): varphi_i(alpha) = alpha (rest) or k_q (1 - alpha)
 __host__ __device__ constexpr float varphi_k(int i) {
     return csq(i) == 1 ? 2.0f / 19.0f : csq(i) == 2 ? 1.0f / 38.0f : 1.0f / 152.0f;
 }
 __device__ __forceinline__ float varphi(int i, float alpha, float one_m_alpha) {
     return csq(i) == 0 ? alpha : varphi_k(i) * one_m_alpha;
 }
-// Eq. (Phi): coefficient of nu (G : c c) by speed class, G : c c = (c.u)(c.grad rho)/24
+// Eq. (21): coefficient of nu (G : c c) by speed class, G : c c = (c.u)(c.grad rho)/24
 __host__ __device__ constexpr float phi_corr(int i) {
     return csq(i) == 1 ? 16.0f / 24.0f : csq(i) == 2 ? 4.0f / 24.0f : 1.0f / 24.0f;
 }
@@ -103,7 +103,7 @@ __host__ __device__ constexpr float inv_cnorm(int i) {
     return csq(i) == 0 ? 0.0f : csq(i) == 1 ? 1.0f : csq(i) == 2 ? 0.70710678118654752f : 0.57735026918962576f;
 }
 
-// Polynomial part of Eq. (EES): 3 cu + 9/2 cu^2 - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2
+// Polynomial part of Eq. (18): 3 cu + 9/2 cu^2 - 3/2 u^2 + 9/2 cu^3 - 9/2 cu u^2
 __device__ __forceinline__ float eq_poly(float cu, float usq) {
     float t = fmaf(4.5f, cu, 3.0f);            // 3 + 4.5 cu
     t = fmaf(4.5f * cu, cu, t) - 4.5f * usq;  // 3 + 4.5cu + 4.5cu^2 - 4.5u^2
@@ -187,7 +187,7 @@ struct MassAcc {
     __device__ __forceinline__ float total() const { return f0 + s; }
 };
 
-// Order parameter of Eq. (order) from the colour densities (1/rho_k0 given).
+// Order parameter of Eq. (23) from the colour densities (1/rho_k0 given).
 __device__ __forceinline__ float order_parameter(float rho_r, float rho_b, float inv_rho_r0, float inv_rho_b0) {
     const float A = rho_r * inv_rho_r0, B = rho_b * inv_rho_b0;
     return (A - B) / (A + B);

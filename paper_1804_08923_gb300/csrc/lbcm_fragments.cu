@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) frag_init_kernel(StepArgs a, int *label) 
             rr += v.x;
             rb += v.y;
         }
-        // phi > 0  <=>  rho_r / rho_r0 > rho_b / rho_b0 (Eq. order)
+        // phi > 0  <=>  rho_r / rho_r0 > rho_b / rho_b0 (Eq. (23))
         label[n] = rr * a.inv_rho_r0 > rb * a.inv_rho_b0 ? (int)n : -1;
     }
 }

@@ -35,7 +35,7 @@ __device__ __forceinline__ void gather_one(const StepArgs &a, const Nbr &nb, int
     }
 }
 
-// Post-stream populations of node (x, y, z) (Eq. LBE, pull form) with the boundary
+// Post-stream populations of node (x, y, z) (Eq. (9), pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
 template <int S, bool W>
 __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, float (&fr)[27], float (&fb)[27]) {

@@ -8,16 +8,16 @@
 //                             (Section IV.A).  One warp per (x, y) column.
 //   2. moment_kernel          pull-gathers the 54 post-stream populations of a node (the
 //                             step's only gather) and writes its order parameter phi
-//                             (Eq. order) and total density rho (Section II, densities) for
+//                             (Eq. (23)) and total density rho (Section II, densities) for
 //                             the gradient stencil, and the 12 moments the collision needs
 //                             (colour densities, mass, momentum, raw second moment).  One
 //                             thread per node.
 //   3. collide_kernel         reads a node's moments, takes the isotropic gradients of phi
 //                             and rho from the fields of step 2 (end of Section II), and
 //                             applies the central-moment collision with the enhanced
-//                             equilibrium and GMRT forcing (Eqs. scoll, EES, Phi, ketF,
-//                             ketFd), the perturbation (Eq. perturb) and the recolouring
-//                             (Eqs. op3r, op3b); writes the 54 post-collision populations
+//                             equilibrium and GMRT forcing (Eqs. (11), (18), (21), (28),
+//                             (29)), the perturbation (Eq. (30)) and the recolouring
+//                             (Eqs. (33), (34)); writes the 54 post-collision populations
 //                             of the node (pull scheme: streaming happens in the next
 //                             step's gathers).
 // With relaxation rates other than the paper's, step 2 is phase_field_kernel (phase entry
@@ -26,14 +26,14 @@
 // The collision applies T^-1 K T through the tensor-product central moments
 //   kappa_abc = sum_i f_i (c_ix - u_x)^a (c_iy - u_y)^b (c_iz - u_z)^c,  a, b, c in {0,1,2},
 // computed by three 1-D shifted sweeps and undone by three reverse sweeps.  The 27 rows
-// of the paper's moment set (Eq. momentSet) are, order by order, invertible combinations
+// of the paper's moment set (Eq. (14)) are, order by order, invertible combinations
 // of these; K holds one rate per order except order 2, where the trace relaxes with s_2b
 // and the deviatoric part with s_2nu.  Relaxing kappa with those rates is therefore the
 // same linear map as T^-1 K T (exact up to rounding).  The forcing is folded in:
 //   f* = f^e + F'/2 + T^-1 (I - K) T (f - f^e + F'/2)
-// which equals f - T^-1 K T (f - f^e) + T^-1 (I - K/2) T F' (Eqs. scoll and ketF).
+// which equals f - T^-1 K T (f - f^e) + T^-1 (I - K/2) T F' (Eqs. (11) and (28)).
 //
-// With the paper's rates s3 = s4 = s5 = s6 = 1 (Section II, below Eq. bulk), (I - K) removes
+// With the paper's rates s3 = s4 = s5 = s6 = 1 (Section II, below Eq. (17)), (I - K) removes
 // every central moment of order three and above, so f* depends on f only through its
 // moments of order <= 2: mass, momentum and the raw second moment Pi(f).  Those of f^e and
 // F' have closed forms (Pi(f^e) = rho c_s^2 I + rho u u + nu (u g + g u + (u.g) I) with
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
         const float s_ = fr + fb;
         const float rho = warp_sum_f(s_), jz = warp_sum_f((float)czi * s_);
         const float Fz = (rho - a.rho_b0) * a.gz;
-        float lam = (jz + 0.5f * Fz) / rho;  // u_z(x, y, N-1, t+1), Eq. (Momentum)
+        float lam = (jz + 0.5f * Fz) / rho;  // u_z(x, y, N-1, t+1), Eq. (13)
         lam = fminf(fmaxf(lam, 0.0f), 1.0f);
         const float inv = 1.0f / (1.0f + lam);
         if (mine) {
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     float gpx, gpy, gpz, grx, gry, grz;
     stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
 
-    // macroscopic velocity with the Guo half-force (Eq. Momentum), body force Eq. (bodyForceJet)
+    // macroscopic velocity with the Guo half-force (Eq. (13)), body force Eq. (48)
     const float rho = rho_r + rho_b;
     const float inv_rho = 1.0f / rho;
     const float Fx = (rho - a.rho_b0) * a.gx, Fy = (rho - a.rho_b0) * a.gy, Fz = (rho - a.rho_b0) * a.gz;
@@ -267,15 +267,15 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     }
     const float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
 
-    // order parameter (Eq. order) and mixture parameters
+    // order parameter (Eq. (23)) and mixture parameters
     const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
     const float alpha = alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
     const float one_m_alpha = 1.0f - alpha;
     const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);  // harmonic mean
-    const float tau = 3.0f * nu + 0.5f;                           // Eq. (shear): 1/s_2nu
+    const float tau = 3.0f * nu + 0.5f;                           // Eq. (16): 1/s_2nu
     const float s2nu = 1.0f / tau;
-    const float Acoef = 2.25f * a.sigma / tau;                     // Eq. (sigma): A = 9 sigma / (4 tau)
+    const float Acoef = 2.25f * a.sigma / tau;                     // Eq. (32): A = 9 sigma / (4 tau)
 
     const float usq = ux * ux + uy * uy + uz * uz;
     const float ugr = ux * grx + uy * gry + uz * grz;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
 #pragma unroll
     for (int p = 0; p < 9; ++p) sweep_inv(m[p * 3 + 0], m[p * 3 + 1], m[p * 3 + 2], uz);
 
-    // perturbation (Eq. perturb, squared numerator, both colours) and recolouring
+    // perturbation (Eq. (30), squared numerator, both colours) and recolouring
     const float g2 = gpx * gpx + gpy * gpy + gpz * gpz;
     const float inv_gm = 1.0f / sqrtf(g2 + a.eps2);  // 1/|grad phi|_eps
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
@@ -378,7 +378,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     const int n = nb.n;
     const float rho_r = mo.rho_r, rho_b = mo.rho_b, sf = mo.sf, jx = mo.jx, jy = mo.jy, jz = mo.jz;
     const float pxx = mo.pxx, pyy = mo.pyy, pzz = mo.pzz, pxy = mo.pxy, pxz = mo.pxz, pyz = mo.pyz;
-    // macroscopic quantities (Eqs. Momentum, bodyForceJet, order) and mixture parameters
+    // macroscopic quantities (Eqs. (13), (48), (23)) and mixture parameters
     const float rho = rho_r + rho_b;
     const float inv_rho = 1.0f / rho;
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
@@ -459,7 +459,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
             W2[b][c] = Ay.g0[b] * V20[c];
         }
 
-    // perturbation (Eq. perturb, squared numerator, both colours) and recolouring
+    // perturbation (Eq. (30), squared numerator, both colours) and recolouring
     const float g2 = gpx * gpx + gpy * gpy + gpz * gpz;
     const float inv_gm = 1.0f / sqrtf(g2 + a.eps2);  // 1/|grad phi|_eps
     const float pert = Acoef * inv_gm;
@@ -502,7 +502,7 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     }
     // Rest direction.  In exact arithmetic the step keeps each colour's mass at this node
     // (sum_i f_i^k* = rho_k), so the rest population is that mass minus the moving ones as
-    // they will be read back; this equals Eqs. (op3r, op3b) for i = 0 and keeps the FP32
+    // they will be read back; this equals Eqs. (33), (34) for i = 0 and keeps the FP32
     // rounding of the lattice constants and any storage rounding from drifting the colour
     // masses step after step (the pairwise sum above is MassAcc's association).
     store_pop<S>(a, 0, n, make_float2(rho_r - sum_r, rho_b - sum_b), no_shift());

@@ -34,7 +34,7 @@ def lb():
 
 
 def test_golden_table1_is_eq_sigma():
-    """The printed theoretical column equals 2 sigma / R with sigma = (4/9) A tau (Eq. sigma)."""
+    """The printed theoretical column equals 2 sigma / R with sigma = (4/9) A tau (Eq. (32))."""
     for row in table1().values():
         assert abs(2 * (4 / 9) * 0.01 * 1.0 / 25 - row["dp_theory"]) < 5e-9
 

@@ -31,19 +31,19 @@ def random_u(scale=0.2):
 
 # ------------------------------------------------------------------ Appendix A matrices
 def test_printed_M_Minv_consistent():
-    """The printed M and (1/48) * 48 M^-1 are inverse (Appendix A, Eq. M)."""
+    """The printed M and (1/48) * 48 M^-1 are inverse (Appendix A, Eq. (A1))."""
     assert np.abs(M_PRINTED @ MINV_PRINTED - np.eye(27)).max() < 1e-14
 
 
 def test_velocity_set_is_rows_of_M():
-    """Rows 1-3 of the printed M are c_x, c_y, c_z (Eq. velVec); T(u=0) equals M."""
+    """Rows 1-3 of the printed M are c_x, c_y, c_z (Eq. (8)); T(u=0) equals M."""
     assert np.array_equal(M_PRINTED[1:4].T, C)
     assert np.abs(oracle.build_T([0, 0, 0]) - M_PRINTED).max() == 0.0
 
 
 @pytest.mark.parametrize("trial", range(6))
 def test_T_equals_printed_N_times_M(trial):
-    """T(u) from the moment set of Eq. (momentSet) equals N(u) M with N, M as printed."""
+    """T(u) from the moment set of Eq. (14) equals N(u) M with N, M as printed."""
     u = random_u()
     T = oracle.build_T(u)
     assert np.abs(T - N_PRINTED(u) @ M_PRINTED).max() < 1e-13
@@ -59,7 +59,7 @@ def test_T_inverse_equals_printed_Minv_Ninv(trial):
 
 
 def test_shift_matrix_is_lower_triangular():
-    """N is lower triangular with unit diagonal (Section II, text below Eq. momentSet)."""
+    """N is lower triangular with unit diagonal (Section II, text below Eq. (14))."""
     u = random_u()
     N = oracle.build_T(u) @ MINV_PRINTED
     assert np.abs(np.triu(N, 1)).max() < 1e-14
@@ -78,7 +78,7 @@ def test_weights_isotropy():
 
 
 def test_opposite_directions_pairwise():
-    """Directions come in opposite pairs (1,2), (3,4), ..., (25,26) (Eq. velVec)."""
+    """Directions come in opposite pairs (1,2), (3,4), ..., (25,26) (Eq. (8))."""
     for i in range(1, 27, 2):
         assert np.array_equal(C[i], -C[i + 1])
 
@@ -86,11 +86,11 @@ def test_opposite_directions_pairwise():
 # ------------------------------------------------------------------------ equilibrium
 @pytest.mark.parametrize("alpha", [8 / 27, 0.5309, 0.912])
 def test_equilibrium_moments(alpha):
-    """Mass, momentum and pressure tensor of Eq. (EES).
+    """Mass, momentum and pressure tensor of Eq. (18).
 
     sum fe = rho, sum fe c = rho u, and sum fe c c = rho c_s^2 I + rho u u
-    + nu (u g + g u + (u.g) I) where c_s^2 = 9(1 - alpha)/19 is the EOS of Eq. (press)
-    and the last term is the second moment of the correction Phi_i (Eq. Phi with G)."""
+    + nu (u g + g u + (u.g) I) where c_s^2 = 9(1 - alpha)/19 is the EOS of Eq. (26)
+    and the last term is the second moment of the correction Phi_i (Eq. (21) with G)."""
     rho, nu = 1.3, 0.04
     u, g = random_u(0.1), RNG.normal(size=3) * 0.05
     fe = oracle.equilibrium(rho, u, alpha, nu, g)
@@ -103,7 +103,7 @@ def test_equilibrium_moments(alpha):
 
 
 def test_equilibrium_correction_has_no_mass():
-    """sum_i Phi_i = 0: the correction of Eq. (Phi) changes neither mass nor momentum."""
+    """sum_i Phi_i = 0: the correction of Eq. (21) changes neither mass nor momentum."""
     u, g = random_u(0.1), RNG.normal(size=3)
     fe_g = oracle.equilibrium(1.0, u, 0.4, 0.1, g)
     fe_0 = oracle.equilibrium(1.0, u, 0.4, 0.1, [0, 0, 0])
@@ -113,7 +113,7 @@ def test_equilibrium_correction_has_no_mass():
 
 
 def test_equilibrium_reduces_to_maxwell_moments():
-    """At alpha = 8/27 and grad rho = 0 the weights varphi_i are w_i and Eq. (EES) is the
+    """At alpha = 8/27 and grad rho = 0 the weights varphi_i are w_i and Eq. (18) is the
     third-order Hermite expansion: its third moments that D3Q27 resolves equal those of a
     Maxwellian, sum fe cx cy cz = rho ux uy uz and sum fe cx^2 cy = rho (uy/3 + ux^2 uy)."""
     rho, u = 0.9, random_u(0.1)
@@ -128,7 +128,7 @@ def test_equilibrium_reduces_to_maxwell_moments():
 
 # ---------------------------------------------------------------------------- forcing
 def test_forcing_moments_are_guo():
-    """Eq. (ketFd): sum F' = 0, sum F' c = F, sum F' c c = u F + F u (Guo et al. 2002)."""
+    """Eq. (29): sum F' = 0, sum F' c = F, sum F' c c = u F + F u (Guo et al. 2002)."""
     u, F = random_u(0.1), RNG.normal(size=3) * 1e-3
     Fp = oracle.forcing_prime(u, F)
     assert abs(Fp.sum()) < 1e-17
@@ -143,8 +143,8 @@ def paper_K(s2nu, s2b=1.0, s3=1.0, s4=1.0, s5=1.0, s6=1.0, s0=0.0, s1=0.0):
 
 @pytest.mark.parametrize("s", [0.6, 1.0, 1.7])
 def test_collision_bgk_limit(s):
-    """Equal rates reduce Eqs. (scoll, ketF) to BGK with Guo forcing:
-    Omega = -s (f - fe) + (1 - s/2) F' (Section II, text below Eqs. K and ketFd)."""
+    """Equal rates reduce Eqs. (11), (28) to BGK with Guo forcing:
+    Omega = -s (f - fe) + (1 - s/2) F' (Section II, text below Eqs. (15) and (29))."""
     f, fe = RNG.uniform(0.01, 0.1, 27), RNG.uniform(0.01, 0.1, 27)
     Fp, u = RNG.uniform(-1e-3, 1e-3, 27), random_u()
     om = oracle.collide(f, fe, Fp, u, np.full(27, s))
@@ -176,10 +176,10 @@ def test_collision_shift_matters():
 
 # ----------------------------------------------------------------------- perturbation
 def test_perturbation_conserves_and_gives_sigma():
-    """Eq. (perturb) with the squared numerator: zero mass and momentum, and second moment
+    """Eq. (30) with the squared numerator: zero mass and momentum, and second moment
     sum Omega c c = (2A/9)|g| (n n - I) for both colours together, so the capillary stress
     S = -tau sum_i sum_k Omega c c integrated across a flat interface (int |grad phi| = 2)
-    gives sigma = (4/9) A tau, Eq. (sigma)."""
+    gives sigma = (4/9) A tau, Eq. (32)."""
     A, tau = 0.0225, 1.0
     g = RNG.normal(size=3) * 0.2
     om = oracle.perturbation(A, g, 0.0)
@@ -201,7 +201,7 @@ def test_perturbation_regularised_at_zero_gradient():
 
 
 def test_B_coefficients_sum():
-    """Eq. (B_i), recovered from the operator at two unit gradients: independent of the
+    """Eq. (31), recovered from the operator at two unit gradients: independent of the
     gradient, B_0 = -10/27, sum_i B_i = 1/3 and sum_i B_i c c = I/3."""
     g1, g2 = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
     o1, o2 = oracle.perturbation(2.0, g1, 0.0), oracle.perturbation(2.0, g2, 0.0)
@@ -215,7 +215,7 @@ def test_B_coefficients_sum():
 
 # ------------------------------------------------------------------------ recolouring
 def test_recolor_per_colour_mass_and_segregation():
-    """Eqs. (op3r, op3b): per-colour mass is kept, the colours add up to f*, and the red
+    """Eqs. (33), (34): per-colour mass is kept, the colours add up to f*, and the red
     flux is pushed along grad phi by beta (rho_r rho_b / rho) sum_i varphi_i c_i (c_i.n)/|c_i|."""
     fstar = RNG.uniform(0.01, 0.1, 27)
     rho = fstar.sum()
@@ -227,7 +227,7 @@ def test_recolor_per_colour_mass_and_segregation():
     assert np.abs(fr + fb - fstar).max() < 1e-16
     n = g / np.linalg.norm(g)
     flux = fr @ C - rho_r / rho * (fstar @ C)
-    # sum_i varphi_i c_a c_b / |c_i| = k I with k from Eq. (varphi_ik):
+    # sum_i varphi_i c_a c_b / |c_i| = k I with k from Eq. (20):
     k = (2 * 2 * (1 - alpha) / 19) + 8 * (1 - alpha) / 38 / math.sqrt(2) + 8 * (1 - alpha) / 152 / math.sqrt(3)
     assert np.abs(flux - beta * rho_r * rho_b / rho * k * n).max() < 1e-16
     fr0, _ = oracle.recolor(fstar, rho_r, rho_b, alpha, 0.1, 0.0, g, 0.0)
@@ -408,7 +408,7 @@ def test_inlet_fourier_profile(m, kind):
 @pytest.mark.parametrize("gamma,nu,tol", [(1.0, 1 / 6, 1e-4), (2.0, 1 / 6, 1e-4), (1.0, 0.05, 0.01), (8.0, 0.02, 0.01)])
 def test_shear_wave_decay_gives_viscosity(gamma, nu, tol):
     """A single-colour shear wave u_x = u0 sin(2 pi y/L) decays as exp(-nu k^2 t) with
-    nu = (1/3)(1/s_2nu - 1/2) (Eq. shear), also for alpha_r != 8/27 (gamma != 1)."""
+    nu = (1/3)(1/s_2nu - 1/2) (Eq. (16)), also for alpha_r != 8/27 (gamma != 1)."""
     L = 32
     shape = (1, L, 1)
     lat = make_lattice(shape, rho_b0=1 / gamma, nu_r=nu, nu_b=nu, sigma=0.0)
@@ -428,7 +428,7 @@ def test_shear_wave_decay_gives_viscosity(gamma, nu, tol):
 
 def test_laplace_law_static_droplet():
     """Static droplet of Section III (R = 8, W = 4, 32^3, periodic, gamma = 1, tau = 1):
-    after 200 steps the pressure jump from Eq. (press) is 2 sigma / R (Eq. lap) to the
+    after 200 steps the pressure jump from Eq. (26) is 2 sigma / R (Eq. (43)) to the
     accuracy a small, diffuse droplet allows at this time (within 10%)."""
     n, R, sigma = 32, 8.0, 0.01
     lat = make_lattice((n, n, n), sigma=sigma)
@@ -446,7 +446,7 @@ def test_laplace_law_static_droplet():
 
 # ---------------------------------------------------------- adjoint objectives (R12)
 def _phi_fields(phi, rho_r0=1.0, rho_b0=0.5, s=1.0):
-    """Colour densities with order parameter phi (Eq. order): rho_k / rho_k0 = s (1 +- phi) / 2."""
+    """Colour densities with order parameter phi (Eq. (23)): rho_k / rho_k0 = s (1 +- phi) / 2."""
     return rho_r0 * s * (1 + phi) / 2, rho_b0 * s * (1 - phi) / 2
 
 
