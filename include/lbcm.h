@@ -154,6 +154,42 @@ LB_API lb_status lb_init(lb_ctx *ctx, int32_t kind, const double *args, int32_t 
 /* Advances the lattice by n >= 0 time steps (Eq. (9) with the operator split of Section II). */
 LB_API lb_status lb_step(lb_ctx *ctx, int64_t n);
 
+/* ----------------------------------------------------------- z-slab decomposition
+ * One lattice split into slabs of consecutive z planes, one context per slab (on one GPU or
+ * several; not in the paper, whose runs are single lattices): the step is a nearest-neighbour
+ * stencil, so a slab needs one plane of each neighbour slab per side, twice per step.  A slab's
+ * context holds its own planes plus a ghost plane on every side that borders another slab
+ * (bc_zlo / bc_zhi of such a side are LB_BC_FREESLIP: the ghost plane computes values that no
+ * real plane reads); the first slab keeps the lattice's z_lo boundary, the last its z_hi.
+ * One step of the split lattice, on every slab:
+ *   1. population halo: lb_halo_pack(LB_HALO_POPULATIONS) of the first and last real plane,
+ *      exchanged with the neighbours, lb_halo_unpack into the ghost planes;
+ *   2. lb_step_gather: boundary planes and the gather pass (phase field, collision moments);
+ *   3. phase halo: the same with LB_HALO_PHASE (the phase entries the gather pass just wrote,
+ *      which the collision's gradient stencil and, with FP16 storage, its encoding read);
+ *   4. lb_step_collide: the collision; the state advances to t+1.
+ * The real planes then evolve bit for bit as the same planes of the whole lattice.  Colour
+ * masses of the real planes come from lb_mass_planes, summed over the slabs by the caller.
+ *
+ * lb_step_gather / lb_step_collide: the two halves of one lb_step (Eq. (9) with the operator
+ * split of Section II).  LB_ESTATE for a gather that follows a gather, a collide without a
+ * gather, and lb_step or lb_adjoint in between.  Profiling events are not recorded for them.
+ * lb_halo_bytes: bytes of one halo plane of the given kind in the context's storage (FP32:
+ * 216 (populations) or 8 (phase) per (x, y) column; FP16 encodings: 112 or 16).
+ * lb_halo_pack / lb_halo_unpack: copy plane z (0 <= z < nz) of the current populations (kind
+ * LB_HALO_POPULATIONS, only outside a split step) or of the phase entries of the step being
+ * taken (LB_HALO_PHASE, only between lb_step_gather and lb_step_collide) into / from a
+ * contiguous buffer of lb_halo_bytes, in the context's own encoding.  buf is device memory
+ * if on_device, else host memory (then the call synchronises).
+ * lb_mass_planes: lb_mass restricted to planes [z_begin, z_end).  Synchronises. */
+enum { LB_HALO_POPULATIONS = 0, LB_HALO_PHASE = 1 };
+LB_API lb_status lb_step_gather(lb_ctx *ctx);
+LB_API lb_status lb_step_collide(lb_ctx *ctx);
+LB_API lb_status lb_halo_bytes(const lb_ctx *ctx, int32_t kind, size_t *nbytes);
+LB_API lb_status lb_halo_pack(lb_ctx *ctx, int32_t kind, int32_t z, void *dst, int32_t on_device);
+LB_API lb_status lb_halo_unpack(lb_ctx *ctx, int32_t kind, int32_t z, const void *src, int32_t on_device);
+LB_API lb_status lb_mass_planes(lb_ctx *ctx, int32_t z_begin, int32_t z_end, double out[2]);
+
 /* Number of steps taken since lb_init / lb_load. */
 LB_API int64_t lb_step_count(const lb_ctx *ctx);
 

@@ -116,6 +116,42 @@ class Lattice:
     def step(self, n=1):
         _abi.check(self.lib.lb_step(self._ctx, C.c_int64(n)))
 
+    def step_gather(self):
+        """First half of a step (boundary planes, gather pass); see lb_step_gather."""
+        _abi.check(self.lib.lb_step_gather(self._ctx))
+
+    def step_collide(self):
+        """Second half of a step (collision); see lb_step_collide."""
+        _abi.check(self.lib.lb_step_collide(self._ctx))
+
+    def halo_bytes(self, kind: int) -> int:
+        n = C.c_size_t()
+        _abi.check(self.lib.lb_halo_bytes(self._ctx, int(kind), C.byref(n)))
+        return int(n.value)
+
+    def halo_pack(self, kind: int, z: int, buf):
+        """Copies halo plane z into buf: a CUDA uint8 tensor (device) or a numpy uint8 array
+        (host) of halo_bytes(kind) bytes."""
+        dev, ptr = self._buffer(buf, self.halo_bytes(kind))
+        _abi.check(self.lib.lb_halo_pack(self._ctx, int(kind), int(z), ptr, dev))
+
+    def halo_unpack(self, kind: int, z: int, buf):
+        dev, ptr = self._buffer(buf, self.halo_bytes(kind))
+        _abi.check(self.lib.lb_halo_unpack(self._ctx, int(kind), int(z), ptr, dev))
+
+    def _buffer(self, buf, nbytes):
+        torch = _torch()
+        if isinstance(buf, torch.Tensor):
+            assert buf.is_contiguous() and buf.numel() * buf.element_size() >= nbytes
+            return (1 if buf.is_cuda else 0), C.c_void_p(buf.data_ptr())
+        assert buf.flags.c_contiguous and buf.nbytes >= nbytes
+        return 0, C.c_void_p(buf.ctypes.data)
+
+    def mass_planes(self, z_begin: int, z_end: int):
+        out = (C.c_double * 2)()
+        _abi.check(self.lib.lb_mass_planes(self._ctx, int(z_begin), int(z_end), out))
+        return np.array([out[0], out[1]])
+
     @property
     def step_count(self) -> int:
         return int(self.lib.lb_step_count(self._ctx))

@@ -20,8 +20,9 @@ STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_EUNS
 EXPORTS = ("lb_params_default", "lb_buffer_sizes", "lb_create", "lb_create_with_buffers", "lb_init", "lb_step",
            "lb_step_count", "lb_fields", "lb_populations", "lb_history", "lb_mass", "lb_mass_noalloc", "lb_save", "lb_load",
            "lb_profile_enable", "lb_profile_read", "lb_kernel_launches", "lb_set_params", "lb_adjoint",
-           "lb_adjoint_state", "lb_fragments", "lb_last_error",
-           "lb_destroy")
+           "lb_adjoint_state", "lb_fragments", "lb_step_gather", "lb_step_collide", "lb_halo_bytes",
+           "lb_halo_pack", "lb_halo_unpack", "lb_mass_planes", "lb_last_error", "lb_destroy")
+HALO_POPULATIONS, HALO_PHASE = 0, 1
 ADJ_NOUT = 21  # LB_ADJ_NOUT: J and 20 parameter gradients
 
 
@@ -93,6 +94,12 @@ def library(path: str = LIB_PATH):
         L.lb_adjoint_state.argtypes = [vp, fp, C.c_int32]
         L.lb_fragments.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp,
                                    C.c_int64, C.POINTER(FragmentStats)]
+        L.lb_step_gather.argtypes = [vp]
+        L.lb_step_collide.argtypes = [vp]
+        L.lb_halo_bytes.argtypes = [vp, C.c_int32, C.POINTER(C.c_size_t)]
+        L.lb_halo_pack.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32]
+        L.lb_halo_unpack.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32]
+        L.lb_mass_planes.argtypes = [vp, C.c_int32, C.c_int32, dp]
         L.lb_last_error.argtypes = []
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]

@@ -133,6 +133,7 @@ struct lb_ctx {
     int cur = 0, hcur = 0;
     int64_t step = 0;
     bool initialized = false;
+    bool half = false;  // lb_step_gather has run, lb_step_collide has not
     long long nn = 0, plane = 0;
     long long launches = 0;
     std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded step
@@ -337,11 +338,11 @@ __global__ void __launch_bounds__(kMassThreads) mass_partial_kernel(const float 
 
 // Same first stage over a context's own population storage (decoded).
 template <int S>
-__global__ void __launch_bounds__(kMassThreads) mass_partial_store_kernel(StepArgs sa, double *__restrict__ partial) {
+__global__ void __launch_bounds__(kMassThreads) mass_partial_store_kernel(StepArgs sa, long long nb, long long ne,
+                                                                          double *__restrict__ partial) {
     const int k = blockIdx.y;
-    const long long NN = sa.NN;
-    const long long per = (NN + gridDim.x - 1) / gridDim.x;
-    const long long n0 = blockIdx.x * per, n1 = min(NN, n0 + per);
+    const long long per = (ne - nb + gridDim.x - 1) / gridDim.x;
+    const long long n0 = nb + blockIdx.x * per, n1 = min(ne, n0 + per);
     double acc = 0.0;
     for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
         const Nbr nb = node_nbr(sa, n);
@@ -496,7 +497,6 @@ StepArgs make_args(const lb_ctx *c) {
     return a;
 }
 
-// FP64 colour masses of the current state (store-aware first stage).
 // Step arguments describing the current state for diagnostics: pin = the current
 // populations, ph_cur = the phase entries they were encoded for (FP16).
 StepArgs state_args(const lb_ctx *c) {
@@ -506,14 +506,18 @@ StepArgs state_args(const lb_ctx *c) {
     return a;
 }
 
-lb_status run_mass(lb_ctx *c, double out[2]) {
+// FP64 colour masses of planes [z0, z1) of the current state (store-aware first stage).
+lb_status run_mass(lb_ctx *c, double out[2], int z0 = 0, int z1 = -1) {
     const StepArgs sa = state_args(c);
+    if (z1 < 0) z1 = c->g.nz;
+    const long long nb = (long long)z0 * c->plane, ne = (long long)z1 * c->plane;
+    const dim3 grid(kMassBlocks, 2);
     if (c->p.storage == LB_STORE_FP16)
-        mass_partial_store_kernel<STORE_FP16><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
+        mass_partial_store_kernel<STORE_FP16><<<grid, kMassThreads, 0, c->stream>>>(sa, nb, ne, c->partial);
     else if (c->p.storage == LB_STORE_FP16_FIT)
-        mass_partial_store_kernel<STORE_FP16_FIT><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
+        mass_partial_store_kernel<STORE_FP16_FIT><<<grid, kMassThreads, 0, c->stream>>>(sa, nb, ne, c->partial);
     else
-        mass_partial_store_kernel<STORE_FP32><<<dim3(kMassBlocks, 2), kMassThreads, 0, c->stream>>>(sa, c->partial);
+        mass_partial_store_kernel<STORE_FP32><<<grid, kMassThreads, 0, c->stream>>>(sa, nb, ne, c->partial);
     mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->partial, kMassBlocks, c->partial + 2 * kMassBlocks);
     c->launches += 2;
     LB_CUDA(cudaGetLastError());
@@ -720,29 +724,146 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
     if (kind == LB_INIT_FIELDS && !fields_on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = 0;
     c->initialized = true;
+    c->half = false;
     return LB_OK;
+}
+
+// The end of a step: the state now at t+1, and the periodic mass check.
+static lb_status finish_step(lb_ctx *c) {
+    c->cur ^= 1;
+    if (c->g.bc_zhi == LB_BC_CONVECTIVE) c->hcur ^= 1;
+    c->step += 1;
+    if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
+        double m[2];
+        lb_status st = run_mass(c, m);
+        if (st != LB_OK) return st;
+        if (!std::isfinite(m[0]) || !std::isfinite(m[1]))
+            return fail(LB_EUNSTABLE, "non-finite colour mass at step " + std::to_string(c->step));
+    }
+    return LB_OK;
+}
+
+lb_status lb_step_gather(lb_ctx *c) {
+    if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_step_gather before lb_init/lb_load");
+    if (c->half) return fail(LB_ESTATE, "lb_step_gather twice without lb_step_collide");
+    cudaError_t e = launch_step(make_args(c), c->p.storage, c->stream, nullptr, &c->launches, PASS_GATHER);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_step (gather)");
+    c->half = true;
+    return LB_OK;
+}
+
+lb_status lb_step_collide(lb_ctx *c) {
+    if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
+    if (!c->half) return fail(LB_ESTATE, "lb_step_collide without lb_step_gather");
+    cudaError_t e = launch_step(make_args(c), c->p.storage, c->stream, nullptr, &c->launches, PASS_COLLIDE);
+    if (e != cudaSuccess) return cuda_fail(e, "launch_step (collide)");
+    c->half = false;
+    return finish_step(c);
+}
+
+// Offset, row pitch, row width and row count (bytes) of the parts of plane z of one halo
+// kind, in the context's own layout; part 1 is empty (rows = 0) where one part suffices.
+struct HaloPart {
+    char *base;
+    size_t pitch, width, rows;
+};
+static int halo_parts(lb_ctx *c, int kind, int z, HaloPart (&hp)[2]) {
+    const size_t P = (size_t)c->plane, NN = (size_t)c->nn;
+    hp[1] = HaloPart{nullptr, 0, 0, 0};
+    if (kind == LB_HALO_POPULATIONS) {
+        char *pop = (char *)c->pop[c->cur];
+        if (c->p.storage == LB_STORE_FP32) {
+            hp[0] = HaloPart{pop + (size_t)z * P * 8, NN * 8, P * 8, 27};
+        } else {
+            hp[0] = HaloPart{pop + (size_t)z * P * 8, P * 8, P * 8, 1};
+            hp[1] = HaloPart{pop + NN * 8 + (size_t)z * P * 4, NN * 4, P * 4, 26};
+        }
+    } else {
+        if (c->p.storage == LB_STORE_FP32)
+            hp[0] = HaloPart{(char *)(c->phase + (size_t)z * P), P * 8, P * 8, 1};
+        else
+            hp[0] = HaloPart{(char *)(c->ph4[c->cur ^ 1] + (size_t)z * P), P * 16, P * 16, 1};
+    }
+    return hp[1].rows ? 2 : 1;
+}
+
+static lb_status halo_check(lb_ctx *c, int kind, int z) {
+    if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
+    if (kind != LB_HALO_POPULATIONS && kind != LB_HALO_PHASE) return fail(LB_EINVAL, "unknown halo kind");
+    if (z < 0 || z >= c->g.nz) return fail(LB_EINVAL, "halo plane outside the lattice");
+    if (!c->initialized) return fail(LB_ESTATE, "halo copy before lb_init/lb_load");
+    if (kind == LB_HALO_POPULATIONS && c->half) return fail(LB_ESTATE, "population halo inside a split step");
+    if (kind == LB_HALO_PHASE && !c->half) return fail(LB_ESTATE, "phase halo outside a split step");
+    return LB_OK;
+}
+
+lb_status lb_halo_bytes(const lb_ctx *c, int32_t kind, size_t *nbytes) {
+    if (!c || !nbytes) return fail(LB_EINVAL, "ctx and nbytes must not be NULL");
+    const size_t P = (size_t)c->plane;
+    const bool fp32 = c->p.storage == LB_STORE_FP32;
+    if (kind == LB_HALO_POPULATIONS)
+        *nbytes = fp32 ? 216 * P : 112 * P;
+    else if (kind == LB_HALO_PHASE)
+        *nbytes = fp32 ? 8 * P : 16 * P;
+    else
+        return fail(LB_EINVAL, "unknown halo kind");
+    return LB_OK;
+}
+
+static lb_status halo_copy(lb_ctx *c, int kind, int z, char *buf, bool pack, int on_device) {
+    HaloPart hp[2];
+    const int n = halo_parts(c, kind, z, hp);
+    size_t off = 0;
+    for (int j = 0; j < n; ++j) {
+        const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice
+                                           : (pack ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+        if (pack)
+            LB_CUDA(cudaMemcpy2DAsync(buf + off, hp[j].width, hp[j].base, hp[j].pitch, hp[j].width, hp[j].rows, k,
+                                      c->stream));
+        else
+            LB_CUDA(cudaMemcpy2DAsync(hp[j].base, hp[j].pitch, buf + off, hp[j].width, hp[j].width, hp[j].rows, k,
+                                      c->stream));
+        off += hp[j].width * hp[j].rows;
+    }
+    if (!on_device) LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_halo_pack(lb_ctx *c, int32_t kind, int32_t z, void *dst, int32_t on_device) {
+    lb_status s = halo_check(c, kind, z);
+    if (s != LB_OK) return s;
+    if (!dst) return fail(LB_EINVAL, "dst must not be NULL");
+    return halo_copy(c, kind, z, (char *)dst, true, on_device);
+}
+
+lb_status lb_halo_unpack(lb_ctx *c, int32_t kind, int32_t z, const void *src, int32_t on_device) {
+    lb_status s = halo_check(c, kind, z);
+    if (s != LB_OK) return s;
+    if (!src) return fail(LB_EINVAL, "src must not be NULL");
+    return halo_copy(c, kind, z, (char *)src, false, on_device);
+}
+
+lb_status lb_mass_planes(lb_ctx *c, int32_t z_begin, int32_t z_end, double out[2]) {
+    if (!c || !out) return fail(LB_EINVAL, "ctx and out must not be NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_mass_planes before lb_init/lb_load");
+    if (z_begin < 0 || z_end > c->g.nz || z_begin >= z_end) return fail(LB_EINVAL, "plane range outside the lattice");
+    return run_mass(c, out, z_begin, z_end);
 }
 
 lb_status lb_step(lb_ctx *c, int64_t n) {
     if (!c) return fail(LB_EINVAL, "ctx must not be NULL");
     if (n < 0) return fail(LB_EINVAL, "n must be >= 0");
     if (!c->initialized) return fail(LB_ESTATE, "lb_step before lb_init/lb_load");
+    if (c->half) return fail(LB_ESTATE, "lb_step inside a split step (lb_step_gather without lb_step_collide)");
     for (int64_t s = 0; s < n; ++s) {
         StepArgs a = make_args(c);
         cudaEvent_t *ev = nullptr;
         if (c->prof_used < c->prof_cap) ev = &c->prof_ev[4 * (size_t)c->prof_used++];
         cudaError_t e = launch_step(a, c->p.storage, c->stream, ev, &c->launches);
         if (e != cudaSuccess) return cuda_fail(e, "launch_step");
-        c->cur ^= 1;
-        if (c->g.bc_zhi == LB_BC_CONVECTIVE) c->hcur ^= 1;
-        c->step += 1;
-        if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
-            double m[2];
-            lb_status st = run_mass(c, m);
-            if (st != LB_OK) return st;
-            if (!std::isfinite(m[0]) || !std::isfinite(m[1]))
-                return fail(LB_EUNSTABLE, "non-finite colour mass at step " + std::to_string(c->step));
-        }
+        lb_status st = finish_step(c);
+        if (st != LB_OK) return st;
     }
     return LB_OK;
 }
@@ -898,6 +1019,7 @@ lb_status lb_load(lb_ctx *c, const void *buf, size_t nbytes) {
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->step = h.step;
     c->initialized = true;
+    c->half = false;
     return LB_OK;
 }
 
@@ -942,6 +1064,7 @@ lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_
                      int32_t n_grad) {
     if (!c || !obj_args || !grad_out) return fail(LB_EINVAL, "ctx, obj_args and grad_out must not be NULL");
     if (!c->initialized) return fail(LB_ESTATE, "lb_adjoint before lb_init/lb_load");
+    if (c->half) return fail(LB_ESTATE, "lb_adjoint inside a split step");
     if (c->p.storage != LB_STORE_FP32) return fail(LB_EINVAL, "lb_adjoint needs FP32 population storage");
     if (c->p.s3 != 1.0 || c->p.s4 != 1.0 || c->p.s5 != 1.0 || c->p.s6 != 1.0)
         return fail(LB_EINVAL, "lb_adjoint needs the paper's rates s3 = s4 = s5 = s6 = 1");

@@ -4,14 +4,16 @@
 #include "lbcm_device.cuh"
 
 namespace lbcm {
-// One time step (boundary planes, phase field, collision) on stream s, for population
-// storage STORE_FP32 or STORE_FP16.  When ev is not
-// NULL, ev[0..3] are recorded before the boundary kernel, before the phase-field kernel,
-// before the collision kernel and after it.  *launches is increased by the number of
-// kernels launched.  collide = false stops after the phase-field kernel (boundary planes and
-// phase field of the step, no new populations; ev[3] is then not recorded).
+// One time step (boundary planes, gather pass, collision) on stream s, for population storage
+// STORE_FP32, STORE_FP16 or STORE_FP16_FIT.  passes selects PASS_GATHER (boundary planes and the
+// gather pass: phase field and collision moments), PASS_COLLIDE (the collision, which writes
+// S(t+1)) or both; a z-slab decomposition exchanges the phase halo between the two.  When ev
+// is not NULL, ev[0..3] are recorded before the boundary kernel, before the gather kernel,
+// before the collision kernel and after it (those of the passes launched).  *launches is
+// increased by the number of kernels launched.
+enum { PASS_GATHER = 1, PASS_COLLIDE = 2, PASS_BOTH = 3 };
 cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches,
-                        bool collide = true);
+                        int passes = PASS_BOTH);
 
 // Adjoint state and scratch of one reverse step (FP32 populations, paper rates).
 //   lp_in / lr_in   lambda of S(n+1): pushed part [27][NN] float2 and deferred density part [NN]

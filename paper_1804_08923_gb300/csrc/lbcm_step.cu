@@ -535,32 +535,36 @@ __global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : (S == STORE_FP16 ?
 
 // ------------------------------------------------------------------------ launchers
 template <int S, bool W>
-static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, bool collide) {
-    if (ev) cudaEventRecord(ev[0], s);
-    if (a.bc_zlo != BC_PERIODIC || a.bc_zhi != BC_PERIODIC) {
-        boundary_plane_kernel<S><<<(unsigned)((a.plane + 3) / 4), 128, 0, s>>>(a);
-        *launches += 1;
-    }
+static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, int passes) {
     const bool paper_rates = a.s3 == 1.0f && a.s4 == 1.0f && a.s5 == 1.0f && a.s6 == 1.0f;
     const bool force = a.gx != 0.0f || a.gy != 0.0f || a.gz != 0.0f;
     dim3 blk(32, 4, 1), grd((a.nx + 31) / 32, (a.ny + 3) / 4, a.nz);
-    if (ev) cudaEventRecord(ev[1], s);
-    // pass 1: the step's pull gather (phase field, and the collision moments when the paper's
-    // rates let the collision work from them)
-    if (paper_rates) {
-        if constexpr (W && S != STORE_FP32)
-            moment_wall_kernel<S><<<grd, blk, 0, s>>>(a);
-        else
-            moment_kernel<S, W><<<grd, blk, 0, s>>>(a);
-    } else {
-        if constexpr (W && S != STORE_FP32)
-            phase_field_wall_kernel<S><<<grd, blk, 0, s>>>(a);
-        else
-            phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
+    if (passes & PASS_GATHER) {
+        if (ev) cudaEventRecord(ev[0], s);
+        if (a.bc_zlo != BC_PERIODIC || a.bc_zhi != BC_PERIODIC) {
+            boundary_plane_kernel<S><<<(unsigned)((a.plane + 3) / 4), 128, 0, s>>>(a);
+            *launches += 1;
+        }
+        if (ev) cudaEventRecord(ev[1], s);
+        // pass 1: the step's pull gather (phase field, and the collision moments when the
+        // paper's rates let the collision work from them)
+        if (paper_rates) {
+            if constexpr (W && S != STORE_FP32)
+                moment_wall_kernel<S><<<grd, blk, 0, s>>>(a);
+            else
+                moment_kernel<S, W><<<grd, blk, 0, s>>>(a);
+        } else {
+            if constexpr (W && S != STORE_FP32)
+                phase_field_wall_kernel<S><<<grd, blk, 0, s>>>(a);
+            else
+                phase_field_kernel<S, W><<<grd, blk, 0, s>>>(a);
+        }
+        if (ev) cudaEventRecord(ev[2], s);
+        *launches += 1;
     }
-    if (ev) cudaEventRecord(ev[2], s);
-    *launches += 1;
-    if (!collide) return;
+    if (!(passes & PASS_COLLIDE)) return;
+    // pass 2: the collision, writing S(t+1)
+    if (ev && !(passes & PASS_GATHER)) cudaEventRecord(ev[2], s);
     const bool rec = S == STORE_FP32 && a.grad4 != nullptr;  // paper rates only (adjoint)
     if (!paper_rates)
         collide_general_kernel<S, W><<<grd, blk, 0, s>>>(a);
@@ -577,21 +581,21 @@ static void launch_step_sw(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, l
 }
 
 template <int S>
-static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, bool collide) {
+static void launch_step_s(const StepArgs &a, cudaStream_t s, cudaEvent_t *ev, long long *launches, int passes) {
     if (a.wall_x || a.wall_y)
-        launch_step_sw<S, true>(a, s, ev, launches, collide);
+        launch_step_sw<S, true>(a, s, ev, launches, passes);
     else
-        launch_step_sw<S, false>(a, s, ev, launches, collide);
+        launch_step_sw<S, false>(a, s, ev, launches, passes);
 }
 
 cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches,
-                        bool collide) {
+                        int passes) {
     if (storage == STORE_FP16)
-        launch_step_s<STORE_FP16>(a, s, ev, launches, collide);
+        launch_step_s<STORE_FP16>(a, s, ev, launches, passes);
     else if (storage == STORE_FP16_FIT)
-        launch_step_s<STORE_FP16_FIT>(a, s, ev, launches, collide);
+        launch_step_s<STORE_FP16_FIT>(a, s, ev, launches, passes);
     else
-        launch_step_s<STORE_FP32>(a, s, ev, launches, collide);
+        launch_step_s<STORE_FP32>(a, s, ev, launches, passes);
     return cudaGetLastError();
 }
 
