@@ -430,6 +430,39 @@ def job_mlups(nodes_per_rank, steps, world, ms_max):
     return nodes_per_rank * steps * world / (ms_max * 1e-3) / 1e6
 
 
+def run_slabs(args, cfg, lb, torch, dist, rank, world, local, barrier, max_over_ranks, peak):
+    """One lattice split into `world` z-slabs, one per rank, halos over NCCL (device buffers):
+    strong scaling; the throughput counts the lattice's nodes once."""
+    from paper_1804_08923_gb300 import slab
+    nodes = int(np.prod(cfg["grid"]))
+    s = slab.SlabLattice(cfg["grid"], with_storage(cfg["params"], args.storage), cfg["bc"], rank, world, dist,
+                         device=f"cuda:{local}")
+    init_state(s, cfg)
+    s.step(args.warmup)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        s.step(args.steps)
+        e1.record()
+        barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = nodes * args.steps / (ms * 1e-3) / 1e6
+    bytes_step, _ = BYTES[args.storage]
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32" if args.storage == 0 else "f32 arithmetic, f16 population storage",
+            "data": "synthetic", "config": dict(config_block(cfg, args.storage),
+                                                parallelism=f"z-slabs over {world} GPUs, halos over NCCL"),
+            "hbm_pct_of_peak": 100.0 * value * 1e6 * bytes_step / (peak[0] * 1e9) / world,
+            "slab_planes": [list(r) for r in slab.partition(cfg["grid"][2], world)],
+            "mass": s.mass().tolist(), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def config_block(cfg, storage):
     nx, ny, nz = cfg["grid"]
     return {"workload": f"{cfg['name']}: {cfg['text']}", "lattice": [nx, ny, nz], "nodes": nx * ny * nz,
@@ -455,6 +488,9 @@ def main():
     ap.add_argument("--no-paper-workload", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 384x384x1536 mass-drift leg")
     ap.add_argument("--no-oracle-error", action="store_true")
+    ap.add_argument("--slabs", action="store_true",
+                    help="with N > 1 ranks: split the one lattice into z-slabs (halo exchange over NCCL, strong "
+                         "scaling) instead of one replica per rank")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint leg (lb_adjoint against lb_step on the 64x64x256 jet)")
     ap.add_argument("--adjoint-steps", type=int, default=500)
@@ -497,6 +533,8 @@ def main():
     nodes = nx * ny * nz
     peak = measured_peaks()
     st = args.storage
+    if args.slabs and world > 1:
+        return run_slabs(args, cfg, lb, torch, dist, rank, world, local, barrier, max_over_ranks, peak)
     lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], st), bc=cfg["bc"])
     init_state(lat, cfg)
     stream = lat.stream
