@@ -187,7 +187,7 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
                 uz = fmaf(0.5f, Fz, mo.jz) * inv_rho;
     const float phi = order_parameter(rr, rb, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
-    const float alpha = alpha_bar(a.alpha_mix, rr, rb, inv_rho, hp, hm, a.alpha_r, a.alpha_b), oma = 1.0f - alpha;
+    const float oma = one_minus_alpha_bar(a.alpha_mix, rr, rb, inv_rho, hp, hm, a.oma_r, a.oma_b), alpha = 1.0f - oma;
     const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);
     const float tau = 3.0f * nu + 0.5f, s2nu = 1.0f / tau;
     const float Acoef = 2.25f * a.sigma / tau;
@@ -408,10 +408,10 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
     part[1] += -lH * hp * a.inv_nu_r * a.inv_nu_r;
     part[2] += -lH * hm * a.inv_nu_b * a.inv_nu_b;
     if (a.alpha_mix) {  // alpha-bar = (rho_r alpha_r + rho_b alpha_b) / rho
-        lrr = fmaf(lalpha, (a.alpha_r - alpha) * inv_rho, lrr);
-        lrb = fmaf(lalpha, (a.alpha_b - alpha) * inv_rho, lrb);
+        lrr = fmaf(lalpha, (oma - a.oma_r) * inv_rho, lrr);  // (alpha_r - alpha-bar) / rho
+        lrb = fmaf(lalpha, (oma - a.oma_b) * inv_rho, lrb);
     } else {
-        lphi = fmaf(lalpha, 0.5f * (a.alpha_r - a.alpha_b), lphi);
+        lphi = fmaf(lalpha, 0.5f * (a.oma_b - a.oma_r), lphi);  // (alpha_r - alpha_b) / 2
     }
     // ---- u = (j + F/2) / rho, F = (rho - rho_b0) g
     const float ljx = lux * inv_rho, ljy = luy * inv_rho, ljz = luz * inv_rho;

@@ -166,7 +166,7 @@ struct InitArgs {
     float *hist;
     const float *fr, *fb, *fu;
     int kind, nx, ny, nz;
-    float a0, a1, a2, a3, a4, rho_r0, rho_b0, alpha_r, alpha_b;
+    float a0, a1, a2, a3, a4, rho_r0, rho_b0, alpha_r, alpha_b, oma_r, oma_b;
 };
 
 __device__ __forceinline__ Nbr node_nbr(const StepArgs &a, long long n) {
@@ -215,8 +215,8 @@ __global__ void init_phase_kernel(InitArgs ia, StepArgs sa) {
             for (int i = 0; i < 27; ++i) {
                 const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
                 const float pw = wgt(i) * eq_poly(cu, usq);
-                fr[i] = rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw);
-                fb[i] = rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw);
+                fr[i] = rr * (varphi(i, ia.alpha_r, ia.oma_r) + pw);
+                fb[i] = rb * (varphi(i, ia.alpha_b, ia.oma_b) + pw);
             }
             sa.ph_cur[n] = pack_fit_entry(ph, rr + rb, fit_even(sa, rr, rb, ph), fit_odd_fp8(sa, fr, fb));
         }
@@ -238,8 +238,8 @@ __global__ void init_kernel(InitArgs ia, StepArgs sa) {
         for (int i = 1; i < 27; ++i) {
             const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
             const float pw = wgt(i) * eq_poly(cu, usq);
-            const float2 f = make_float2(rr * (varphi(i, ia.alpha_r, 1.0f - ia.alpha_r) + pw),
-                                         rb * (varphi(i, ia.alpha_b, 1.0f - ia.alpha_b) + pw));
+            const float2 f = make_float2(rr * (varphi(i, ia.alpha_r, ia.oma_r) + pw),
+                                         rb * (varphi(i, ia.alpha_b, ia.oma_b) + pw));
             const float2 d = store_pop<S>(sa, i, (int)n, f, dest_shift<S>(sa, nb, i));
             sr.add(i, d.x);
             sb.add(i, d.y);
@@ -289,9 +289,9 @@ __global__ void fields_kernel(StepArgs sa, FieldOut fo, float gx, float gy, floa
         if (fo.o[LB_FIELD_UY]) fo.o[LB_FIELD_UY][n] = (jy - 0.5f * fc * gy) / rho;
         if (fo.o[LB_FIELD_UZ]) fo.o[LB_FIELD_UZ][n] = (jz - 0.5f * fc * gz) / rho;
         if (fo.o[LB_FIELD_P]) {
-            const float alpha = sa.alpha_mix ? (rr * sa.alpha_r + rb * sa.alpha_b) / rho
-                                             : 0.5f * (1.0f + phi) * sa.alpha_r + 0.5f * (1.0f - phi) * sa.alpha_b;
-            fo.o[LB_FIELD_P][n] = rho * 9.0f * (1.0f - alpha) / 19.0f;  // Eq. (26)
+            const float oma = sa.alpha_mix ? (rr * sa.oma_r + rb * sa.oma_b) / rho
+                                           : 0.5f * (1.0f + phi) * sa.oma_r + 0.5f * (1.0f - phi) * sa.oma_b;
+            fo.o[LB_FIELD_P][n] = rho * 9.0f * oma / 19.0f;  // Eq. (26)
         }
     }
 }
@@ -464,6 +464,8 @@ StepArgs make_args(const lb_ctx *c) {
     a.alpha_b = (float)alpha_b;
     a.alpha_mix = p.alpha_mix;
     a.alpha_r = (float)(1.0 - (1.0 - alpha_b) / (p.rho_r0 / p.rho_b0));
+    a.oma_r = (float)((1.0 - alpha_b) / (p.rho_r0 / p.rho_b0));
+    a.oma_b = (float)(1.0 - alpha_b);
     a.inv_nu_r = (float)(1.0 / p.nu_r); a.inv_nu_b = (float)(1.0 / p.nu_b);
     a.sigma = (float)p.sigma; a.beta = (float)p.beta;
     a.eps2 = (float)(p.eps_grad * p.eps_grad);
@@ -707,7 +709,7 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
     sa.pout = c->pop[0];
     sa.ph_cur = c->ph4[0];
     InitArgs ia{c->hist[0], fr, fb, fu, kind, c->g.nx, c->g.ny, c->g.nz,
-                a[0], a[1], a[2], a[3], a[4], sa.rho_r0, sa.rho_b0, sa.alpha_r, sa.alpha_b};
+                a[0], a[1], a[2], a[3], a[4], sa.rho_r0, sa.rho_b0, sa.alpha_r, sa.alpha_b, sa.oma_r, sa.oma_b};
     if (c->p.storage == LB_STORE_FP16) {
         init_phase_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);
         init_kernel<STORE_FP16><<<grid_for(c->nn, 256), 256, 0, c->stream>>>(ia, sa);

@@ -159,10 +159,14 @@ __device__ __forceinline__ void inlet_velocity(float u_in, float noise_amp, cons
     v.uz = u_in * prof;
 }
 
-// alpha-bar: (1 + phi)/2 alpha_r + (1 - phi)/2 alpha_b as printed, or by mass fractions.
-__device__ __forceinline__ float alpha_bar(int mix, float rho_r, float rho_b, float inv_rho, float hp, float hm,
-                                           float alpha_r, float alpha_b) {
-    return mix ? (rho_r * alpha_r + rho_b * alpha_b) * inv_rho : hp * alpha_r + hm * alpha_b;
+// 1 - alpha-bar (Eq. (27) as printed, (1 + phi)/2 alpha_r + (1 - phi)/2 alpha_b, or by mass
+// fractions), formed from the colours' 1 - alpha_k (oma_r, oma_b, rounded once from FP64): at
+// large density ratios alpha-bar is close to 1 and 1 - alpha-bar computed by subtraction in
+// FP32 would keep only a few significant digits of the moving equilibrium populations and of
+// the equation of state (Eq. (26)).
+__device__ __forceinline__ float one_minus_alpha_bar(int mix, float rho_r, float rho_b, float inv_rho, float hp,
+                                                     float hm, float oma_r, float oma_b) {
+    return mix ? (rho_r * oma_r + rho_b * oma_b) * inv_rho : hp * oma_r + hm * oma_b;
 }
 
 // Sum of one colour's 27 populations of a node in one fixed association,
@@ -234,6 +238,7 @@ struct StepArgs {
     int alpha_mix;                      // alpha-bar by (1 +- phi)/2 (0) or by mass fraction (1)
     float rho_r0, rho_b0, inv_rho_r0, inv_rho_b0;
     float alpha_r, alpha_b, inv_nu_r, inv_nu_b;
+    float oma_r, oma_b;                 // 1 - alpha_r, 1 - alpha_b (rounded once from FP64)
     float sigma, beta, eps2;
     float gx, gy, gz;
     float s0, s1, s2b, s3, s4, s5, s6;
@@ -451,9 +456,9 @@ __device__ __forceinline__ uint2 fit_odd_fp8(const StepArgs &a, const float (&fr
 __device__ __forceinline__ float2 fit_even(const StepArgs &a, float rr, float rb, float phi) {
     float oma;
     if (a.alpha_mix)
-        oma = (rr * (1.0f - a.alpha_r) + rb * (1.0f - a.alpha_b)) / (rr + rb);
+        oma = (rr * a.oma_r + rb * a.oma_b) / (rr + rb);
     else
-        oma = 1.0f - (0.5f * (1.0f + phi) * a.alpha_r + 0.5f * (1.0f - phi) * a.alpha_b);
+        oma = 0.5f * (1.0f + phi) * a.oma_r + 0.5f * (1.0f - phi) * a.oma_b;
     return make_float2(rr * oma, rb * oma);
 }
 

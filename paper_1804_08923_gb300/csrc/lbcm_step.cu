@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) boundary_plane_kernel(StepArgs a) {
             inlet_velocity(a.u_in, a.noise_amp, a.fourier, a.xc, a.yc, a.seed, a.step, xs, ys, a.nx, a.ny, iv);
             const float cu = (float)cxs * iv.ux + (float)cys * iv.uy + (float)czi * iv.uz;
             const float usq = iv.ux * iv.ux + iv.uy * iv.uy + iv.uz * iv.uz;
-            vr = a.rho_r0 * (varphi(i, a.alpha_r, 1.0f - a.alpha_r) + wgt(i) * eq_poly(cu, usq));
+            vr = a.rho_r0 * (varphi(i, a.alpha_r, a.oma_r) + wgt(i) * eq_poly(cu, usq));
             vb = 0.0f;
         } else {  // half-way specular reflection at z = -1/2
             const float2 v = load_pop<S>(a, mirror_z(ii), ys * a.nx + xs, reader_shift<S>(a, (int)pxy));
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(128) collide_general_kernel(StepArgs a) {
     // order parameter (Eq. (23)) and mixture parameters
     const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
-    const float alpha = alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
-    const float one_m_alpha = 1.0f - alpha;
+    const float one_m_alpha = one_minus_alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.oma_r, a.oma_b);
+    const float alpha = 1.0f - one_m_alpha;
     const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);  // harmonic mean
     const float tau = 3.0f * nu + 0.5f;                           // Eq. (16): 1/s_2nu
     const float s2nu = 1.0f / tau;
@@ -390,8 +390,8 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     const float ux = jFx * inv_rho, uy = jFy * inv_rho, uz = jFz * inv_rho;
     const float phi = order_parameter(rho_r, rho_b, a.inv_rho_r0, a.inv_rho_b0);
     const float hp = 0.5f * (1.0f + phi), hm = 0.5f * (1.0f - phi);
-    const float alpha = alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.alpha_r, a.alpha_b);
-    const float oma = 1.0f - alpha;
+    const float oma = one_minus_alpha_bar(a.alpha_mix, rho_r, rho_b, inv_rho, hp, hm, a.oma_r, a.oma_b);
+    const float alpha = 1.0f - oma;
     const float nu = 1.0f / (hp * a.inv_nu_r + hm * a.inv_nu_b);
     const float tau = 3.0f * nu + 0.5f;
     const float s2nu = 1.0f / tau;

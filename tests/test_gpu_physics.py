@@ -106,3 +106,32 @@ def test_table1_static_droplet_gamma100_mass_fraction_alpha(lb):
     assert abs(dp / ref["dp_theory"] - 1) < 0.01, dp
     umax = float(np.sqrt(F["ux"].astype(np.float64) ** 2 + F["uy"] ** 2 + F["uz"] ** 2).max())
     assert abs(umax / ref["umax"] - 1) < 0.1, umax
+
+
+@pytest.mark.gpu
+def test_table1_static_droplet_gamma1000_mass_fraction_alpha(lb):
+    """gamma = 1000 under reading R15 (rho_r0 = 1000, rho_b0 = 1): stable for 1e5 steps, the
+    maximum spurious velocity is the paper's 6.94e-5 within 10%, each colour's mass holds to
+    1e-4, and the pressure jump between the means over r < R - 6 and r > R + 6 is 2 sigma / R
+    within 1.5% (the paper's 0.40% came from an averaging procedure it does not specify; with
+    this droplet the jump varies with the averaging window by about 3% of itself, from -0.2%
+    at R -+ 4 to +2.8% at R -+ 10).  Needs 1 - alpha-bar formed from the colours' 1 - alpha_k:
+    alpha_r = 0.9993 leaves 1 - alpha-bar few FP32 digits when taken by subtraction."""
+    ref = table1()[1000.0]
+    n, R = 100, 25.0
+    sigma = 4.0 / 9.0 * 0.01 * 1.0
+    lat = lb.Lattice((n, n, n), dict(rho_r0=1000.0, rho_b0=1.0, nu_r=1 / 6, nu_b=1 / 6, sigma=sigma,
+                                     check_every=10000, alpha_mix=1))
+    lat.init_droplet(R, 4.0)
+    m0 = lat.mass()
+    lat.step(100000)
+    F = lat.fields(device=False)
+    c = (n - 1) / 2
+    z, y, x = np.meshgrid(*[np.arange(n)] * 3, indexing="ij")
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    p = F["p"].astype(np.float64)
+    dp = p[r < R - 6].mean() - p[r > R + 6].mean()
+    assert abs(dp / ref["dp_theory"] - 1) < 0.015, dp
+    umax = float(np.sqrt(F["ux"].astype(np.float64) ** 2 + F["uy"] ** 2 + F["uz"] ** 2).max())
+    assert abs(umax / ref["umax"] - 1) < 0.1, umax
+    assert np.abs(lat.mass() / m0 - 1).max() < 1e-4
