@@ -102,6 +102,11 @@ typedef struct {
                                theta the polar angle of the inlet column about the disc centre;
                                stored a_1, b_1, ..., a_8, b_8 (not in the paper: the parameters the
                                adjoint differentiates); all 0 = the paper's uniform inlet */
+    int32_t step_kernel;    /* lb_step with the paper's rates s3..s6 = 1: 0 = one launch per pass
+                               (the default, the faster on GB300); 1 = both passes in one cooperative
+                               launch of the fused step kernel, whose moments stay in L2 between the
+                               passes (less DRAM traffic, more synchronisation).  The same arithmetic,
+                               up to the compiler's choice of fused multiply-adds (FP32 rounding) */
     int32_t alpha_mix;      /* alpha-bar of Eqs. (20), (26): 0 = the printed interpolation by
                                (1 +- phi)/2; 1 = by mass fractions rho_k/rho, which makes the
                                equation of state additive over the colours (the reading under
@@ -252,8 +257,9 @@ LB_API lb_status lb_load(lb_ctx *ctx, const void *buf, size_t nbytes);
  * disables.  lb_profile_read synchronises, writes per-kernel total device milliseconds
  * and launch counts (index LB_KERNEL_*, up to n_kinds entries), and clears the record. */
 /* Index 1 is the step's gather pass: moment_kernel with the paper's rates s3..s6 = 1
- * (phase field and collision moments), phase_field_kernel otherwise. */
-enum { LB_KERNEL_BOUNDARY = 0, LB_KERNEL_GATHER = 1, LB_KERNEL_COLLIDE = 2, LB_NKERNELS = 3,
+ * (phase field and collision moments), phase_field_kernel otherwise; 2 the collision pass;
+ * 3 the fused step kernel, which runs both passes in one launch (params.step_kernel = 0). */
+enum { LB_KERNEL_BOUNDARY = 0, LB_KERNEL_GATHER = 1, LB_KERNEL_COLLIDE = 2, LB_KERNEL_STEP = 3, LB_NKERNELS = 4,
        LB_KERNEL_PHASE_FIELD = LB_KERNEL_GATHER };
 LB_API lb_status lb_profile_enable(lb_ctx *ctx, int32_t capacity);
 LB_API lb_status lb_profile_read(lb_ctx *ctx, double *ms, int64_t *launches, int32_t n_kinds);

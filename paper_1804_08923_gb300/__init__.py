@@ -214,10 +214,11 @@ class Lattice:
 
     def profile_read(self) -> dict:
         """{kernel name: (total device ms, launches)} since profile_enable / the last read."""
-        ms = (C.c_double * 3)()
-        cnt = (C.c_int64 * 3)()
-        _abi.check(self.lib.lb_profile_read(self._ctx, ms, cnt, 3))
-        return {_abi.KERNEL_NAMES[k]: (ms[k], int(cnt[k])) for k in range(3)}
+        nk = len(_abi.KERNEL_NAMES)
+        ms = (C.c_double * nk)()
+        cnt = (C.c_int64 * nk)()
+        _abi.check(self.lib.lb_profile_read(self._ctx, ms, cnt, nk))
+        return {_abi.KERNEL_NAMES[k]: (ms[k], int(cnt[k])) for k in range(nk)}
 
     @property
     def kernel_launches(self) -> int:

@@ -29,7 +29,7 @@ ADJ_NOUT = 21  # LB_ADJ_NOUT: J and 20 parameter gradients
 class FragmentStats(C.Structure):
     _fields_ = [("n_fragments", C.c_int64), ("column_volume", C.c_int64), ("total_volume", C.c_int64),
                 ("mass_median_diameter", C.c_double)]
-KERNEL_NAMES = ("boundary_plane_kernel", "moment_kernel", "collide_kernel")
+KERNEL_NAMES = ("boundary_plane_kernel", "moment_kernel", "collide_kernel", "step_kernel")
 
 
 class LBError(RuntimeError):
@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("s4", C.c_double), ("s5", C.c_double), ("s6", C.c_double),
                 ("u_in", C.c_double), ("d_in", C.c_double), ("noise_amp", C.c_double),
                 ("seed", C.c_uint64), ("eps_grad", C.c_double), ("storage", C.c_int32),
-                ("check_every", C.c_int32), ("fourier", C.c_double * 16), ("alpha_mix", C.c_int32)]
+                ("check_every", C.c_int32), ("fourier", C.c_double * 16), ("step_kernel", C.c_int32),
+                ("alpha_mix", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -134,7 +135,7 @@ def make_params(d: dict) -> Params:
             vals = list(v) + [0.0] * 16
             for m in range(16):
                 p.fourier[m] = float(vals[m])
-        elif k in ("seed", "storage", "check_every", "alpha_mix"):
+        elif k in ("seed", "storage", "check_every", "alpha_mix", "step_kernel"):
             setattr(p, k, int(v))
         elif k in dict(Params._fields_):
             setattr(p, k, float(v))

@@ -53,7 +53,7 @@ size_t phase_buffer_bytes(size_t nn, int storage) {
 }
 
 struct AuxLayout {
-    size_t disc, zin, zout, partial, total;
+    size_t disc, zin, zout, partial, done, ops, err, total;
 };
 
 AuxLayout aux_layout(const lb_grid &g) {
@@ -68,6 +68,12 @@ AuxLayout aux_layout(const lb_grid &g) {
     off = align_up(off + 18 * plane * sizeof(float));
     L.partial = off;
     off = align_up(off + 2 * kMassBlocks * sizeof(double) + 2 * sizeof(double));
+    L.done = off;  // fused step kernel: per-plane completion counters, item sequence, wait flag
+    off = align_up(off + (size_t)g.nz * sizeof(unsigned long long));
+    L.ops = off;
+    off = align_up(off + 2 * (size_t)g.nz * sizeof(int2));
+    L.err = off;
+    off = align_up(off + sizeof(int));
     L.total = off;
     return L;
 }
@@ -101,6 +107,7 @@ lb_status validate(const lb_grid *g, const lb_params *p) {
         return fail(LB_EINVAL, "storage must be LB_STORE_FP32, LB_STORE_FP16 or LB_STORE_FP16_FIT");
     if (p->check_every < 0) return fail(LB_EINVAL, "check_every must be >= 0");
     if (p->alpha_mix != 0 && p->alpha_mix != 1) return fail(LB_EINVAL, "alpha_mix must be 0 or 1");
+    if (p->step_kernel != 0 && p->step_kernel != 1) return fail(LB_EINVAL, "step_kernel must be 0 or 1");
     if (g->bc_zlo == LB_BC_INLET) {
         if (!(p->d_in >= 0) || !std::isfinite(p->d_in) || !std::isfinite(p->u_in) || !std::isfinite(p->noise_amp))
             return fail(LB_EINVAL, "inlet parameters must be finite, d_in >= 0");
@@ -126,6 +133,12 @@ struct lb_ctx {
     float2 *phase = nullptr;               // FP32: (phi, rho) of the current step
     float4 *ph4[2] = {nullptr, nullptr};   // FP16: (phi, rho, rho_r, rho_b) paired with pop[0], pop[1]
     float4 *mom = nullptr;                 // collision moments written and read within a step
+    // fused step kernel (both passes in one cooperative launch)
+    unsigned long long *fdone = nullptr;
+    int2 *fops = nullptr;
+    int *ferr = nullptr;
+    unsigned long long epoch = 0;          // fused launches so far (done[] counts accumulate)
+    int fgrid = 0, fnops = 0, flag = 0;    // grid, item sequence length and plane lag of the sequence
     float *hist[2] = {nullptr, nullptr};
     uint8_t *disc = nullptr;
     float *zin = nullptr, *zout = nullptr;
@@ -137,6 +150,7 @@ struct lb_ctx {
     long long nn = 0, plane = 0;
     long long launches = 0;
     std::vector<cudaEvent_t> prof_ev;  // 4 events per recorded step
+    std::vector<char> prof_fused;      // whether the recorded step ran the fused step kernel
     int prof_cap = 0, prof_used = 0;
     // discrete-adjoint workspace (one device allocation, grown on demand)
     struct {
@@ -434,6 +448,11 @@ lb_status setup_ctx(lb_ctx *c) {
     c->zout = (float *)(aux + L.zout);
     c->partial = (double *)(aux + L.partial);
     c->mom = (float4 *)c->bufs[5];
+    c->fdone = (unsigned long long *)(aux + L.done);
+    c->fops = (int2 *)(aux + L.ops);
+    c->ferr = (int *)(aux + L.err);
+    LB_CUDA(cudaMemsetAsync(c->fdone, 0, (size_t)g.nz * sizeof(unsigned long long), c->stream));
+    LB_CUDA(cudaMemsetAsync(c->ferr, 0, sizeof(int), c->stream));
     return upload_disc(c);
 }
 
@@ -524,7 +543,13 @@ lb_status run_mass(lb_ctx *c, double out[2], int z0 = 0, int z1 = -1) {
     c->launches += 2;
     LB_CUDA(cudaGetLastError());
     LB_CUDA(cudaMemcpyAsync(out, c->partial + 2 * kMassBlocks, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int err = 0;
+    LB_CUDA(cudaMemcpyAsync(&err, c->ferr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
+    if (err) {
+        cudaMemsetAsync(c->ferr, 0, sizeof(int), c->stream);
+        return fail(LB_ETIMEOUT, "a wait of the fused step kernel ran out: the state is not to be trusted");
+    }
     return LB_OK;
 }
 
@@ -730,6 +755,45 @@ lb_status lb_init(lb_ctx *c, int32_t kind, const double *args, int32_t nargs, co
     return LB_OK;
 }
 
+// Whether lb_step runs the fused step kernel: selected (step_kernel = 1) and the paper's rates.
+static bool use_fused(const lb_ctx *c) {
+    const lb_params &p = c->p;
+    return p.step_kernel == 1 && p.s3 == 1.0 && p.s4 == 1.0 && p.s5 == 1.0 && p.s6 == 1.0;
+}
+
+// Grid of the fused kernel (all blocks resident) and its item sequence: the gathers of plane
+// c + lag issued before the collisions of plane c, lag about two rounds of the grid's blocks
+// (with periodic z the collisions of plane 0 need the last plane and come last).  Once per
+// context, and again if the grid changes (force switched on or off by lb_set_params).
+static lb_status prepare_fused(lb_ctx *c, const StepArgs &a) {
+    int occ = 0, dev = 0, sms = 0;
+    LB_CUDA(fused_occupancy(a, c->p.storage, &occ));
+    LB_CUDA(cudaGetDevice(&dev));
+    LB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int nz = c->g.nz;
+    const long long T = (long long)((c->g.nx + 31) / 32) * ((c->g.ny + kFusedRows - 1) / kFusedRows);
+    const int grid = (int)std::min<long long>((long long)occ * sms, 2 * nz * T);
+    if (grid == c->fgrid && c->fnops > 0) return LB_OK;
+    c->fgrid = 0;
+    if (occ < 1) return LB_OK;  // cannot be resident: two launches
+    const bool pz = c->g.bc_zlo == LB_BC_PERIODIC;
+    const int lag = (int)std::max<long long>(1, std::min<long long>(nz - 1, (kFusedLagRounds * (long long)grid + T - 1) / T));
+    std::vector<int2> ops;
+    int g = 0;
+    for (int k = 0; k < nz; ++k) {
+        const int cz = pz ? (k + 1) % nz : k;  // periodic: plane 0 last
+        const int need = (pz && cz == 0) ? nz - 1 : std::min(nz - 1, cz + lag);
+        while (g <= need) ops.push_back(make_int2(0, g++));
+        ops.push_back(make_int2(1, cz));
+    }
+    LB_CUDA(cudaMemcpyAsync(c->fops, ops.data(), ops.size() * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    c->fnops = (int)ops.size();
+    c->flag = lag;
+    c->fgrid = grid;
+    return LB_OK;
+}
+
 // The end of a step: the state now at t+1, and the periodic mass check.
 static lb_status finish_step(lb_ctx *c) {
     c->cur ^= 1;
@@ -861,8 +925,27 @@ lb_status lb_step(lb_ctx *c, int64_t n) {
     for (int64_t s = 0; s < n; ++s) {
         StepArgs a = make_args(c);
         cudaEvent_t *ev = nullptr;
-        if (c->prof_used < c->prof_cap) ev = &c->prof_ev[4 * (size_t)c->prof_used++];
-        cudaError_t e = launch_step(a, c->p.storage, c->stream, ev, &c->launches);
+        if (c->prof_used < c->prof_cap) {
+            c->prof_fused[c->prof_used] = 0;
+            ev = &c->prof_ev[4 * (size_t)c->prof_used++];
+        }
+        cudaError_t e;
+        if (use_fused(c)) {
+            lb_status fs = prepare_fused(c, a);
+            if (fs != LB_OK) return fs;
+        }
+        if (c->fgrid > 0 && use_fused(c)) {
+            // done[z] grows by the plane's item count in every launch: this launch's target
+            const int ty = (c->g.ny + kFusedRows - 1) / kFusedRows;
+            const int T = ((c->g.nx + 31) / 32) * ty;
+            FusedCtl f{c->fdone, c->fops, c->ferr, (c->epoch + 1) * (unsigned long long)T, c->fnops,
+                       (c->g.nx + 31) / 32, ty, c->g.nx % 32 == 0};
+            if (ev) c->prof_fused[c->prof_used - 1] = 1;
+            e = launch_fused_step(a, c->p.storage, f, c->fgrid, c->stream, ev, &c->launches);
+            if (e == cudaSuccess) c->epoch += 1;
+        } else {
+            e = launch_step(a, c->p.storage, c->stream, ev, &c->launches);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "launch_step");
         lb_status st = finish_step(c);
         if (st != LB_OK) return st;
@@ -1031,6 +1114,7 @@ lb_status lb_profile_enable(lb_ctx *c, int32_t capacity) {
     LB_CUDA(cudaStreamSynchronize(c->stream));
     free_profile(c);
     c->prof_ev.resize(4 * (size_t)capacity);
+    c->prof_fused.assign((size_t)capacity, 0);
     for (auto &e : c->prof_ev) LB_CUDA(cudaEventCreate(&e));
     c->prof_cap = capacity;
     return LB_OK;
@@ -1039,17 +1123,19 @@ lb_status lb_profile_enable(lb_ctx *c, int32_t capacity) {
 lb_status lb_profile_read(lb_ctx *c, double *ms, int64_t *launches, int32_t n_kinds) {
     if (!c || !ms || !launches) return fail(LB_EINVAL, "ctx, ms and launches must not be NULL");
     LB_CUDA(cudaStreamSynchronize(c->stream));
-    double acc[LB_NKERNELS] = {0, 0, 0};
-    int64_t cnt[LB_NKERNELS] = {0, 0, 0};
+    double acc[LB_NKERNELS] = {0, 0, 0, 0};
+    int64_t cnt[LB_NKERNELS] = {0, 0, 0, 0};
     const bool planes = c->g.bc_zlo != LB_BC_PERIODIC || c->g.bc_zhi != LB_BC_PERIODIC;
     for (int s = 0; s < c->prof_used; ++s) {
         cudaEvent_t *ev = &c->prof_ev[4 * (size_t)s];
         float t;
-        for (int k = 0; k < LB_NKERNELS; ++k) {
+        for (int k = 0; k < 3; ++k) {
             if (k == LB_KERNEL_BOUNDARY && !planes) continue;
+            if (c->prof_fused[s] && k == LB_KERNEL_COLLIDE) continue;
+            const int kind = (c->prof_fused[s] && k == LB_KERNEL_GATHER) ? LB_KERNEL_STEP : k;
             LB_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
-            acc[k] += t;
-            cnt[k] += 1;
+            acc[kind] += t;
+            cnt[kind] += 1;
         }
     }
     for (int k = 0; k < n_kinds && k < LB_NKERNELS; ++k) {

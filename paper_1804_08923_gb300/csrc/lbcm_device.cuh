@@ -257,6 +257,7 @@ struct StepArgs {
     float *__restrict__ fm_out;
     unsigned long long seed;
     long long step;  // index of the step being taken (state t -> t+1 uses t)
+    int z_base;      // first plane of the launch (a launch covers planes z_base .. z_base + gridDim.z - 1)
 };
 
 // Shift weight varphi_i(alpha_k) of the FP16 encoding (same value at encode and decode).

@@ -15,6 +15,26 @@ enum { PASS_GATHER = 1, PASS_COLLIDE = 2, PASS_BOTH = 3 };
 cudaError_t launch_step(const StepArgs &a, int storage, cudaStream_t s, cudaEvent_t *ev, long long *launches,
                         int passes = PASS_BOTH);
 
+// Control block of the fused step kernel (both passes of a step in one cooperative launch,
+// paper rates only): the item sequence and the per-plane completion counters.
+struct FusedCtl {
+    unsigned long long *done;   // done[z]: gather items of plane z finished, summed over launches
+    const int2 *ops;            // (0 gather / 1 collision, plane) in issue order, nops entries
+    int *err;                   // set when a wait for a plane's gathers ran out
+    unsigned long long target;  // done[z] after this launch has gathered plane z
+    int nops, items_x, items_y; // items per row of tiles and rows of tiles of a plane
+    int discard;                // the moments' L2 lines may be dropped once read (nx % 32 == 0)
+};
+constexpr long long kFusedSpinLimit = 1ll << 24;  // ~1 s of 64 ns naps
+constexpr int kFusedRows = 32;                    // an item is a 32 x kFusedRows tile of a plane
+constexpr int kFusedLagRounds = 2;                // gathers lead the collisions by about this many rounds
+// Blocks per SM the fused kernel can keep resident (its cooperative grid is this times the SMs).
+cudaError_t fused_occupancy(const StepArgs &a, int storage, int *blocks_per_sm);
+// Boundary planes, then the fused kernel on `grid` blocks; ev as for launch_step (the fused
+// kernel's time lands between ev[1] and ev[2], the collision's slot stays empty).
+cudaError_t launch_fused_step(const StepArgs &a, int storage, const FusedCtl &f, int grid, cudaStream_t s,
+                              cudaEvent_t *ev, long long *launches);
+
 // Adjoint state and scratch of one reverse step (FP32 populations, paper rates).
 //   lp_in / lr_in   lambda of S(n+1): pushed part [27][NN] float2 and deferred density part [NN]
 //   lp_out / lr_out the same for S(n)

@@ -226,4 +226,36 @@ __device__ __forceinline__ Moments load_moments(const float4 *__restrict__ mom, 
     return Moments{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 }
 
+// The same for the fused step kernel, where the moments were written earlier in the same launch
+// and are read once: L1 is bypassed (ld.global.cg), and the L2 lines can be dropped afterwards.
+__device__ __forceinline__ Moments load_moments_once(const float4 *__restrict__ mom, size_t NN, int n) {
+    const float4 a = __ldcg(mom + n), b = __ldcg(mom + NN + n), c = __ldcg(mom + 2 * NN + n);
+    return Moments{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+}
+
+// L2 cache policy that keeps lines over evict-first and evict-normal ones.
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float4 *p, float4 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+// Moments stored with the evict-last policy (the fused step kernel reads them a few planes later).
+__device__ __forceinline__ void store_moments_keep(float4 *__restrict__ mom, size_t NN, int n, const Moments &m,
+                                                   unsigned long long pol) {
+    st_keep(mom + n, make_float4(m.rho_r, m.rho_b, m.sf, m.jx), pol);
+    st_keep(mom + NN + n, make_float4(m.jy, m.jz, m.pxx, m.pyy), pol);
+    st_keep(mom + 2 * NN + n, make_float4(m.pzz, m.pxy, m.pxz, m.pyz), pol);
+}
+// Drops the 128-byte L2 line at p (128-byte aligned) without writing it back: its contents
+// become undefined.  For data that is dead (read for the last time by every thread that
+// shares the line).
+__device__ __forceinline__ void l2_discard(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 }  // namespace lbcm

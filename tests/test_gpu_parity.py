@@ -505,3 +505,34 @@ def test_fitted_fp16_encoding_is_closer_to_the_oracle(lb, case):
         g.step(50)
         rms[st] = float(np.sqrt(np.mean(norm_err(g, ref, params) ** 2)))
     assert rms[2] < 0.6 * rms[1], rms
+
+
+@pytest.mark.parametrize("storage,bc", [(0, None), (1, None), (2, None), (0, (0, 0))])
+def test_fused_step_kernel_equals_the_two_launches(lb, storage, bc):
+    """The fused step kernel (one cooperative launch, params.step_kernel = 1) computes what the
+    two launches compute, node by node with the same device functions; the compiler contracts
+    some products into FMAs differently in the two kernels, so the populations agree to FP32
+    rounding (the normalised error of the parity tests within 1e-6 after 30 steps; with the
+    half-precision storages a last-bit FP32 difference can move a stored deviation by one FP16
+    step, so there the FP16 parity bar TOL16 applies), on the small jet (inlet, outflow, every
+    storage; nx = 64 drops the moments' L2 lines after use) and a periodic two-phase lattice
+    with gravity."""
+    if bc is None:
+        cfg = workloads.scaled_jet("jet96", 64, 34, 40, D=10)
+        grid, bc, params, shape = (64, 34, 40), cfg["bc"], dict(cfg["params"]), None
+    else:
+        shape = (24, 9, 40)
+        grid, params = (40, 9, 24), dict(rho_r0=1.0, rho_b0=0.5, nu_r=0.02, nu_b=0.08, sigma=0.003, g=(0.0, 0.0, 1e-5))
+    out = []
+    for sk in (0, 1):
+        lat = lb.Lattice(grid, dict(params, storage=storage, step_kernel=sk), bc=bc)
+        if shape is None:
+            lat.init_jet()
+        else:
+            lat.init_fields(*workloads.random_two_phase_fields(shape, 6, 1.0, 0.5, u_amp=0.03))
+        lat.step(30)
+        out.append(lat.populations(device=False))
+        lat.mass()  # reports a wait of the fused kernel that ran out (LB_ETIMEOUT)
+    w = oracle.weights()[None, :, None, None, None]
+    err = np.abs(out[0].astype(np.float64) - out[1]) / (w * max(params["rho_r0"], params["rho_b0"]))
+    assert err.max() < (1e-6 if storage == 0 else TOL16), err.max()
