@@ -474,7 +474,8 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
     const float frac_r = rho_r * inv_rho, frac_b = rho_b * inv_rho;
     const float seg0 = a.beta * rho_r * rho_b * inv_rho * inv_gm;
     // moving populations written (as read back), per colour, summed as MassAcc sums them
-    float sum_r = 0.0f, sum_b = 0.0f;
+    float2 sum = make_float2(0.0f, 0.0f);
+    const float2 frac = make_float2(frac_r, frac_b);
     // opposite pairs (i, i+1), c_{i+1} = -c_i: c.u, c.grad rho and c.grad phi change sign;
     // f^e splits into an even part (rest weight, quadratic terms, Phi) and an odd part
     // (linear and cubic terms), the perturbation is even and the recolouring flux odd.
@@ -501,13 +502,24 @@ __device__ __forceinline__ void collide_from_moments(const StepArgs &a, const Nb
         const float rm = fmaf(Ax.g0[2 - X], W0[2 - Y][2 - Z], fmaf(Ax.g1[2 - X], W1[2 - Y][2 - Z], g2c(cx(i)) * W2[2 - Y][2 - Z]));
         const float fsp = (even + odd) + rp, fsm = (even - odd) + rm;
         const float seg = seg0 * varphi(i, alpha, oma) * inv_cnorm(i) * cgp;
-        const float2 dp_ = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fsp, seg), fmaf(frac_b, fsp, -seg)),
-                                        dest_shift<S>(a, nb, i));
-        const float2 dm_ = store_pop<S>(a, i + 1, n, make_float2(fmaf(frac_r, fsm, -seg), fmaf(frac_b, fsm, seg)),
-                                        dest_shift<S>(a, nb, i + 1));
-        sum_r += dp_.x + dm_.x;
-        sum_b += dp_.y + dm_.y;
+        if constexpr (S == STORE_FP32) {
+            // both colours at once: packed FP32x2 operations, each lane rounded as the scalar
+            // ones (measured 2% faster for FP32, slower for the half-precision encodings)
+            const float2 vp = __ffma2_rn(frac, make_float2(fsp, fsp), make_float2(seg, -seg));
+            const float2 vm = __ffma2_rn(frac, make_float2(fsm, fsm), make_float2(-seg, seg));
+            store_pop<S>(a, i, n, vp, no_shift());
+            store_pop<S>(a, i + 1, n, vm, no_shift());
+            sum = __fadd2_rn(sum, __fadd2_rn(vp, vm));
+        } else {
+            const float2 dp_ = store_pop<S>(a, i, n, make_float2(fmaf(frac_r, fsp, seg), fmaf(frac_b, fsp, -seg)),
+                                            dest_shift<S>(a, nb, i));
+            const float2 dm_ = store_pop<S>(a, i + 1, n, make_float2(fmaf(frac_r, fsm, -seg), fmaf(frac_b, fsm, seg)),
+                                            dest_shift<S>(a, nb, i + 1));
+            sum.x += dp_.x + dm_.x;
+            sum.y += dp_.y + dm_.y;
+        }
     }
+    const float sum_r = sum.x, sum_b = sum.y;
     // Rest direction.  In exact arithmetic the step keeps each colour's mass at this node
     // (sum_i f_i^k* = rho_k), so the rest population is that mass minus the moving ones as
     // they will be read back; this equals Eqs. (33), (34) for i = 0 and keeps the FP32
