@@ -60,6 +60,9 @@ STORAGE_TEXT = {
 
 STORAGE_NAMES = {0: "fp32", 1: "fp16", 2: "fp16_fit"}
 BYTES = {0: (BYTES_STEP, BYTES_KERNEL), 1: (BYTES_STEP_FP16, BYTES_KERNEL_FP16), 2: (BYTES_STEP_FIT, BYTES_KERNEL_FIT)}
+# the fused step kernel (both passes in one launch) needs only the method's bytes
+for _s, (_b, _k) in BYTES.items():
+    _k["step_kernel"] = _b
 
 
 def init_state(lat, cfg):
@@ -183,30 +186,37 @@ def mass_drift_leg(lb, torch, name, steps_by_storage):
     return out
 
 
-def oracle_error_leg(lb, torch, steps=100):
+def oracle_error_leg(lb, torch, checkpoints=(100,)):
     """Every storage against the FP64 oracle on the 48x48x192 jet (D = 8, the 96x96x384
-    jet's lattice parameters): relative L2 error of the velocity and max |d phi| after
-    `steps` steps."""
+    jet's lattice parameters): relative L2 error of the velocity and max |d phi| at each
+    checkpoint step (all lattices stepped in lockstep)."""
     import oracle
     cfg = workloads.scaled_jet("jet96", 48, 48, 192, D=8)
     nx, ny, nz = cfg["grid"]
-    t0 = time.perf_counter()
     ref = oracle.Lattice(oracle.make_grid(nx, ny, nz, *cfg["bc"]), oracle.make_params(cfg["params"]))
     ref.init_jet()
-    ref.step(steps)
-    R = ref.fields()
-    oracle_s = time.perf_counter() - t0
-    out = {"workload": "jet 48x48x192, D=8, the 96x96x384 jet's lattice parameters", "steps": steps,
-           "oracle_seconds": oracle_s, "oracle_cores": oracle.num_threads()}
-    un = np.linalg.norm(R["u"])
-    for s in (0, 1, 2):
-        lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], s), bc=cfg["bc"])
+    lats = {s: lb.Lattice(cfg["grid"], with_storage(cfg["params"], s), bc=cfg["bc"]) for s in (0, 1, 2)}
+    for lat in lats.values():
         lat.init_jet()
-        lat.step(steps)
-        F = lat.fields(device=False)
-        du = np.stack([F[k].astype(np.float64) - R["u"][d] for d, k in enumerate(("ux", "uy", "uz"))])
-        out[STORAGE_NAMES[s]] = {"rel_u_l2": float(np.linalg.norm(du) / un),
-                                 "max_abs_dphi": float(np.abs(F["phi"] - R["phi"]).max())}
+    out = {"workload": "jet 48x48x192, D=8, the 96x96x384 jet's lattice parameters", "oracle_cores": oracle.num_threads(),
+           "oracle_seconds": 0.0, "checkpoints": []}
+    done = 0
+    for cp in checkpoints:
+        t0 = time.perf_counter()
+        ref.step(cp - done)
+        out["oracle_seconds"] += time.perf_counter() - t0
+        R = ref.fields()
+        un = np.linalg.norm(R["u"])
+        row = {"steps": cp}
+        for s, lat in lats.items():
+            lat.step(cp - done)
+            F = lat.fields(device=False)
+            du = np.stack([F[k].astype(np.float64) - R["u"][d] for d, k in enumerate(("ux", "uy", "uz"))])
+            row[STORAGE_NAMES[s]] = {"rel_u_l2": float(np.linalg.norm(du) / un),
+                                     "max_abs_dphi": float(np.abs(F["phi"] - R["phi"]).max())}
+        out["checkpoints"].append(row)
+        done = cp
+    for lat in lats.values():
         lat.close()
     return out
 
@@ -488,6 +498,9 @@ def main():
     ap.add_argument("--no-paper-workload", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 384x384x1536 mass-drift leg")
     ap.add_argument("--no-oracle-error", action="store_true")
+    ap.add_argument("--oracle-error-steps", default="100", help="checkpoints of the FP64-oracle error leg")
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1],
+                    help="headline loop: 0 one launch per pass (default), 1 the fused step kernel")
     ap.add_argument("--slabs", action="store_true",
                     help="with N > 1 ranks: split the one lattice into z-slabs (halo exchange over NCCL, strong "
                          "scaling) instead of one replica per rank")
@@ -535,7 +548,7 @@ def main():
     st = args.storage
     if args.slabs and world > 1:
         return run_slabs(args, cfg, lb, torch, dist, rank, world, local, barrier, max_over_ranks, peak)
-    lat = lb.Lattice(cfg["grid"], with_storage(cfg["params"], st), bc=cfg["bc"])
+    lat = lb.Lattice(cfg["grid"], dict(with_storage(cfg["params"], st), step_kernel=args.step_kernel), bc=cfg["bc"])
     init_state(lat, cfg)
     stream = lat.stream
 
@@ -656,7 +669,8 @@ def main():
             line["adjoint_forward_ratio"] = adjoint["ratio"]
         # ---- error of every storage against the FP64 oracle
         if not args.no_oracle_error:
-            line["error_vs_oracle"] = oracle_error_leg(lb, torch)
+            line["error_vs_oracle"] = oracle_error_leg(
+                lb, torch, [int(v) for v in args.oracle_error_steps.split(",") if v.strip()])
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
