@@ -762,8 +762,8 @@ static bool use_fused(const lb_ctx *c) {
 }
 
 // Grid of the fused kernel (all blocks resident) and its item sequence: the gathers of plane
-// c + lag issued before the collisions of plane c, lag about two rounds of the grid's blocks
-// (with periodic z the collisions of plane 0 need the last plane and come last).  Once per
+// c + lag issued before the collisions of plane c (with periodic z the collisions of plane 0
+// need the last plane and come last).  Once per
 // context, and again if the grid changes (force switched on or off by lb_set_params).
 static lb_status prepare_fused(lb_ctx *c, const StepArgs &a) {
     int occ = 0, dev = 0, sms = 0;
@@ -777,7 +777,10 @@ static lb_status prepare_fused(lb_ctx *c, const StepArgs &a) {
     c->fgrid = 0;
     if (occ < 1) return LB_OK;  // cannot be resident: two launches
     const bool pz = c->g.bc_zlo == LB_BC_PERIODIC;
-    const int lag = (int)std::max<long long>(1, std::min<long long>(nz - 1, (kFusedLagRounds * (long long)grid + T - 1) / T));
+    // the collisions of plane c follow the gathers of plane c + 1 by 2 lag - 1 planes of items
+    // (the sequence below); lag is chosen so that this is kFusedLeadPct / 100 rounds of the grid
+    const long long lead = ((long long)kFusedLeadPct * grid + 99) / 100;
+    const int lag = (int)std::max<long long>(1, std::min<long long>(nz - 1, ((lead + T - 1) / T + 2) / 2));
     std::vector<int2> ops;
     int g = 0;
     for (int k = 0; k < nz; ++k) {

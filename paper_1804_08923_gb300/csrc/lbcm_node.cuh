@@ -37,14 +37,16 @@ __device__ __forceinline__ void gather_one(const StepArgs &a, const Nbr &nb, int
 
 // Post-stream populations of node (x, y, z) (Eq. (9), pull form) with the boundary
 // planes of this step substituted.  Branches are uniform across a warp (one z per warp).
-template <int S, bool W>
+// kEdge = false: the caller knows that 0 < z < nz - 1, and the boundary-plane tests of every
+// direction drop out of the code.
+template <int S, bool W, bool kEdge = true>
 __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, float (&fr)[27], float (&fb)[27]) {
     const size_t P = (size_t)a.plane;
     const int N = a.nz - 1;
     const bool periodic_z = a.bc_zlo == BC_PERIODIC;
-    const bool lo = (z == 0) && !periodic_z;
-    const bool conv = (z == N) && a.bc_zhi == BC_CONVECTIVE;
-    const bool slip_hi = (z == N) && a.bc_zhi == BC_FREESLIP;
+    const bool lo = kEdge && (z == 0) && !periodic_z;
+    const bool conv = kEdge && (z == N) && a.bc_zhi == BC_CONVECTIVE;
+    const bool slip_hi = kEdge && (z == N) && a.bc_zhi == BC_FREESLIP;
     if (conv) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
@@ -119,11 +121,11 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
 // c_j, summed over the 13 pairs of opposite directions (j, j+1) as 3 w_j c_j (chi(x + c_j) -
 // chi(x - c_j)), so that a uniform field gives exactly zero and nearby values subtract
 // exactly.  Ghosts: z = -1 is phi = 1, rho = rho_r0 inside the inlet disc and the mirror of
-// z = 0 elsewhere; z = N + 1 mirrors z = N.
-template <int S>
+// z = 0 elsewhere; z = N + 1 mirrors z = N.  kEdge = false: the caller knows that z > 0.
+template <int S, bool kEdge = true>
 __device__ __forceinline__ void stencil_gradients(const StepArgs &a, const Nbr &nb, int z, float &gpx, float &gpy,
                                                   float &gpz, float &grx, float &gry, float &grz) {
-    const bool inlet_lo = z == 0 && a.bc_zlo == BC_INLET;
+    const bool inlet_lo = kEdge && z == 0 && a.bc_zlo == BC_INLET;
     float ph[27], rh[27];
 #pragma unroll
     for (int j = 1; j < 27; ++j) {

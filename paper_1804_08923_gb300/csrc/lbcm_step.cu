@@ -178,7 +178,10 @@ template <int S, bool W, bool kKeep>
 __device__ __forceinline__ void moment_at(const StepArgs &a, int x, int y, int z, unsigned long long pol) {
     const Nbr nb(a, x, y, z);
     float fr[27], fb[27];
-    gather<S, W>(a, nb, z, fr, fb);
+    if (z == 0 || z == a.nz - 1)
+        gather<S, W, true>(a, nb, z, fr, fb);
+    else
+        gather<S, W, false>(a, nb, z, fr, fb);
     Moments mo;
     moments_of(fr, fb, mo);
     const float rr = mo.rho_r, rb = mo.rho_b;
@@ -540,7 +543,10 @@ __device__ __forceinline__ void collide_at(const StepArgs &a, int x, int y, int 
     const Nbr nb(a, x, y, z);
     const Moments mo = kOnce ? load_moments_once(a.mom, (size_t)a.NN, nb.n) : load_moments(a.mom, (size_t)a.NN, nb.n);
     float gpx, gpy, gpz, grx, gry, grz;
-    stencil_gradients<S>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    if (z == 0)
+        stencil_gradients<S, true>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
+    else
+        stencil_gradients<S, false>(a, nb, z, gpx, gpy, gpz, grx, gry, grz);
     if constexpr (kRec) {
         a.grad4[nb.n] = make_float4(gpx, gpy, gpz, grx);
         a.grad2[nb.n] = make_float2(gry, grz);
