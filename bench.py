@@ -350,16 +350,28 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken from the
-    current kernel source (its sha256 is recorded in the summary)."""
+# The sources a kernel is compiled from, besides the shared headers: its translation unit, and
+# for the fused step kernel the host code that builds its item sequence.
+KERNEL_SOURCES = {"step_kernel": ("lbcm_step.cu", "lbcm_api.cu")}
+
+
+def kernel_source_sha(kernel: str, src: str = None) -> str:
+    """sha256 (16 hex digits) of the sources `kernel` is built from: every header of csrc/ and
+    the kernel's own translation unit(s), so that a summary stays valid while those are
+    unchanged."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1804_08923_gb300", "csrc")
+    src = src or os.path.join(ROOT, "paper_1804_08923_gb300", "csrc")
+    units = KERNEL_SOURCES.get(kernel, ("lbcm_adjoint.cu",) if kernel.startswith("adj_") else ("lbcm_step.cu",))
     h = hashlib.sha256()
     for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cuh", ".h")) or f in units:
             h.update(open(os.path.join(src, f), "rb").read())
-    sha = h.hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken from the
+    current sources of the kernel (their sha256 is recorded in the summary)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         kv = {}
@@ -367,7 +379,7 @@ def profile_traffic(kernel: str, workload: str):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("source_sha256_16") != sha:
+        if kv.get("source_sha256_16") != kernel_source_sha(kernel):
             return None
         return float(kv["dram_bytes_per_launch"])
     except Exception:

@@ -44,3 +44,22 @@ def test_step_bytes_match_the_layout(abi):
         assert step == 2 * pop + 2 * phase
         assert kern["collide_kernel"] == pop + phase + mom
         assert kern["moment_kernel"] == pop + 2 * phase + mom
+
+
+def test_profile_hash_covers_the_kernels_own_sources(tmp_path):
+    """A committed ncu summary stays valid while the sources its kernel is built from are
+    unchanged: the headers and the kernel's translation unit, not the others."""
+    import shutil
+    src = tmp_path / "csrc"
+    shutil.copytree(bench.os.path.join(bench.ROOT, "paper_1804_08923_gb300", "csrc"), src)
+    before = {k: bench.kernel_source_sha(k, str(src)) for k in ("collide_kernel", "step_kernel", "adj_collide_kernel")}
+    assert before["collide_kernel"] == bench.kernel_source_sha("moment_kernel_fp16", str(src))
+    assert len(set(before.values())) == 3
+    with open(src / "lbcm_adjoint.cu", "a") as f:
+        f.write("\n")
+    after = {k: bench.kernel_source_sha(k, str(src)) for k in before}
+    assert after["collide_kernel"] == before["collide_kernel"] and after["step_kernel"] == before["step_kernel"]
+    assert after["adj_collide_kernel"] != before["adj_collide_kernel"]
+    with open(src / "lbcm_device.cuh", "a") as f:
+        f.write("\n")
+    assert all(bench.kernel_source_sha(k, str(src)) != after[k] for k in after)
