@@ -139,6 +139,77 @@ __device__ __forceinline__ void m3uu(const RawMom &M, float ux, float uy, float 
     oz = M.m201 * xx + M.m021 * yy + M.m001 * zz + M.m111 * xy + M.m102 * xz + M.m012 * yz;
 }
 
+// Starts the copies of lambda_S(n+1) of node nb.n into shared memory: the pushed part of each
+// slot, and the deferred density adjoint of the node that reads the slot in step n+1 where a
+// pull reads it (else zero).  kEdge = false: the caller knows that 0 < z < N - 1, where every
+// slot is read.
+template <bool kEdge>
+__device__ __forceinline__ void adj_fetch(const StepArgs &a, const AdjArgs &g, const Nbr &nb, int z, float2 *L_s,
+                                          float2 *R_s) {
+    const bool own_in_disc = kEdge && a.bc_zlo == BC_INLET && z == 0 && a.disc[nb.pxy];
+    const unsigned sL = (unsigned)__cvta_generic_to_shared(L_s), sR = (unsigned)__cvta_generic_to_shared(R_s);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        cp_async8(sL + cell(i) * 128 * 8, g.lp_in + (size_t)i * a.NN + nb.n);
+        if (!kEdge || slot_read(a, i, z, own_in_disc))
+            cp_async8(sR + cell(i) * 128 * 8, g.lr_in + nb.nbr(i));
+        else
+            R_s[cell(i) * 128] = make_float2(0.0f, 0.0f);
+    }
+    cp_async_commit();
+}
+
+// The adjoints of the 54 gathered populations of a node, from the adjoints of its momentum,
+// raw second moment and colour densities.
+struct AdjPush {
+    float ljx, ljy, ljz, lQxx, lQyy, lQzz, lQxy, lQxz, lQyz, lrr, lrb;
+};
+
+// Pushes lambda_f_i of node nb.n to the slot its pull read: the transposed streaming, with the
+// mirror, the inlet disc and the convective outflow on the boundary planes.  kEdge = false:
+// the caller knows that 0 < z < N, and the boundary-plane tests of every direction drop out.
+template <bool W, bool kEdge>
+__device__ __forceinline__ void adj_push(const StepArgs &a, const AdjArgs &g, const Nbr &nb, int z, const AdjPush &q) {
+    const int N = a.nz - 1;
+    const bool pz = a.bc_zlo == BC_PERIODIC;
+    const bool conv_top = kEdge && !pz && z == N && a.bc_zhi == BC_CONVECTIVE;
+    const bool bot = kEdge && !pz && z == 0;
+    const bool slip_top = kEdge && !pz && z == N && a.bc_zhi == BC_FREESLIP;
+    const size_t P = (size_t)a.plane;
+#define PULLED(i) (W ? nb.pulled(i) : (i))
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const float c0 = (float)cx(i), c1 = (float)cy(i), c2 = (float)cz(i);
+        float lf = c0 * q.ljx + c1 * q.ljy + c2 * q.ljz;
+        lf += c0 * c0 * q.lQxx + c1 * c1 * q.lQyy + c2 * c2 * q.lQzz + c0 * c1 * q.lQxy + c0 * c2 * q.lQxz +
+              c1 * c2 * q.lQyz;
+        const float2 o = make_float2(lf + q.lrr, lf + q.lrb);
+        if (conv_top) {
+            // f(N) comes from the outflow rule: its adjoint goes to the boundary kernel; the
+            // slots the plain pulls would have read are read by nobody
+            g.lc[(size_t)i * P + nb.pxy] = o.x;
+            g.lc[(size_t)(27 + i) * P + nb.pxy] = o.y;
+            if (cz(i) >= 0) g.lp_out[(size_t)PULLED(i) * a.NN + nb.src(i)] = make_float2(0.0f, 0.0f);
+            if (cz(i) == 1) g.lp_out[(size_t)i * a.NN + nb.n] = make_float2(0.0f, 0.0f);
+        } else if (bot && cz(i) == 1) {
+            const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];  // source column (offsets, reflected)
+            const size_t slot = (size_t)mirror_z(PULLED(i)) * a.NN + ys + xs;
+            if (a.bc_zlo == BC_INLET && a.disc[ys + xs]) {
+                g.li[(size_t)zrank(i) * P + nb.pxy] = o.x;
+                g.lp_out[slot] = make_float2(0.0f, 0.0f);
+            } else {
+                g.lp_out[slot] = o;
+            }
+        } else if (slip_top && cz(i) == -1) {
+            const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];
+            g.lp_out[(size_t)mirror_z(PULLED(i)) * a.NN + (size_t)N * P + ys + xs] = o;
+        } else {
+            g.lp_out[(size_t)PULLED(i) * a.NN + nb.src(i)] = o;
+        }
+    }
+#undef PULLED
+}
+
 // ---------------------------------------------------------------- reverse collision
 // Every per-direction sum of the reverse pass is linear in a_i = (rho_r lS^r_i + rho_b lS^b_i)/rho
 // or b_i = lS^r_i - lS^b_i with coefficients that are polynomials in c_i times shell constants
@@ -150,25 +221,14 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
                                                  float (&part)[3], float2 *L_s, float2 *R_s) {
     const Nbr nb(a, x, y, z);
     const int N = a.nz - 1;
-    const bool pz = a.bc_zlo == BC_PERIODIC;
-    const bool conv_top = !pz && z == N && a.bc_zhi == BC_CONVECTIVE;
-    const bool own_in_disc = !pz && z == 0 && a.bc_zlo == BC_INLET && a.disc[nb.pxy];
 
     // lambda of S(n+1) for the 27 directions: the pushed and the deferred parts are copied
     // asynchronously into this thread's two columns of shared memory (tensor layout), and the
     // node's recorded forward quantities are loaded and used while they are in flight
-    {
-        const unsigned sL = (unsigned)__cvta_generic_to_shared(L_s), sR = (unsigned)__cvta_generic_to_shared(R_s);
-#pragma unroll
-        for (int i = 0; i < 27; ++i) {
-            cp_async8(sL + cell(i) * 128 * 8, g.lp_in + (size_t)i * a.NN + nb.n);
-            if (slot_read(a, i, z, own_in_disc))
-                cp_async8(sR + cell(i) * 128 * 8, g.lr_in + nb.nbr(i));
-            else
-                R_s[cell(i) * 128] = make_float2(0.0f, 0.0f);
-        }
-        cp_async_commit();
-    }
+    if (z == 0 || z >= N - 1)
+        adj_fetch<true>(a, g, nb, z, L_s, R_s);
+    else
+        adj_fetch<false>(a, g, nb, z, L_s, R_s);
 
     // ---- the forward step's collision inputs of this node (recorded in the recompute)
     const size_t NN = (size_t)a.NN;
@@ -434,40 +494,13 @@ __device__ __forceinline__ void adj_collide_node(const StepArgs &a, const AdjArg
 
     // ---- outputs: lambda_f_i^k = lambda_j . c_i + c_i Lambda_P c_i + lambda_rho_k, pushed to the
     // slot the pull read (with side walls, W: the reflected direction, selected at run time)
-#define PULLED(i) (W ? nb.pulled(i) : (i))
     g.lga[nb.n] = make_float4(lgpx, lgpy, lgpz, lgrx);
     g.lgb[nb.n] = make_float2(lgry, lgrz);
-    const size_t P = (size_t)a.plane;
-#pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        const float c0 = (float)cx(i), c1 = (float)cy(i), c2 = (float)cz(i);
-        float lf = c0 * ljx + c1 * ljy + c2 * ljz;
-        lf += c0 * c0 * lQxx + c1 * c1 * lQyy + c2 * c2 * lQzz + c0 * c1 * lQxy + c0 * c2 * lQxz + c1 * c2 * lQyz;
-        const float2 o = make_float2(lf + lrr, lf + lrb);
-        if (conv_top) {
-            // f(N) comes from the outflow rule: its adjoint goes to the boundary kernel; the
-            // slots the plain pulls would have read are read by nobody
-            g.lc[(size_t)i * P + nb.pxy] = o.x;
-            g.lc[(size_t)(27 + i) * P + nb.pxy] = o.y;
-            if (cz(i) >= 0) g.lp_out[(size_t)PULLED(i) * a.NN + nb.src(i)] = make_float2(0.0f, 0.0f);
-            if (cz(i) == 1) g.lp_out[(size_t)i * a.NN + nb.n] = make_float2(0.0f, 0.0f);
-        } else if (!pz && z == 0 && cz(i) == 1) {
-            const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];  // source column (offsets, reflected)
-            const size_t slot = (size_t)mirror_z(PULLED(i)) * a.NN + ys + xs;
-            if (a.bc_zlo == BC_INLET && a.disc[ys + xs]) {
-                g.li[(size_t)zrank(i) * P + nb.pxy] = o.x;
-                g.lp_out[slot] = make_float2(0.0f, 0.0f);
-            } else {
-                g.lp_out[slot] = o;
-            }
-        } else if (!pz && z == N && cz(i) == -1 && a.bc_zhi == BC_FREESLIP) {
-            const int xs = nb.xo[cx(i) + 1], ys = nb.yo[cy(i) + 1];
-            g.lp_out[(size_t)mirror_z(PULLED(i)) * a.NN + (size_t)N * P + ys + xs] = o;
-        } else {
-            g.lp_out[(size_t)PULLED(i) * a.NN + nb.src(i)] = o;
-        }
-    }
-#undef PULLED
+    const AdjPush o{ljx, ljy, ljz, lQxx, lQyy, lQzz, lQxy, lQxz, lQyz, lrr, lrb};
+    if (z == 0 || z == N)
+        adj_push<W, true>(a, g, nb, z, o);
+    else
+        adj_push<W, false>(a, g, nb, z, o);
 }
 
 #ifndef LBCM_ADJ_MIN_BLOCKS
