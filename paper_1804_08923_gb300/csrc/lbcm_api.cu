@@ -761,6 +761,14 @@ static bool use_fused(const lb_ctx *c) {
     return p.step_kernel == 1 && p.s3 == 1.0 && p.s4 == 1.0 && p.s5 == 1.0 && p.s6 == 1.0;
 }
 
+// A collision item of the fused kernel comes kFusedLeadPct / 100 rounds of the grid's blocks
+// after the gather items of the next plane, so that those are usually complete when it starts;
+// the moments in flight (held in L2) grow with this lead.  Settable at build time.
+#ifndef LBCM_FUSED_LEAD_PCT
+#define LBCM_FUSED_LEAD_PCT 100
+#endif
+constexpr int kFusedLeadPct = LBCM_FUSED_LEAD_PCT;
+
 // Grid of the fused kernel (all blocks resident) and its item sequence: the gathers of plane
 // c + lag issued before the collisions of plane c (with periodic z the collisions of plane 0
 // need the last plane and come last).  Once per

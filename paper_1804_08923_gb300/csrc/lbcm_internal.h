@@ -27,17 +27,12 @@ struct FusedCtl {
 };
 constexpr long long kFusedSpinLimit = 1ll << 24;  // ~1 s of 64 ns naps
 // An item is a 32 x kFusedRows tile of a plane (a multiple of 4: each of the 4 warps walks
-// every fourth row).  A collision item comes kFusedLeadPct / 100 rounds of the grid's blocks
-// after the gather items of the next plane, so that those are usually complete when it starts;
-// the moments in flight (and held in L2) grow with this lead.  Both can be set at build time.
+// every fourth row); settable at build time.  The lead of the gathers over the collisions is
+// host code (lbcm_api.cu).
 #ifndef LBCM_FUSED_ROWS
 #define LBCM_FUSED_ROWS 32
 #endif
-#ifndef LBCM_FUSED_LEAD_PCT
-#define LBCM_FUSED_LEAD_PCT 250
-#endif
 constexpr int kFusedRows = LBCM_FUSED_ROWS;
-constexpr int kFusedLeadPct = LBCM_FUSED_LEAD_PCT;
 static_assert(kFusedRows % 4 == 0 && kFusedRows >= 4, "fused item rows must be a positive multiple of 4");
 // Blocks per SM the fused kernel can keep resident (its cooperative grid is this times the SMs).
 cudaError_t fused_occupancy(const StepArgs &a, int storage, int *blocks_per_sm);

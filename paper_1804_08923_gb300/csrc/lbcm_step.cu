@@ -572,12 +572,13 @@ __global__ void __launch_bounds__(128, (S == STORE_FP32 ? 6 : (S == STORE_FP16 ?
 // are counted complete.  Every item waits only for items earlier in the sequence, held by
 // resident blocks that do not wait on it, so the waits end; each is also bounded, and on running
 // out it sets f.err (reported by the next synchronising call) and goes on.  With the lag (about
-// two rounds of G items) a collision item rarely waits, and a plane's 48-byte moments are read a
+// one round of G items) a collision item seldom waits, and a plane's 48-byte moments are read a
 // few planes after they were written: they stay in L2 (stored with the evict-last policy) and,
-// read once, their lines are dropped without being written back.  The step then moves about the
-// method's 448 bytes a node from DRAM (432 measured on the 96x96x384 jet, against 521 for the
-// two launches) but its blocks synchronise at every item: on GB300 it runs 7% slower than the
-// two launches, which stay the default.
+// read once, their lines are dropped without being written back.  The step then moves close to
+// the method's 448 bytes a node from DRAM (450-500 measured, against 522 for the two launches),
+// but its blocks wait and synchronise at every item and it streams at a lower fraction of the
+// bandwidth: on GB300 it is 3% slower than the two launches on the 256x256x1024 jet and about
+// level with them on smaller ones, and the two launches stay the default.
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
