@@ -608,15 +608,21 @@ def main():
     outs = {k: torch.empty(shp, dtype=torch.float32).pin_memory() for k in ("rho_r", "rho_b", "ux", "uy", "uz")}
     # three repeats of the whole job, the median reported (the host side of the copies varies
     # from one box to the next)
-    reps = []
-    for _ in range(3):
-        barrier()
-        t0 = time.perf_counter()
-        lat.init_fields(rr.numpy(), rb.numpy(), uu.numpy())
-        lat.step(args.steps)
-        got = lat.fields(names=tuple(outs), device=False, out={k: v.numpy() for k, v in outs.items()})
-        barrier()
-        reps.append(max_over_ranks(time.perf_counter() - t0))
+    reps, parts = [], []
+    with ClockSampler(local) as clk_e2e:
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            lat.init_fields(rr.numpy(), rb.numpy(), uu.numpy())  # returns once the fields are copied
+            t1 = time.perf_counter()
+            lat.step(args.steps)
+            barrier()
+            t2 = time.perf_counter()
+            got = lat.fields(names=tuple(outs), device=False, out={k: v.numpy() for k, v in outs.items()})
+            barrier()
+            t3 = time.perf_counter()
+            reps.append(max_over_ranks(t3 - t0))
+            parts.append([round(t1 - t0, 4), round(t2 - t1, 4), round(t3 - t2, 4)])
     e2e_s = sorted(reps)[1]
     h2d = 5 * 4 * nodes
     d2h = 4 * nodes * len(got)
@@ -624,7 +630,8 @@ def main():
                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                    "job": f"host fields -> lb_init, {args.steps} x lb_step, lb_fields -> host (pinned); "
                           "median of 3 repeats",
-                   "repeats_s": reps}
+                   "repeats_s": reps, "repeat_parts_s": {"init, steps, fields": parts},
+                   "clocks": clk_e2e.summary()}
     lat.close()
     del lat, rr, rb, uu, outs
     torch.cuda.empty_cache()

@@ -256,9 +256,10 @@ LB_API lb_status lb_load(lb_ctx *ctx, const void *buf, size_t nbytes);
  * at most `capacity` steps (events are created here, not during stepping); capacity 0
  * disables.  lb_profile_read synchronises, writes per-kernel total device milliseconds
  * and launch counts (index LB_KERNEL_*, up to n_kinds entries), and clears the record. */
-/* Index 1 is the step's gather pass: moment_kernel with the paper's rates s3..s6 = 1
- * (phase field and collision moments), phase_field_kernel otherwise; 2 the collision pass;
- * 3 the fused step kernel, which runs both passes in one launch (params.step_kernel = 0). */
+/* Index 0 is the boundary planes (one of two kernels, chosen by the plane size); 1 the step's
+ * gather pass: moment_kernel with the paper's rates s3..s6 = 1 (phase field and collision
+ * moments), phase_field_kernel otherwise; 2 the collision pass; 3 the fused step kernel, which
+ * runs both passes in one launch (params.step_kernel = 1). */
 enum { LB_KERNEL_BOUNDARY = 0, LB_KERNEL_GATHER = 1, LB_KERNEL_COLLIDE = 2, LB_KERNEL_STEP = 3, LB_NKERNELS = 4,
        LB_KERNEL_PHASE_FIELD = LB_KERNEL_GATHER };
 LB_API lb_status lb_profile_enable(lb_ctx *ctx, int32_t capacity);

@@ -29,7 +29,7 @@ ADJ_NOUT = 21  # LB_ADJ_NOUT: J and 20 parameter gradients
 class FragmentStats(C.Structure):
     _fields_ = [("n_fragments", C.c_int64), ("column_volume", C.c_int64), ("total_volume", C.c_int64),
                 ("mass_median_diameter", C.c_double)]
-KERNEL_NAMES = ("boundary_plane_kernel", "moment_kernel", "collide_kernel", "step_kernel")
+KERNEL_NAMES = ("boundary_kernel", "moment_kernel", "collide_kernel", "step_kernel")
 
 
 class LBError(RuntimeError):

@@ -23,7 +23,7 @@ __host__ __device__ constexpr int csq(int i) { return cx(i) * cx(i) + cy(i) * cy
 // position of direction i in the 3x3x3 tensor-product array [cx+1][cy+1][cz+1]
 __host__ __device__ constexpr int cell(int i) { return (cx(i) + 1) * 9 + (cy(i) + 1) * 3 + (cz(i) + 1); }
 // Inverse maps as packed tables built at compile time, so that a call with a run-time
-// argument (a lane's direction in the boundary kernels) is a shift and a mask, not a loop.
+// argument (a direction reflected at a side wall at run time) is a shift and a mask, not a loop.
 __host__ __device__ constexpr int dir_search(int x, int y, int z) {
     int r = 0;
     for (int j = 0; j < 27; ++j)
