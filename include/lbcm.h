@@ -45,7 +45,7 @@ typedef enum {
     LB_ENOMEM = 2,     /* device allocation failed */
     LB_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
     LB_EUNSTABLE = 4,  /* a periodic check found a non-finite colour mass */
-    LB_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    LB_ETIMEOUT = 5,   /* a bounded device wait gave up (the fused step kernel's plane waits) */
     LB_ESTATE = 6,     /* call out of order (e.g. lb_step before lb_init) */
     LB_ENOTIMPL = 7    /* entry point declared but not provided by this build */
 } lb_status;
@@ -267,6 +267,18 @@ LB_API lb_status lb_profile_read(lb_ctx *ctx, double *ms, int64_t *launches, int
 
 /* Total number of kernels this context has launched since creation. */
 LB_API int64_t lb_kernel_launches(const lb_ctx *ctx);
+
+/* Self-test of a failure path on the device.  which = LB_SELFTEST_FUSED_WAIT runs, on the
+ * context's stream, the plane wait of the fused step kernel (params.step_kernel = 1) against a
+ * completion target that no gather reaches: the wait gives up after its limit (1 s of the
+ * device's global timer), sets the context's error flag and returns, as a wait that ran out
+ * inside the fused kernel would.  The call then reads and clears the flag:
+ *   *result  LB_ETIMEOUT if the wait gave up and reported it (the expected outcome), else LB_OK
+ *   *ms      how long the wait lasted, milliseconds
+ * The context's state is untouched and the context stays usable.  Synchronises.  Returns
+ * LB_EINVAL for an unknown `which` or NULL outputs, LB_ESTATE inside a split step. */
+enum { LB_SELFTEST_FUSED_WAIT = 1 };
+LB_API lb_status lb_selftest(lb_ctx *ctx, int32_t which, int32_t *result, double *ms);
 
 /* Replaces the parameters of an existing context (same grid and storage; the state is kept;
  * with FP16 storage rho_r0 and rho_b0 stay fixed once the context holds a state).

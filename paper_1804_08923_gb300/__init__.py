@@ -152,6 +152,13 @@ class Lattice:
         _abi.check(self.lib.lb_mass_planes(self._ctx, int(z_begin), int(z_end), out))
         return np.array([out[0], out[1]])
 
+    def selftest_fused_wait(self):
+        """Runs the fused step kernel's plane wait against a target nothing reaches (lb_selftest):
+        returns (status the host read, milliseconds the wait lasted)."""
+        res, ms = C.c_int32(), C.c_double()
+        _abi.check(self.lib.lb_selftest(self._ctx, _abi.SELFTEST_FUSED_WAIT, C.byref(res), C.byref(ms)))
+        return int(res.value), float(ms.value)
+
     @property
     def step_count(self) -> int:
         return int(self.lib.lb_step_count(self._ctx))

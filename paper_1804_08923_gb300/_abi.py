@@ -21,7 +21,8 @@ EXPORTS = ("lb_params_default", "lb_buffer_sizes", "lb_create", "lb_create_with_
            "lb_step_count", "lb_fields", "lb_populations", "lb_history", "lb_mass", "lb_mass_noalloc", "lb_save", "lb_load",
            "lb_profile_enable", "lb_profile_read", "lb_kernel_launches", "lb_set_params", "lb_adjoint",
            "lb_adjoint_state", "lb_fragments", "lb_step_gather", "lb_step_collide", "lb_halo_bytes",
-           "lb_halo_pack", "lb_halo_unpack", "lb_mass_planes", "lb_last_error", "lb_destroy")
+           "lb_halo_pack", "lb_halo_unpack", "lb_mass_planes", "lb_selftest", "lb_last_error", "lb_destroy")
+SELFTEST_FUSED_WAIT = 1
 HALO_POPULATIONS, HALO_PHASE = 0, 1
 ADJ_NOUT = 21  # LB_ADJ_NOUT: J and 20 parameter gradients
 

@@ -1159,6 +1159,31 @@ lb_status lb_profile_read(lb_ctx *c, double *ms, int64_t *launches, int32_t n_ki
 
 int64_t lb_kernel_launches(const lb_ctx *c) { return c ? c->launches : -1; }
 
+lb_status lb_selftest(lb_ctx *c, int32_t which, int32_t *result, double *ms) {
+    if (!c || !result || !ms) return fail(LB_EINVAL, "ctx, result and ms must not be NULL");
+    if (which != LB_SELFTEST_FUSED_WAIT) return fail(LB_EINVAL, "unknown self-test");
+    if (c->half) return fail(LB_ESTATE, "lb_selftest inside a split step");
+    // the fused kernel's wait on plane 0 with a target no counter reaches; the scratch of the
+    // mass reduction takes the waited time
+    FusedCtl f{};
+    f.done = c->fdone;
+    f.err = c->ferr;
+    f.target = ~0ull;
+    unsigned long long *ns = reinterpret_cast<unsigned long long *>(c->partial);
+    LB_CUDA(launch_fused_wait_probe(f, ns, c->stream));
+    c->launches += 1;
+    unsigned long long waited = 0;
+    int err = 0;
+    LB_CUDA(cudaMemcpyAsync(&waited, ns, sizeof(waited), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaMemcpyAsync(&err, c->ferr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    LB_CUDA(cudaMemsetAsync(c->ferr, 0, sizeof(int), c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    *result = err ? LB_ETIMEOUT : LB_OK;
+    *ms = (double)waited * 1e-6;
+    return LB_OK;
+}
+
 lb_status lb_adjoint(lb_ctx *c, int32_t objective, int64_t T, const double *obj_args, double *grad_out,
                      int32_t n_grad) {
     if (!c || !obj_args || !grad_out) return fail(LB_EINVAL, "ctx, obj_args and grad_out must not be NULL");

@@ -25,7 +25,8 @@ struct FusedCtl {
     int nops, items_x, items_y; // items per row of tiles and rows of tiles of a plane
     int discard;                // the moments' L2 lines may be dropped once read (nx % 32 == 0)
 };
-constexpr long long kFusedSpinLimit = 1ll << 24;  // ~1 s of 64 ns naps
+constexpr unsigned long long kFusedWaitNs = 1000000000ull;  // a plane wait gives up after 1 s
+constexpr long long kFusedSpinLimit = 1ll << 26;            // and after this many polls (> 4 s)
 // An item is a 32 x kFusedRows tile of a plane (a multiple of 4: each of the 4 warps walks
 // every fourth row); settable at build time.  The lead of the gathers over the collisions is
 // host code (lbcm_api.cu).
@@ -40,6 +41,9 @@ cudaError_t fused_occupancy(const StepArgs &a, int storage, int *blocks_per_sm);
 // kernel's time lands between ev[1] and ev[2], the collision's slot stays empty).
 cudaError_t launch_fused_step(const StepArgs &a, int storage, const FusedCtl &f, int grid, cudaStream_t s,
                               cudaEvent_t *ev, long long *launches);
+// One thread runs the fused kernel's plane wait with f.target out of reach: it gives up after
+// the wait's limit and sets *f.err; *ns receives the time it waited.
+cudaError_t launch_fused_wait_probe(const FusedCtl &f, unsigned long long *ns, cudaStream_t s);
 
 // Adjoint state and scratch of one reverse step (FP32 populations, paper rates).
 //   lp_in / lr_in   lambda of S(n+1): pushed part [27][NN] float2 and deferred density part [NN]

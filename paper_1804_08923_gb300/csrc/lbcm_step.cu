@@ -704,19 +704,41 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Waits until the gathers of planes p0, p1, p2 are all counted complete (the three counters
-// are read together); bounded, see above.
+// are read together).  Bounded by time, kFusedWaitNs, and as a backstop by the number of
+// polls; on giving up it sets f.err and returns.
 __device__ __forceinline__ void wait_planes(const FusedCtl &f, int p0, int p1, int p2) {
+    const unsigned long long t0 = global_ns();
     for (long long k = 0;; ++k) {
         const unsigned long long d0 = ld_acquire_u64(f.done + p0), d1 = ld_acquire_u64(f.done + p1),
                                  d2 = ld_acquire_u64(f.done + p2);
         if (d0 >= f.target && d1 >= f.target && d2 >= f.target) return;
-        if (k > kFusedSpinLimit) {
+        if (global_ns() - t0 > kFusedWaitNs || k > kFusedSpinLimit) {
             atomicExch(f.err, 1);
             return;
         }
         __nanosleep(64);
     }
+}
+
+// The fused kernel's wait on a plane that no gather completes (f.target beyond reach): one
+// thread gives up after the wait's limit, sets f.err and records the time it waited in *ns.
+__global__ void fused_wait_probe_kernel(FusedCtl f, unsigned long long *ns) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long t0 = global_ns();
+    wait_planes(f, 0, 0, 0);
+    *ns = global_ns() - t0;
+}
+
+cudaError_t launch_fused_wait_probe(const FusedCtl &f, unsigned long long *ns, cudaStream_t s) {
+    fused_wait_probe_kernel<<<1, 32, 0, s>>>(f, ns);
+    return cudaGetLastError();
 }
 
 template <bool kForce, int S, bool W>

@@ -109,3 +109,9 @@ def test_product_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.lower(), f
+
+
+def test_selftest_rejects_a_missing_context(lib):
+    import ctypes as C
+    res, ms = C.c_int32(), C.c_double()
+    assert lib.lb_selftest(None, 1, C.byref(res), C.byref(ms)) == 1  # LB_EINVAL, no GPU work

@@ -536,3 +536,25 @@ def test_fused_step_kernel_equals_the_two_launches(lb, storage, bc):
     w = oracle.weights()[None, :, None, None, None]
     err = np.abs(out[0].astype(np.float64) - out[1]) / (w * max(params["rho_r0"], params["rho_b0"]))
     assert err.max() < (1e-6 if storage == 0 else TOL16), err.max()
+
+
+@pytest.mark.parametrize("storage,walls", [(0, False), (0, True), (1, False), (2, True)])
+def test_large_plane_jet_boundaries_parity(lb, storage, walls):
+    """The boundary planes on a plane of 160 x 160 = 25 600 columns, which the library treats
+    with its thread-per-column kernel (planes of at least 24 576 columns; the other parity cases
+    use the warp-per-column kernel): inlet disc with noise and convective outflow, optionally
+    free-slip side walls, 6 steps, populations and the outflow history plane against the oracle."""
+    cfg = workloads.scaled_jet("jet96", 160, 160, 8, D=40)
+    params = dict(cfg["params"], storage=storage)
+    shape = (8, 160, 160)
+    bc = tuple(cfg["bc"]) + ((1, 1) if walls else ())
+    gpu, ref = pair(lb, shape, params, bc=bc)
+    gpu.init_jet()
+    ref.init_jet()
+    run_both(gpu, ref, 6)
+    tol = TOL if storage == 0 else TOL16
+    e = norm_err(gpu, ref, params)
+    assert e.max() < tol, e.max()
+    h = gpu.history().astype(np.float64)
+    assert np.abs(h - ref.hist).max() / max(params["rho_r0"], params["rho_b0"]) < tol
+    assert gpu.fields(device=False)["rho_r"].sum() > 0.5  # red has entered
