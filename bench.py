@@ -608,6 +608,24 @@ def main():
     outs = {k: torch.empty(shp, dtype=torch.float32).pin_memory() for k in ("rho_r", "rho_b", "ux", "uy", "uz")}
     # three repeats of the whole job, the median reported (the host side of the copies varies
     # from one box to the next)
+    # the box's own pinned-copy bandwidth, outside the timed region, for reading the e2e figure
+    host_gbs = None
+    try:
+        dev = torch.empty(5 * nodes, dtype=torch.float32, device=f"cuda:{local}")
+        hbuf = torch.empty(5 * nodes, dtype=torch.float32).pin_memory()
+        bw = []
+        for src, dst in ((hbuf, dev), (dev, hbuf)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            tc = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            bw.append(round(5 * nodes * 4 / (time.perf_counter() - tc) / 1e9, 1))
+        host_gbs = {"h2d": bw[0], "d2h": bw[1]}
+        del dev, hbuf
+        torch.cuda.empty_cache()
+    except Exception:
+        pass
     reps, parts = [], []
     with ClockSampler(local) as clk_e2e:
         for _ in range(3):
@@ -631,7 +649,7 @@ def main():
                    "job": f"host fields -> lb_init, {args.steps} x lb_step, lb_fields -> host (pinned); "
                           "median of 3 repeats",
                    "repeats_s": reps, "repeat_parts_s": {"init, steps, fields": parts},
-                   "clocks": clk_e2e.summary()}
+                   "clocks": clk_e2e.summary(), "pinned_copy_gbs_torch": host_gbs}
     lat.close()
     del lat, rr, rb, uu, outs
     torch.cuda.empty_cache()

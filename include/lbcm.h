@@ -47,7 +47,7 @@ typedef enum {
     LB_EUNSTABLE = 4,  /* a periodic check found a non-finite colour mass */
     LB_ETIMEOUT = 5,   /* a bounded device wait gave up (the fused step kernel's plane waits) */
     LB_ESTATE = 6,     /* call out of order (e.g. lb_step before lb_init) */
-    LB_ENOTIMPL = 7    /* entry point declared but not provided by this build */
+    LB_ENOTIMPL = 7    /* entry point declared but not provided by the library */
 } lb_status;
 
 /* Boundary kinds.  z_lo: PERIODIC, FREESLIP or INLET; z_hi: PERIODIC, FREESLIP or CONVECTIVE;
