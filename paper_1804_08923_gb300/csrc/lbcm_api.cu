@@ -511,7 +511,13 @@ StepArgs make_args(const lb_ctx *c) {
     a.inv_dev_scale = std::ldexp(1.0f, -eh);
     a.v_scale = std::ldexp(1.0f, ev);
     const double wq[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
-    for (int q = 0; q < 4; ++q) a.wv[q] = (float)std::ldexp(wq[q], -ev);
+    for (int q = 0; q < 4; ++q) {
+        a.wv[q] = (float)std::ldexp(wq[q], -ev);
+        // the prediction's constants in half precision (k_q of Eq. (20) and w_q / S_v)
+        const float k = (float)kq[q];
+        a.kqh[q] = __floats2half2_rn(k, k);
+        a.wvh[q] = __floats2half2_rn(a.wv[q], a.wv[q]);
+    }
     for (int m = 0; m < 16; ++m) a.fourier[m] = (float)p.fourier[m];
     a.seed = p.seed;
     a.step = c->step;

@@ -245,6 +245,7 @@ struct StepArgs {
     float u_in, noise_amp, xc, yc;
     float shift_r[4], shift_b[4];       // varphi_i(alpha_k) by speed class |c|^2 = 1..3 (FP16 shift)
     float wv[4];                        // FP16_FIT: w_q / S_v by speed class
+    __half2 kqh[4], wvh[4];             // FP16_FIT prediction: k_q and w_q / S_v in half precision
     float dev_scale, inv_dev_scale;     // FP16_FIT: S_h, 1/S_h (powers of two)
     float v_scale;                      // FP16_FIT: S_v (power of two)
     float fourier[16];                  // inlet profile coefficients a_1, b_1, ..., a_8, b_8
@@ -269,8 +270,9 @@ __device__ __forceinline__ float2 shift_w(const StepArgs &a, int i) {
 // FP16_FIT, A = (A_r, A_b) and v[d] = (v_r, v_b) along axis d, times S_v, widened from FP8 to
 // half precision (exactly).  Unused for FP32.
 struct Own {
-    float2 A;
-    __half2 v[3];
+    float2 A;      // FP16
+    __half2 Ah;    // FP16_FIT
+    __half2 v[3];  // FP16_FIT
 };
 
 __device__ __forceinline__ __half2 fp8x2_to_half2(unsigned int bits) {
@@ -299,7 +301,7 @@ __device__ __forceinline__ Own own_of(const float4 *ph, int n) {
     } else if constexpr (S == STORE_FP16_FIT) {
         const float4 v = __ldg(ph + n);
         const unsigned int y = __float_as_uint(v.y), z = __float_as_uint(v.z), w = __float_as_uint(v.w);
-        o.A = __half22float2(*reinterpret_cast<const __half2 *>(&y));
+        o.Ah = *reinterpret_cast<const __half2 *>(&y);
         o.v[0] = fp8x2_to_half2(z);
         o.v[1] = fp8x2_to_half2(z >> 16);
         o.v[2] = fp8x2_to_half2(w);
@@ -307,14 +309,14 @@ __device__ __forceinline__ Own own_of(const float4 *ph, int n) {
     return o;
 }
 
-// FP16_FIT prediction P^k for the slot of direction j (class q of i = class of j):
-//   P = fl(fl(A k_q) + fl(w_q/S_v (c_j . v))),
-// one fixed sequence of operations, so that the writer and the reader get the same bits.  The
-// odd sum c_j . v runs on both colours at once in half precision (a prediction needs no more).
-// Opposite slots share fl(A k_q) and get exactly opposite odd terms (negation is exact), which
-// lets a reader decode a pair of opposite pulls with one odd sum (gather, lbcm_node.cuh).  The products
-// and sums are __fmul_rn / __fadd_rn, which the compiler never contracts into an FMA, so every
-// call site rounds the same way.
+// FP16_FIT prediction P^k for the slot of direction j (class q of i = class of j), in half-precision
+// arithmetic on both colours at once:
+//   P = fl16(A k_q + fl16(w_q/S_v (c_j . v)))   (one HMUL2, one HFMA2; A, v, k_q, w_q/S_v in half)
+// then widened to FP32.  One fixed sequence of operations, so that the writer and the reader get
+// the same bits; a prediction needs no more precision than this (the deviation from it is what
+// is stored, and the FP8 fit v is far coarser).  Opposite slots get exactly opposite odd terms
+// (negation commutes with rounding to nearest), which lets a reader decode a pair of opposite
+// pulls with one odd sum and one product (gather, lbcm_node.cuh).
 __device__ __forceinline__ __half2 odd_sum(int j, const Own &o) {
     __half2 dh = __float2half2_rn(0.0f);
     if (cx(j) > 0) dh = __hadd2(dh, o.v[0]); else if (cx(j) < 0) dh = __hsub2(dh, o.v[0]);
@@ -322,17 +324,16 @@ __device__ __forceinline__ __half2 odd_sum(int j, const Own &o) {
     if (cz(j) > 0) dh = __hadd2(dh, o.v[2]); else if (cz(j) < 0) dh = __hsub2(dh, o.v[2]);
     return dh;
 }
-__device__ __forceinline__ float2 fit_base(float2 A, int i) {
-    return make_float2(__fmul_rn(A.x, varphi_k(i)), __fmul_rn(A.y, varphi_k(i)));
+// the odd term fl16(w_q/S_v (c_j . v)) of class q of i from the odd sum dh
+__device__ __forceinline__ __half2 fit_odd_h(const StepArgs &a, int i, __half2 dh) {
+    return __hmul2(a.wvh[csq(i)], dh);
 }
-__device__ __forceinline__ float2 fit_odd(const StepArgs &a, int i, __half2 dh) {
-    const float2 d = __half22float2(dh);
-    const float wq = a.wv[csq(i)];
-    return make_float2(__fmul_rn(wq, d.x), __fmul_rn(wq, d.y));
+// P from A and the odd term e
+__device__ __forceinline__ float2 fit_pred_h(const StepArgs &a, int i, __half2 Ah, __half2 e) {
+    return __half22float2(__hfma2(Ah, a.kqh[csq(i)], e));
 }
 __device__ __forceinline__ float2 fit_pred(const StepArgs &a, int i, int j, const Own &o) {
-    const float2 b = fit_base(o.A, i), e = fit_odd(a, i, odd_sum(j, o));
-    return make_float2(__fadd_rn(b.x, e.x), __fadd_rn(b.y, e.y));
+    return fit_pred_h(a, i, o.Ah, fit_odd_h(a, i, odd_sum(j, o)));
 }
 
 // Populations (red, blue) of direction j stored at node src, decoded to FP32; for FP16,
@@ -368,12 +369,12 @@ __device__ __forceinline__ float2 load_pop(const StepArgs &a, int i, int src, co
 // 0, likewise y), so the sum runs over compile-time signs of i.  The sums equal those of
 // fit_pred for slot j bit for bit: 0 + (-v) = 0 - v and d + (-v) = d - v exactly.
 struct OwnFlip {
-    float2 A;
+    __half2 Ah;
     __half2 xp, xn, yp, yn, z;
 };
 __device__ __forceinline__ OwnFlip flip_own(const Own &o, bool wxl, bool wxh, bool wyl, bool wyh) {
     OwnFlip f;
-    f.A = o.A;
+    f.Ah = o.Ah;
     f.xp = wxl ? __hneg2(o.v[0]) : o.v[0];
     f.xn = wxh ? __hneg2(o.v[0]) : o.v[0];
     f.yp = wyl ? __hneg2(o.v[1]) : o.v[1];
@@ -390,8 +391,7 @@ __device__ __forceinline__ float2 load_pop_flip(const StepArgs &a, int i, int sr
     if (cx(i) > 0) dh = __hadd2(dh, o.xp); else if (cx(i) < 0) dh = __hsub2(dh, o.xn);
     if (cy(i) > 0) dh = __hadd2(dh, o.yp); else if (cy(i) < 0) dh = __hsub2(dh, o.yn);
     if (cz(i) > 0) dh = __hadd2(dh, o.z); else if (cz(i) < 0) dh = __hsub2(dh, o.z);
-    const float2 b = fit_base(o.A, i), e = fit_odd(a, i, dh);
-    const float2 p = make_float2(__fadd_rn(b.x, e.x), __fadd_rn(b.y, e.y));
+    const float2 p = fit_pred_h(a, i, o.Ah, fit_odd_h(a, i, dh));
     return make_float2(fmaf(h.x, a.inv_dev_scale, p.x), fmaf(h.y, a.inv_dev_scale, p.y));
 }
 

@@ -83,7 +83,7 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
         }
     } else if constexpr (S == STORE_FP16_FIT) {
         // opposite pulls (i, i+1) were both encoded for this node, with odd terms of opposite
-        // sign: one odd sum and one base product decode the pair
+        // sign: one odd sum and one odd product decode the pair
         const float2 *rest = reinterpret_cast<const float2 *>(a.pin);
         const __half2 *mov = reinterpret_cast<const __half2 *>(rest + a.NN);
         const float2 f0 = __ldg(rest + nb.src(0));
@@ -93,9 +93,8 @@ __device__ __forceinline__ void gather(const StepArgs &a, const Nbr &nb, int z, 
         for (int i = 1; i < 27; i += 2) {
             const float2 hp = __half22float2(__ldg(mov + (size_t)(i - 1) * a.NN + nb.src(i)));
             const float2 hm = __half22float2(__ldg(mov + (size_t)i * a.NN + nb.src(i + 1)));
-            const float2 b = fit_base(own.A, i), e = fit_odd(a, i, odd_sum(i, own));
-            const float2 pp = make_float2(__fadd_rn(b.x, e.x), __fadd_rn(b.y, e.y));
-            const float2 pm = make_float2(__fsub_rn(b.x, e.x), __fsub_rn(b.y, e.y));
+            const __half2 e = fit_odd_h(a, i, odd_sum(i, own));
+            const float2 pp = fit_pred_h(a, i, own.Ah, e), pm = fit_pred_h(a, i, own.Ah, __hneg2(e));
             fr[i] = fmaf(hp.x, a.inv_dev_scale, pp.x);
             fb[i] = fmaf(hp.y, a.inv_dev_scale, pp.y);
             fr[i + 1] = fmaf(hm.x, a.inv_dev_scale, pm.x);
