@@ -661,7 +661,7 @@ def main():
                 line[f"{STORAGE_NAMES[s]}_storage"] = storage_leg(lb, torch, cfg, s, args.steps, args.warmup, peak,
                                                                   world, max_over_ranks, barrier)
         cps = [int(v) for v in args.error_steps.split(",") if v.strip()]
-        if cps:
+        if cps and world == 1:  # numerics, not throughput: one GPU only
             line["error_vs_fp32"] = error_vs_fp32(lb, torch, cfg, cps)
             line["error_vs_fp32"]["note"] = ("velocity relative L2 and max |d phi| against FP32 on the same "
                                              "lattice; by step 2000 the high-Re jet is chaotic and the two "
