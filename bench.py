@@ -112,6 +112,14 @@ def kernel_profile(lat, steps, nodes, storage, peak, cfg_name):
                 "algorithmic_bytes_per_node": bk[top],
                 "traffic": traffic * 1.0 if traffic is not None else None,
                 "traffic_per_node": traffic / nodes if traffic is not None else None}
+    # the same kernel against the instruction issue limit: thread instructions per node from the
+    # committed ncu summary (same sources) over the live duration
+    ipn = profile_value(top if storage == 0 else f"{top}_{tag}", cfg_name, "thread_instructions_per_node")
+    if ipn is not None:
+        rate = ipn * nodes / (kernels[top]["avg_ms"] * 1e-3)
+        roofline["issue"] = {"thread_instructions_per_node": ipn, "achieved": rate / 1e12, "peak": ISSUE_PEAK_TINST_S / 1e12,
+                             "unit": "T thread-instructions/s", "frac": rate / ISSUE_PEAK_TINST_S,
+                             "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz"}
     return kernels, roofline
 
 
@@ -369,9 +377,9 @@ def kernel_source_sha(kernel: str, src: str = None) -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken from the
-    current sources of the kernel (their sha256 is recorded in the summary)."""
+def profile_value(kernel: str, workload: str, key: str):
+    """A number from the committed ncu summary of `kernel` on `workload`, if the summary was
+    taken from the current sources of the kernel (their sha256 is recorded in it)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         kv = {}
@@ -381,9 +389,19 @@ def profile_traffic(kernel: str, workload: str):
                 kv[k.strip()] = v.strip()
         if kv.get("source_sha256_16") != kernel_source_sha(kernel):
             return None
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv[key].split()[0])
     except Exception:
         return None
+
+
+def profile_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary (None if stale or absent)."""
+    return profile_value(kernel, workload, "dram_bytes_per_launch")
+
+
+# Instruction issue capacity of a GB300: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
+# (one warp instruction per scheduler and clock), in thread instructions per second.
+ISSUE_PEAK_TINST_S = 152 * 4 * 32 * 2.07e9
 
 
 class ClockSampler:
